@@ -1,0 +1,157 @@
+"""Seeded synthetic initial fields for the droplet workloads.
+
+This module builds the inputs both the CUDA path and the oracle start from:
+phi (tanh droplets), psi (surfactant background plus per-droplet ramp and
+noise) and the workload recipes with their seeds.  It holds none of the
+method's arithmetic; it only lays out initial conditions.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood 2014): draw k of the
+stream with seed s is mix(s + (k+1) * 0x9E3779B97F4A7C15) where mix is the
+published finaliser; a uniform in [0, 1) is (draw >> 11) * 2**-53.  Site k
+(index y*nx + x) uses draw k.
+"""
+import math
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+def splitmix64(seed, count, start=0):
+    """Draws start .. start+count-1 of the SplitMix64 stream with this seed."""
+    k = np.arange(start + 1, start + count + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + k * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed, count, start=0):
+    return (splitmix64(seed, count, start) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+
+
+def _min_image(d, L):
+    return d - L * np.round(d / L)
+
+
+def interface_width(a, B0, B1, psi_bg):
+    """xi0 = sqrt(2 kappa / -a), kappa = B0 + B1 psi_bg: width of the tanh profile."""
+    kappa = B0 + B1 * psi_bg
+    return math.sqrt(2.0 * kappa / -a)
+
+
+def droplet_fields(nx, ny, droplets, *, a=-0.001, b=0.001, B0=0.006, B1=-0.05,
+                   psi_bg=0.1, xi=None, seed=0):
+    """phi, psi of shape (ny, nx) for a set of droplets on a periodic lattice.
+
+    droplets: iterable of dicts with keys x, y, R and optional psi_mean (default
+    psi_bg), noise (half-width of the uniform noise inside the droplet, default 0),
+    gx, gy (linear psi ramp: + gx*(x-xc)/R + gy*(y-yc)/R inside the droplet).
+    phi = phi_eq tanh(max_k (R_k - r_k) / xi) with phi_eq = sqrt(-a/b), so phi > 0
+    inside the droplets; r_k is the minimum-image distance to droplet k.
+    """
+    xi = interface_width(a, B0, B1, psi_bg) if xi is None else xi
+    phieq = math.sqrt(-a / b)
+    X, Y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))
+    best = np.full((ny, nx), -np.inf)
+    owner = np.full((ny, nx), -1)
+    rel = []
+    for k, d in enumerate(droplets):
+        dx = _min_image(X - d["x"], nx)
+        dy = _min_image(Y - d["y"], ny)
+        s = d["R"] - np.sqrt(dx * dx + dy * dy)
+        rel.append((dx, dy))
+        better = s > best
+        best = np.where(better, s, best)
+        owner = np.where(better, k, owner)
+    phi = phieq * np.tanh(best / xi)
+    psi = np.full((ny, nx), float(psi_bg))
+    noise = 2.0 * uniform01(seed, nx * ny).reshape(ny, nx) - 1.0
+    for k, d in enumerate(droplets):
+        inside = (owner == k) & (best > 0)
+        dx, dy = rel[k]
+        val = (d.get("psi_mean", psi_bg) + d.get("noise", 0.0) * noise
+               + d.get("gx", 0.0) * dx / d["R"] + d.get("gy", 0.0) * dy / d["R"])
+        psi = np.where(inside, val, psi)
+    return phi, psi
+
+
+def default_source(d, nx=None, ny=None):
+    """Source disk of radius R/4 internally tangent to droplet d on its +x side."""
+    Rp = d["R"] / 4.0
+    x = d["x"] + d["R"] - Rp
+    if nx is not None:
+        x = x % nx
+    return (x, d["y"], Rp)
+
+
+# ---------------------------------------------------------------- workloads
+PAPER = dict(a=-0.001, b=0.001, B0=0.006, B1=-0.05, D=0.1, tau=1.0, M=0.1)
+
+
+def single_droplet(n=128, R=20.0, seed=1):
+    """One droplet, radius R, centred on an n x n lattice; psi = 0.1 with noise
+    +-0.01 and a ramp 0.01 (x - xc)/R inside; passive for the first 1000 steps,
+    then sink gamma = 1.5e-3 and the source schedule switch on."""
+    d = dict(x=n / 2, y=n / 2, R=R, psi_mean=0.1, noise=0.01, gx=0.01)
+    phi, psi = droplet_fields(n, n, [d], seed=seed)
+    params = dict(PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=1000)
+    return dict(nx=n, ny=n, phi=phi, psi=psi, params=params,
+                sources=[default_source(d, n, n)], droplets=[d])
+
+
+def two_droplets(nx=512, ny=256, R=25.0, sep=80.0, offset=0.0, seed=2):
+    """Two droplets R on nx x ny, centres (nx/2 -+ sep/2, ny/2 -+ offset/2), each
+    with a psi ramp pointing at its partner of seeded amplitude."""
+    u = uniform01(seed ^ 0x5EED, 2)
+    amp = 0.005 + 0.01 * u
+    d1 = dict(x=nx / 2 - sep / 2, y=ny / 2 - offset / 2, R=R, psi_mean=0.1, noise=0.005,
+              gx=float(amp[0]))
+    d2 = dict(x=nx / 2 + sep / 2, y=ny / 2 + offset / 2, R=R, psi_mean=0.1, noise=0.005,
+              gx=-float(amp[1]))
+    phi, psi = droplet_fields(nx, ny, [d1, d2], seed=seed)
+    s1 = default_source(d1, nx, ny)
+    s2 = (d2["x"] - d2["R"] + d2["R"] / 4.0, d2["y"], d2["R"] / 4.0)
+    params = dict(PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+    return dict(nx=nx, ny=ny, phi=phi, psi=psi, params=params, sources=[s1, s2],
+                droplets=[d1, d2])
+
+
+def emulsion(n=2048, count=64, R=25.0, seed=5):
+    """count droplets of radius R at seeded non-overlapping positions on an
+    n x n lattice (minimum centre distance 2R + 4 xi0, periodic), with seeded psi
+    ramps of random direction."""
+    xi0 = interface_width(PAPER["a"], PAPER["B0"], PAPER["B1"], 0.1)
+    dmin = 2 * R + 4 * xi0
+    centres = []
+    k = 0
+    while len(centres) < count:
+        u = uniform01(seed, 2, start=2 * k)
+        k += 1
+        c = (float(u[0]) * n, float(u[1]) * n)
+        ok = True
+        for (x, y) in centres:
+            dx = _min_image(c[0] - x, n)
+            dy = _min_image(c[1] - y, n)
+            if dx * dx + dy * dy < dmin * dmin:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+        if k > 100000:
+            raise RuntimeError("could not place droplets")
+    ang = uniform01(seed ^ 0xA11CE, count) * 2 * math.pi
+    drops, srcs = [], []
+    for (x, y), th in zip(centres, ang):
+        g = 0.01
+        drops.append(dict(x=x, y=y, R=R, psi_mean=0.1, noise=0.005,
+                          gx=g * math.cos(th), gy=g * math.sin(th)))
+        Rp = R / 4
+        srcs.append(((x + (R - Rp) * math.cos(th)) % n, (y + (R - Rp) * math.sin(th)) % n, Rp))
+    phi, psi = droplet_fields(n, n, drops, seed=seed)
+    params = dict(PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+    return dict(nx=n, ny=n, phi=phi, psi=psi, params=params, sources=srcs, droplets=drops)
