@@ -1,0 +1,165 @@
+/*
+ * lbd.h -- C ABI of the GB300 (sm_103a) solver for the coupled hybrid
+ * lattice-Boltzmann / finite-difference time step of Fadda, Gonnella, Lamura &
+ * Tiribocchi, "Lattice Boltzmann study of chemically-driven self-propelled
+ * droplets" (arXiv 1711.10984), Section 2.
+ *
+ * Model (Section 2.1): order parameter phi, surfactant concentration psi (the
+ * paper's c), total density rho (the paper's n), free energy Eq. (1) with
+ * f_GL = a/2 phi^2 + b/4 phi^4 and B(psi) = B0 + B1 psi.  One time step
+ * (Sections 2.2-2.3) is: force F = -phi grad mu_phi - psi grad mu_psi (Eq. (14),
+ * mu_phi Eq. (3), mu_psi Eq. (5)); D2Q9 BGK collide-and-stream with Guo forcing
+ * (Eqs. (10)-(13)); the two-step finite-difference update of phi and psi
+ * (Eqs. (16)-(19)) with the surfactant source A Theta(R - |r - r_P|) and sink
+ * -gamma (psi - c0) of Section 2.1.
+ *
+ * Readings where the paper is silent or garbled (the same as the test oracle):
+ * Eq. (12) with the factor 1/2 on the quadratic term; a phi mobility M in front
+ * of lap mu_phi (the paper's runs have M = 1); advection in conservative
+ * donor-cell flux form; psi grad mu_psi = grad psi + psi grad m with
+ * m = (B1/2)|grad phi|^2 (no logarithm is evaluated); isotropic D2Q9
+ * gradient and Laplacian stencils; order force -> LB -> advection ->
+ * diffusion, with u^n = (sum f e + F/2)/rho of the same step driving the
+ * advection; activity off for t < t_on, then gamma on and
+ * A(t) = min(A0 (t - t_on), A_max).
+ *
+ * Lattice: periodic nx x ny, site (x, y) at index y*nx + x in every host array.
+ *
+ * Conventions for every function:
+ *   - return 0 (LBD_OK) or a negative LBD_E* code; lbd_strerror() names the code
+ *     and lbd_last_error() returns the context's last message;
+ *   - host pointers are read or written only during the call and never kept;
+ *   - device memory is owned by the context and released by lbd_destroy();
+ *   - work is queued on the CUDA stream given to lbd_create() (NULL = legacy
+ *     default stream); functions that return host data synchronise that stream;
+ *   - a CUDA error is sticky for the context: later calls return LBD_ECUDA.
+ */
+#ifndef LBD_H
+#define LBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBD_OK 0
+#define LBD_EINVAL (-1)      /* bad argument (message in lbd_last_error)          */
+#define LBD_ENOMEM (-2)      /* device or host allocation failed                  */
+#define LBD_ECUDA (-3)       /* a CUDA call or kernel launch failed               */
+#define LBD_ENONFINITE (-4)  /* a NaN or Inf in the fields                        */
+#define LBD_EUNSTABLE (-5)   /* B(psi) <= 0 or psi <= 0 somewhere (Section 4 notes
+                                that the droplet breaks up when B(c) <= 0)        */
+#define LBD_ETIMEOUT (-6)    /* a bounded device-side wait gave up               */
+
+#define LBD_FP64 0           /* populations, phi, psi in double                   */
+#define LBD_FP32 1           /* populations stored as float deviations f_i - w_i,
+                                phi and psi in float; reductions in double        */
+
+#define LBD_FROZEN_U 1u      /* advection uses the uniform velocity (ux0, uy0)    */
+#define LBD_BODY_FORCE 2u    /* add the constant body force (fx, fy) to F         */
+
+#define LBD_MAX_SOURCES 64
+
+typedef struct { int32_t nx, ny; } lbd_grid;
+
+/* Source disk Theta(R - |r - r_P|) of Section 2.1, inclusive, periodic minimum
+ * image; several disks combine as a union.  Centre (x, y) in lattice units. */
+typedef struct { double x, y, R; } lbd_source;
+
+typedef struct {
+    double a, b, B0, B1;   /* free energy Eq. (1): a < 0 for coexistence, b >= 0   */
+    double M;              /* phi mobility multiplying lap mu_phi (Eq. (18))       */
+    double D;              /* surfactant diffusion, L(psi) = D psi (Eq. (4))       */
+    double tau;            /* BGK relaxation time (> 1/2), Eq. (10)                */
+    double gamma, c0;      /* sink -gamma (psi - c0), on for t >= t_on             */
+    double A0, A_max;      /* source strength A(t) = min(A0 (t - t_on), A_max)     */
+    int64_t t_on;          /* activation step of source and sink                   */
+    double fx, fy;         /* body force (LBD_BODY_FORCE)                          */
+    double ux0, uy0;       /* frozen advection velocity (LBD_FROZEN_U)             */
+    uint32_t flags;        /* LBD_FROZEN_U | LBD_BODY_FORCE                        */
+    int32_t precision;     /* LBD_FP64 or LBD_FP32                                 */
+    int32_t n_src;         /* number of entries of src used (0..LBD_MAX_SOURCES)   */
+    int32_t reserved;      /* must be 0                                            */
+    lbd_source src[LBD_MAX_SOURCES];
+} lbd_params;
+
+/* Global diagnostics, accumulated in double on the device. */
+typedef struct {
+    double sum_rho, sum_phi, sum_psi;  /* totals; conserved by the scheme (Eqs. (2), (4), (7)) */
+    double cm_x, cm_y;                 /* centre of mass of the phi >= 0 region (Section 4),
+                                          each site at its minimum image about the reference */
+    double mass_pos;                   /* sum of phi over phi >= 0                           */
+    double min_B, min_psi;             /* min of B0 + B1 psi and of psi                      */
+    int64_t nonfinite;                 /* count of non-finite phi, psi and population values */
+} lbd_diag;
+
+typedef struct lbd_ctx lbd_ctx;
+
+/* Name of an error code; never NULL. */
+const char *lbd_strerror(int code);
+
+/* Last error message of ctx (empty string if none); valid until the next call. */
+const char *lbd_last_error(const lbd_ctx *ctx);
+
+/* Create a solver on the current CUDA device.  grid: nx, ny in [4, 2^20].
+ * params: copied; tau > 1/2, b >= 0, n_src in [0, LBD_MAX_SOURCES], R >= 0,
+ * precision LBD_FP64 or LBD_FP32.  stream: a cudaStream_t (or NULL).
+ * Initial state: rho = 1, u = 0, phi = psi = 0 until lbd_set_fields(); t = 0.
+ * Allocates about (22 words + reduction scratch) per site on the device. */
+int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd_ctx **out);
+
+/* Replace the model parameters (same precision as at creation). */
+int lbd_set_params(lbd_ctx *ctx, const lbd_params *params);
+
+/* Set the state from host arrays of nx*ny doubles: populations become the
+ * equilibrium f_i^eq(rho, u) of Eq. (12) (rho NULL = 1, ux/uy NULL = 0); phi and
+ * psi are required.  Returns LBD_ENONFINITE for a NaN/Inf and LBD_EUNSTABLE if
+ * B0 + B1 psi <= 0 or psi <= 0 anywhere (nothing is changed then). */
+int lbd_set_fields(lbd_ctx *ctx, const double *rho, const double *ux, const double *uy,
+                   const double *phi, const double *psi);
+
+/* Advance nsteps >= 0 coupled time steps (asynchronous on the stream). */
+int lbd_step(lbd_ctx *ctx, int64_t nsteps);
+
+/* Copy the fields at the current time to host arrays of nx*ny doubles (any may
+ * be NULL).  u is Eq. (11): (sum_i f_i e_i + F/2) / rho with the force of the
+ * current phi, psi.  Synchronises the stream. */
+int lbd_get_fields(lbd_ctx *ctx, double *rho, double *ux, double *uy, double *phi, double *psi);
+
+/* Copy the pre-collision populations f_i(r, t) to a host array of 9*nx*ny
+ * doubles, plane i (velocity e_i) at offset i*nx*ny; velocities in the order
+ * (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).  Synchronises. */
+int lbd_get_populations(lbd_ctx *ctx, double *f);
+
+/* Global diagnostics at the current time.  (ref_x, ref_y) in [0,nx) x [0,ny)
+ * is the reference point for the minimum-image centre of mass (pass the
+ * previous centre to follow a moving droplet).  Synchronises. */
+int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
+
+/* Select the tile shape (output sites per CTA) of the fused step kernel.
+ * Only shapes compiled into the library are accepted (see lbd_tiles); the
+ * result of a step does not depend on the tile, only its speed does. */
+int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
+
+/* Tile shapes compiled into the library: writes up to cap pairs into bx[], by[]
+ * and returns how many shapes exist. */
+int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap);
+
+/* Current step count t. */
+int lbd_get_time(const lbd_ctx *ctx, int64_t *t);
+
+/* Set the step count t (used by the activity schedule). */
+int lbd_set_time(lbd_ctx *ctx, int64_t t);
+
+/* Block until the context's queued work is done; reports any CUDA error. */
+int lbd_synchronize(lbd_ctx *ctx);
+
+/* Release all device memory of ctx (NULL is allowed). */
+void lbd_destroy(lbd_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBD_H */

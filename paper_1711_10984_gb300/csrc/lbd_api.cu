@@ -1,0 +1,598 @@
+// lbd_api.cu -- the C ABI of include/lbd.h: context management, state upload,
+// field read-back, populations, and the FP64 diagnostic reductions.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbd_internal.h"
+
+using lbd::StepArgs;
+using lbd::Tile;
+
+namespace {
+
+constexpr int NRED = 9;      // reduction slots, see reduce_partial
+constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+}  // namespace
+
+struct lbd_ctx {
+    int dev = 0;
+    lbd_grid grid{};
+    lbd_params params{};
+    cudaStream_t stream = nullptr;
+    long long pitch = 0, plane = 0;
+    size_t N = 0, esz = 0;
+    void *g[2] = {nullptr, nullptr};
+    void *phi[2] = {nullptr, nullptr};
+    void *psi[2] = {nullptr, nullptr};
+    int cur = 0;
+    double *staging = nullptr;   // dense doubles, 5*N
+    double *pop_staging = nullptr;  // dense doubles, 9*N (on demand)
+    double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
+    int64_t t = 0;
+    Tile tile{32, 16};
+    int sticky = 0;
+    std::string msg;
+};
+
+namespace {
+
+int fail(lbd_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->msg = buf;
+        if (code == LBD_ECUDA) c->sticky = LBD_ECUDA;
+    }
+    return code;
+}
+
+#define CK(ctx, call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(ctx, LBD_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                        __FILE__, __LINE__);                                               \
+    } while (0)
+
+// ---------------------------------------------------------------- kernels
+
+// f_i = f_i^eq(rho, u) of Eq. (12) stored as g_i = f_i - w_i in the pull
+// layout: buffer_i(x) is what site x + e_i reads, so it holds f_i^eq at x + e_i.
+template <typename T>
+__global__ void init_kernel(int nx, int ny, long long pitch, long long plane, const double *rho,
+                            const double *ux, const double *uy, const double *phi,
+                            const double *psi, T *g, T *phi_o, T *psi_o) {
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        const long long o = (long long)y * pitch + x;
+        phi_o[o] = (T)phi[s];
+        psi_o[o] = (T)psi[s];
+        for (int i = 0; i < 9; ++i) {
+            int xs = x + ex[i], ys = y + ey[i];
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            const long long q = (long long)ys * nx + xs;
+            const double n = rho[q], u = ux[q], v = uy[q];
+            const double eu = ex[i] * u + ey[i] * v, usq = u * u + v * v;
+            g[i * plane + o] = (T)(w[i] * ((n - 1.0) + n * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
+        }
+    }
+}
+
+// Pre-collision populations f_i(x) = w_i + buffer_i(x - e_i) as dense doubles.
+template <typename T>
+__global__ void populations_kernel(int nx, int ny, long long pitch, long long plane, const T *g,
+                                   double *f) {
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        for (int i = 0; i < 9; ++i) {
+            int xs = x - ex[i], ys = y - ey[i];
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            f[i * N + s] = w[i] + (double)g[i * plane + (long long)ys * pitch + xs];
+        }
+    }
+}
+
+// Block-wide reduction of the NRED slots (sums, then two minima).
+__device__ void block_reduce(double v[NRED], double *smem /* [NRED][32] */) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < NRED; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = (k == 6 || k == 7) ? fmin(x, y) : x + y;
+        }
+        if (lane == 0) smem[k * 32 + warp] = x;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int k = 0; k < NRED; ++k) {
+            const bool mn = (k == 6 || k == 7);
+            double x = lane < nw ? smem[k * 32 + lane] : (mn ? INFINITY : 0.0);
+            for (int o = 16; o > 0; o >>= 1) {
+                double y = __shfl_down_sync(0xffffffffu, x, o);
+                x = mn ? fmin(x, y) : x + y;
+            }
+            if (lane == 0) v[k] = x;
+        }
+    }
+}
+
+// Slots: 0 sum of all g_i (so sum rho = N + slot 0), 1 sum phi, 2 sum psi,
+// 3-4 sum phi*dx, phi*dy over phi >= 0 (minimum image about the reference),
+// 5 sum phi over phi >= 0, 6 min B(psi), 7 min psi, 8 non-finite count.
+template <typename T>
+__global__ void reduce_partial(int nx, int ny, long long pitch, long long plane, const T *g,
+                               const T *phi, const T *psi, double B0, double B1, double refx,
+                               double refy, double *partial) {
+    __shared__ double smem[NRED * 32];
+    double v[NRED] = {0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+    for (int y = blockIdx.x; y < ny; y += gridDim.x) {
+        double dy = y - refy;
+        if (dy >= 0.5 * ny) dy -= ny; else if (dy < -0.5 * ny) dy += ny;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const long long o = (long long)y * pitch + x;
+            double sg = 0.0;
+            int bad = 0;
+            for (int i = 0; i < 9; ++i) {
+                const double gi = (double)g[i * plane + o];
+                bad |= !isfinite(gi);
+                sg += gi;
+            }
+            const double ph = (double)phi[o], c = (double)psi[o];
+            bad |= !isfinite(ph) | !isfinite(c);
+            v[0] += sg;
+            v[1] += ph;
+            v[2] += c;
+            if (ph >= 0.0) {
+                double dx = x - refx;
+                if (dx >= 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
+                v[3] += ph * dx;
+                v[4] += ph * dy;
+                v[5] += ph;
+            }
+            v[6] = fmin(v[6], B0 + B1 * c);
+            v[7] = fmin(v[7], c);
+            v[8] += bad;
+        }
+    }
+    block_reduce(v, smem);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NRED; ++k) partial[k * gridDim.x + blockIdx.x] = v[k];
+}
+
+__global__ void reduce_final(int nb, const double *partial, double *out) {
+    __shared__ double smem[NRED * 32];
+    double v[NRED] = {0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        for (int k = 0; k < NRED; ++k) {
+            const double x = partial[k * nb + b];
+            v[k] = (k == 6 || k == 7) ? fmin(v[k], x) : v[k] + x;
+        }
+    block_reduce(v, smem);
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NRED; ++k) out[k] = v[k];
+}
+
+// ---------------------------------------------------------------- helpers
+
+int check_params(lbd_ctx *c, const lbd_grid *gr, const lbd_params *p) {
+    if (!p) return fail(c, LBD_EINVAL, "params is NULL");
+    if (!(p->tau > 0.5)) return fail(c, LBD_EINVAL, "tau must be > 1/2 (got %g)", p->tau);
+    if (!(p->b >= 0.0)) return fail(c, LBD_EINVAL, "b must be >= 0 (got %g)", p->b);
+    const double vals[] = {p->a, p->b, p->B0, p->B1, p->M, p->D, p->tau, p->gamma,
+                           p->c0, p->A0, p->A_max, p->fx, p->fy, p->ux0, p->uy0};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail(c, LBD_EINVAL, "non-finite parameter");
+    if (p->precision != LBD_FP64 && p->precision != LBD_FP32)
+        return fail(c, LBD_EINVAL, "precision must be LBD_FP64 or LBD_FP32");
+    if (p->n_src < 0 || p->n_src > LBD_MAX_SOURCES)
+        return fail(c, LBD_EINVAL, "n_src must be in [0, %d]", LBD_MAX_SOURCES);
+    if (p->flags & ~(LBD_FROZEN_U | LBD_BODY_FORCE)) return fail(c, LBD_EINVAL, "unknown flags");
+    for (int k = 0; k < p->n_src; ++k) {
+        const lbd_source &s = p->src[k];
+        if (!std::isfinite(s.x) || !std::isfinite(s.y) || !(s.R >= 0.0))
+            return fail(c, LBD_EINVAL, "bad source %d", k);
+    }
+    if (gr && (gr->nx < 4 || gr->ny < 4 || gr->nx > (1 << 20) || gr->ny > (1 << 20)))
+        return fail(c, LBD_EINVAL, "grid must be within [4, 2^20] per side");
+    return LBD_OK;
+}
+
+template <typename T>
+StepArgs<T> make_args(const lbd_ctx *c) {
+    StepArgs<T> a;
+    memset(&a, 0, sizeof a);
+    const lbd_params &p = c->params;
+    a.nx = c->grid.nx;
+    a.ny = c->grid.ny;
+    a.pitch = c->pitch;
+    a.plane = c->plane;
+    a.g_in = (const T *)c->g[c->cur];
+    a.g_out = (T *)c->g[1 - c->cur];
+    a.phi_in = (const T *)c->phi[c->cur];
+    a.psi_in = (const T *)c->psi[c->cur];
+    a.phi_out = (T *)c->phi[1 - c->cur];
+    a.psi_out = (T *)c->psi[1 - c->cur];
+    a.a = (T)p.a;
+    a.b = (T)p.b;
+    a.B0 = (T)p.B0;
+    a.B1 = (T)p.B1;
+    a.M = (T)p.M;
+    a.D = (T)p.D;
+    a.omega = (T)(1.0 / p.tau);
+    a.guo = (T)(1.0 - 0.5 / p.tau);
+    a.c0 = (T)p.c0;
+    a.fx = (T)p.fx;
+    a.fy = (T)p.fy;
+    a.ux0 = (T)p.ux0;
+    a.uy0 = (T)p.uy0;
+    a.flags = p.flags;
+    a.n_src = p.n_src;
+    for (int k = 0; k < p.n_src; ++k) {
+        double x = std::fmod(p.src[k].x, (double)a.nx), y = std::fmod(p.src[k].y, (double)a.ny);
+        a.src_x[k] = x < 0 ? x + a.nx : x;
+        a.src_y[k] = y < 0 ? y + a.ny : y;
+        a.src_R[k] = p.src[k].R;
+    }
+    return a;
+}
+
+// Activity at step t: off before t_on, then gamma and A = min(A0 (t - t_on), A_max).
+void activity(const lbd_params &p, int64_t t, double *A, double *gamma) {
+    if (t < p.t_on) {
+        *A = 0.0;
+        *gamma = 0.0;
+        return;
+    }
+    const double a = p.A0 * (double)(t - p.t_on);
+    *A = a < p.A_max ? a : p.A_max;
+    *gamma = p.gamma;
+}
+
+template <typename T>
+int run_steps(lbd_ctx *c, int64_t n) {
+    for (int64_t k = 0; k < n; ++k) {
+        StepArgs<T> a = make_args<T>(c);
+        double A, gm;
+        activity(c->params, c->t, &A, &gm);
+        a.A = (T)A;
+        a.gamma = (T)gm;
+        CK(c, lbd::launch_step<T>(a, lbd::MODE_STEP, c->tile, c->stream));
+        c->cur = 1 - c->cur;
+        c->t += 1;
+    }
+    return LBD_OK;
+}
+
+int ensure_staging(lbd_ctx *c) {
+    if (c->staging) return LBD_OK;
+    if (cudaMalloc(&c->staging, 5 * c->N * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->staging = nullptr;
+        return fail(c, LBD_ENOMEM, "staging allocation of %zu bytes failed",
+                    5 * c->N * sizeof(double));
+    }
+    return LBD_OK;
+}
+
+int grid_for(size_t n) {
+    size_t b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b ? b : 1) : 4096);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+const char *lbd_strerror(int code) {
+    switch (code) {
+        case LBD_OK: return "LBD_OK";
+        case LBD_EINVAL: return "LBD_EINVAL: invalid argument";
+        case LBD_ENOMEM: return "LBD_ENOMEM: out of memory";
+        case LBD_ECUDA: return "LBD_ECUDA: CUDA error";
+        case LBD_ENONFINITE: return "LBD_ENONFINITE: non-finite value";
+        case LBD_EUNSTABLE: return "LBD_EUNSTABLE: B(psi) <= 0 or psi <= 0";
+        case LBD_ETIMEOUT: return "LBD_ETIMEOUT: device wait timed out";
+        default: return "unknown lbd error";
+    }
+}
+
+const char *lbd_last_error(const lbd_ctx *ctx) { return ctx ? ctx->msg.c_str() : ""; }
+
+void lbd_destroy(lbd_ctx *c) {
+    if (!c) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->g[k]);
+        cudaFree(c->phi[k]);
+        cudaFree(c->psi[k]);
+    }
+    cudaFree(c->staging);
+    cudaFree(c->pop_staging);
+    cudaFree(c->red_partial);
+    cudaFree(c->red_out);
+    cudaFreeHost(c->h_red);
+    cudaSetDevice(prev);
+    delete c;
+}
+
+int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd_ctx **out) {
+    if (!out || !grid) return LBD_EINVAL;
+    *out = nullptr;
+    lbd_ctx *c = new (std::nothrow) lbd_ctx();
+    if (!c) return LBD_ENOMEM;
+    int rc = check_params(c, grid, params);
+    if (rc == LBD_OK && params->reserved != 0) rc = LBD_EINVAL;
+    if (rc != LBD_OK) {
+        delete c;
+        return rc;
+    }
+    c->grid = *grid;
+    c->params = *params;
+    c->stream = (cudaStream_t)stream;
+    c->esz = params->precision == LBD_FP64 ? sizeof(double) : sizeof(float);
+    // rows padded to 128 bytes
+    const long long align = 128 / (long long)c->esz;
+    c->pitch = (grid->nx + align - 1) / align * align;
+    c->plane = c->pitch * grid->ny;
+    c->N = (size_t)grid->nx * grid->ny;
+    if (cudaGetDevice(&c->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LBD_ECUDA;
+    }
+    const size_t fbytes = (size_t)c->plane * c->esz;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&c->g[k], 9 * fbytes) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->phi[k], fbytes) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->psi[k], fbytes) == cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&c->red_partial, NRED * RED_BLOCKS * sizeof(double)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->red_out, NRED * sizeof(double)) == cudaSuccess;
+    ok &= ok && cudaMallocHost(&c->h_red, NRED * sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbd_destroy(c);
+        return LBD_ENOMEM;
+    }
+    // rest state: g = 0 (f = w_i, rho = 1, u = 0), phi = psi = 0
+    for (int k = 0; k < 2; ++k) {
+        if (cudaMemsetAsync(c->g[k], 0, 9 * fbytes, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(c->phi[k], 0, fbytes, c->stream) != cudaSuccess ||
+            cudaMemsetAsync(c->psi[k], 0, fbytes, c->stream) != cudaSuccess) {
+            cudaGetLastError();
+            lbd_destroy(c);
+            return LBD_ECUDA;
+        }
+    }
+    c->tile = Tile{32, 16};
+    *out = c;
+    return LBD_OK;
+}
+
+int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
+    if (!c) return LBD_EINVAL;
+    int rc = check_params(c, nullptr, p);
+    if (rc != LBD_OK) return rc;
+    if (p->precision != c->params.precision)
+        return fail(c, LBD_EINVAL, "precision cannot change after creation");
+    c->params = *p;
+    return LBD_OK;
+}
+
+int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double *uy,
+                   const double *phi, const double *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (!phi || !psi) return fail(c, LBD_EINVAL, "phi and psi are required");
+    const size_t N = c->N;
+    const lbd_params &p = c->params;
+    for (size_t s = 0; s < N; ++s) {
+        if (!std::isfinite(phi[s]) || !std::isfinite(psi[s]) || (rho && !std::isfinite(rho[s])) ||
+            (ux && !std::isfinite(ux[s])) || (uy && !std::isfinite(uy[s])))
+            return fail(c, LBD_ENONFINITE, "non-finite initial value at site %zu", s);
+        if (!(psi[s] > 0.0) || !(p.B0 + p.B1 * psi[s] > 0.0))
+            return fail(c, LBD_EUNSTABLE, "psi <= 0 or B(psi) <= 0 at site %zu", s);
+        if (rho && !(rho[s] > 0.0)) return fail(c, LBD_EINVAL, "rho <= 0 at site %zu", s);
+    }
+    int rc = ensure_staging(c);
+    if (rc != LBD_OK) return rc;
+    CK(c, cudaSetDevice(c->dev));
+    double *d = c->staging;
+    const size_t B = N * sizeof(double);
+    if (rho) CK(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
+    else {
+        // rho = 1: fill with a kernel-free pattern copy from a host vector
+        std::vector<double> one(N, 1.0);
+        CK(c, cudaMemcpyAsync(d, one.data(), B, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    if (ux) CK(c, cudaMemcpyAsync(d + N, ux, B, cudaMemcpyHostToDevice, c->stream));
+    else CK(c, cudaMemsetAsync(d + N, 0, B, c->stream));
+    if (uy) CK(c, cudaMemcpyAsync(d + 2 * N, uy, B, cudaMemcpyHostToDevice, c->stream));
+    else CK(c, cudaMemsetAsync(d + 2 * N, 0, B, c->stream));
+    CK(c, cudaMemcpyAsync(d + 3 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(d + 4 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
+    const int nb = grid_for(N);
+    if (p.precision == LBD_FP64)
+        init_kernel<double><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
+            (double *)c->g[c->cur], (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+    else
+        init_kernel<float><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
+            (float *)c->g[c->cur], (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_step(lbd_ctx *c, int64_t n) {
+    if (!c || n < 0) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (n == 0) return LBD_OK;
+    CK(c, cudaSetDevice(c->dev));
+    return c->params.precision == LBD_FP64 ? run_steps<double>(c, n) : run_steps<float>(c, n);
+}
+
+int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi, double *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    int rc = ensure_staging(c);
+    if (rc != LBD_OK) return rc;
+    CK(c, cudaSetDevice(c->dev));
+    const size_t N = c->N;
+    double *d = c->staging;
+    if (c->params.precision == LBD_FP64) {
+        StepArgs<double> a = make_args<double>(c);
+        a.rho_f = d; a.ux_f = d + N; a.uy_f = d + 2 * N; a.phi_f = d + 3 * N; a.psi_f = d + 4 * N;
+        CK(c, lbd::launch_step<double>(a, lbd::MODE_FIELDS, c->tile, c->stream));
+    } else {
+        StepArgs<float> a = make_args<float>(c);
+        a.rho_f = d; a.ux_f = d + N; a.uy_f = d + 2 * N; a.phi_f = d + 3 * N; a.psi_f = d + 4 * N;
+        CK(c, lbd::launch_step<float>(a, lbd::MODE_FIELDS, c->tile, c->stream));
+    }
+    double *outs[5] = {rho, ux, uy, phi, psi};
+    for (int k = 0; k < 5; ++k)
+        if (outs[k])
+            CK(c, cudaMemcpyAsync(outs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_get_populations(lbd_ctx *c, double *f) {
+    if (!c || !f) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK(c, cudaSetDevice(c->dev));
+    if (!c->pop_staging) {
+        if (cudaMalloc(&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->pop_staging = nullptr;
+            return fail(c, LBD_ENOMEM, "population staging allocation failed");
+        }
+    }
+    const int nb = grid_for(c->N);
+    if (c->params.precision == LBD_FP64)
+        populations_kernel<double><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const double *)c->g[c->cur], c->pop_staging);
+    else
+        populations_kernel<float><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const float *)c->g[c->cur], c->pop_staging);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(f, c->pop_staging, 9 * c->N * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
+    if (!c || !out) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (!(refx >= 0 && refx < c->grid.nx && refy >= 0 && refy < c->grid.ny))
+        return fail(c, LBD_EINVAL, "reference point outside the lattice");
+    CK(c, cudaSetDevice(c->dev));
+    const lbd_params &p = c->params;
+    if (p.precision == LBD_FP64)
+        reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const double *)c->g[c->cur],
+            (const double *)c->phi[c->cur], (const double *)c->psi[c->cur], p.B0, p.B1, refx, refy,
+            c->red_partial);
+    else
+        reduce_partial<float><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const float *)c->g[c->cur],
+            (const float *)c->phi[c->cur], (const float *)c->psi[c->cur], p.B0, p.B1, refx, refy,
+            c->red_partial);
+    CK(c, cudaGetLastError());
+    reduce_final<<<1, RED_THREADS, 0, c->stream>>>(RED_BLOCKS, c->red_partial, c->red_out);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(c->h_red, c->red_out, NRED * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    const double *r = c->h_red;
+    out->sum_rho = (double)c->N + r[0];
+    out->sum_phi = r[1];
+    out->sum_psi = r[2];
+    out->mass_pos = r[5];
+    out->cm_x = r[5] > 0 ? refx + r[3] / r[5] : NAN;
+    out->cm_y = r[5] > 0 ? refy + r[4] / r[5] : NAN;
+    out->min_B = r[6];
+    out->min_psi = r[7];
+    out->nonfinite = (int64_t)r[8];
+    return LBD_OK;
+}
+
+int lbd_set_tile(lbd_ctx *c, int32_t bx, int32_t by) {
+    if (!c) return LBD_EINVAL;
+    for (int k = 0; k < lbd::n_tiles(); ++k) {
+        const Tile t = lbd::tile_at(k);
+        if (t.bx == bx && t.by == by) {
+            c->tile = t;
+            return LBD_OK;
+        }
+    }
+    return fail(c, LBD_EINVAL, "tile %dx%d is not compiled into the library", bx, by);
+}
+
+int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap) {
+    const int n = lbd::n_tiles();
+    for (int k = 0; k < n && k < cap; ++k) {
+        if (bx) bx[k] = lbd::tile_at(k).bx;
+        if (by) by[k] = lbd::tile_at(k).by;
+    }
+    return n;
+}
+
+int lbd_get_time(const lbd_ctx *c, int64_t *t) {
+    if (!c || !t) return LBD_EINVAL;
+    *t = c->t;
+    return LBD_OK;
+}
+
+int lbd_set_time(lbd_ctx *c, int64_t t) {
+    if (!c) return LBD_EINVAL;
+    c->t = t;
+    return LBD_OK;
+}
+
+int lbd_synchronize(lbd_ctx *c) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK(c, cudaSetDevice(c->dev));
+    CK(c, cudaStreamSynchronize(c->stream));
+    CK(c, cudaGetLastError());
+    return LBD_OK;
+}
+
+}  // extern "C"

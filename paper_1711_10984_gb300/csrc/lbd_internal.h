@@ -1,0 +1,58 @@
+// lbd_internal.h -- device-side argument blocks and launcher declarations shared
+// by the kernels (lbd_step.cu, lbd_aux.cu) and the C ABI (lbd_api.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lbd.h"
+
+namespace lbd {
+
+// Arguments of the fused coupled-step kernel.  Arrays are pitched: site (x, y)
+// at y*pitch + x, population i at offset i*plane with plane = pitch*ny.
+// Populations are stored as deviations g_i = f_i - w_i from the rest weights,
+// in the pull layout: buffer_i(x) holds the post-collision value that site
+// x + e_i reads at the next step.
+template <typename T>
+struct StepArgs {
+    int nx, ny;
+    long long pitch, plane;
+    const T *g_in;
+    T *g_out;
+    const T *phi_in, *psi_in;
+    T *phi_out, *psi_out;
+    // fields mode: dense double outputs (index y*nx + x)
+    double *rho_f, *ux_f, *uy_f, *phi_f, *psi_f;
+    // model
+    T a, b, B0, B1, M, D, omega, guo;  // omega = 1/tau, guo = 1 - 1/(2 tau)
+    T gamma, c0, A;                    // activity at this step
+    T fx, fy, ux0, uy0;
+    uint32_t flags;
+    int n_src;
+    double src_x[LBD_MAX_SOURCES], src_y[LBD_MAX_SOURCES], src_R[LBD_MAX_SOURCES];
+};
+
+enum { MODE_STEP = 0, MODE_FIELDS = 1 };
+
+// Tile shape of the fused kernel (output sites per CTA).
+struct Tile {
+    int bx, by;
+};
+
+// Launch one coupled step (mode MODE_STEP) or the fields evaluation
+// (MODE_FIELDS) with tile shape `tile`; returns the launch error.
+template <typename T>
+cudaError_t launch_step(const StepArgs<T> &a, int mode, Tile tile, cudaStream_t s);
+
+// Shared memory bytes the fused kernel needs for a tile shape.
+template <typename T>
+size_t step_smem_bytes(Tile tile);
+
+// Tile shapes compiled into the library.
+int n_tiles();
+Tile tile_at(int k);
+
+}  // namespace lbd

@@ -1,0 +1,210 @@
+"""ctypes binding of ``liblbd.so`` (C ABI in ``include/lbd.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  ``load()`` raises if the library has not been built (there is no CPU
+fallback).  ``Sim`` wraps one context; the module-level functions keep the C
+names for callers that want the raw ABI.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbd.so")
+
+LBD_OK, LBD_EINVAL, LBD_ENOMEM, LBD_ECUDA = 0, -1, -2, -3
+LBD_ENONFINITE, LBD_EUNSTABLE, LBD_ETIMEOUT = -4, -5, -6
+LBD_FP64, LBD_FP32 = 0, 1
+LBD_FROZEN_U, LBD_BODY_FORCE = 1, 2
+LBD_MAX_SOURCES = 64
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+class lbd_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32)]
+
+
+class lbd_source(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("R", ctypes.c_double)]
+
+
+class lbd_params(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("B0", ctypes.c_double),
+                ("B1", ctypes.c_double), ("M", ctypes.c_double), ("D", ctypes.c_double),
+                ("tau", ctypes.c_double), ("gamma", ctypes.c_double), ("c0", ctypes.c_double),
+                ("A0", ctypes.c_double), ("A_max", ctypes.c_double), ("t_on", ctypes.c_int64),
+                ("fx", ctypes.c_double), ("fy", ctypes.c_double), ("ux0", ctypes.c_double),
+                ("uy0", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("precision", ctypes.c_int32), ("n_src", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("src", lbd_source * LBD_MAX_SOURCES)]
+
+
+class lbd_diag(ctypes.Structure):
+    _fields_ = [("sum_rho", ctypes.c_double), ("sum_phi", ctypes.c_double),
+                ("sum_psi", ctypes.c_double), ("cm_x", ctypes.c_double),
+                ("cm_y", ctypes.c_double), ("mass_pos", ctypes.c_double),
+                ("min_B", ctypes.c_double), ("min_psi", ctypes.c_double),
+                ("nonfinite", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+# name -> (restype, argtypes); the list mirrors include/lbd.h
+SIGNATURES = {
+    "lbd_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "lbd_last_error": (ctypes.c_char_p, [_P]),
+    "lbd_create": (ctypes.c_int, [ctypes.POINTER(lbd_grid), ctypes.POINTER(lbd_params), _P,
+                                  ctypes.POINTER(_P)]),
+    "lbd_set_params": (ctypes.c_int, [_P, ctypes.POINTER(lbd_params)]),
+    "lbd_set_fields": (ctypes.c_int, [_P, _dp, _dp, _dp, _dp, _dp]),
+    "lbd_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lbd_get_fields": (ctypes.c_int, [_P, _dp, _dp, _dp, _dp, _dp]),
+    "lbd_get_populations": (ctypes.c_int, [_P, _dp]),
+    "lbd_diagnostics": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(lbd_diag)]),
+    "lbd_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "lbd_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                 ctypes.c_int32]),
+    "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lbd_synchronize": (ctypes.c_int, [_P]),
+    "lbd_destroy": (None, [_P]),
+}
+
+_lib = None
+
+
+class LbdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (lib().lbd_strerror(code).decode(), msg))
+        self.code = code
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library; raises if it is missing (no CPU fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("liblbd.so is not built; run __graft_entry__.build() or "
+                               "python paper_1711_10984_gb300/build.py")
+        l = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(l, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = l
+    return _lib
+
+
+lib = load
+
+
+def _arr(a, n):
+    if a is None:
+        return None, None
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a, a.ctypes.data_as(_dp)
+
+
+def make_params(precision=LBD_FP64, sources=(), flags=0, **kw):
+    p = lbd_params()
+    defaults = dict(a=-0.001, b=0.001, B0=0.006, B1=-0.05, M=1.0, D=0.1, tau=1.0, gamma=0.0,
+                    c0=0.0, A0=0.0, A_max=0.0, t_on=0, fx=0.0, fy=0.0, ux0=0.0, uy0=0.0)
+    defaults.update(kw)
+    for k, v in defaults.items():
+        setattr(p, k, int(v) if k == "t_on" else float(v))
+    p.flags = int(flags)
+    p.precision = int(precision)
+    sources = list(sources)
+    if len(sources) > LBD_MAX_SOURCES:
+        raise ValueError("at most %d sources" % LBD_MAX_SOURCES)
+    p.n_src = len(sources)
+    for k, (x, y, R) in enumerate(sources):
+        p.src[k] = lbd_source(float(x), float(y), float(R))
+    return p
+
+
+def tiles():
+    """Tile shapes (bx, by) compiled into the library."""
+    bx = (ctypes.c_int32 * 64)()
+    by = (ctypes.c_int32 * 64)()
+    n = load().lbd_tiles(bx, by, 64)
+    return [(bx[k], by[k]) for k in range(n)]
+
+
+class Sim:
+    """One solver context on the current CUDA device."""
+
+    def __init__(self, nx, ny, precision=LBD_FP64, sources=(), flags=0, stream=None, **kw):
+        self.nx, self.ny = int(nx), int(ny)
+        self.N = self.nx * self.ny
+        self.params = make_params(precision, sources, flags, **kw)
+        self._h = _P()
+        g = lbd_grid(self.nx, self.ny)
+        rc = load().lbd_create(ctypes.byref(g), ctypes.byref(self.params),
+                               ctypes.c_void_p(stream or 0), ctypes.byref(self._h))
+        if rc != LBD_OK:
+            raise LbdError(rc, "lbd_create failed")
+
+    def _check(self, rc):
+        if rc != LBD_OK:
+            raise LbdError(rc, load().lbd_last_error(self._h).decode())
+
+    def set_params(self, precision=None, sources=(), flags=0, **kw):
+        prec = self.params.precision if precision is None else precision
+        self.params = make_params(prec, sources, flags, **kw)
+        self._check(load().lbd_set_params(self._h, ctypes.byref(self.params)))
+
+    def set_fields(self, phi, psi, rho=None, ux=None, uy=None):
+        arrs = [_arr(a, self.N) for a in (rho, ux, uy, phi, psi)]
+        self._check(load().lbd_set_fields(self._h, *[p for _, p in arrs]))
+
+    def step(self, n=1):
+        self._check(load().lbd_step(self._h, int(n)))
+        return self
+
+    def fields(self):
+        """(rho, ux, uy, phi, psi) as (ny, nx) float64 arrays."""
+        out = [np.empty(self.N) for _ in range(5)]
+        self._check(load().lbd_get_fields(self._h, *[o.ctypes.data_as(_dp) for o in out]))
+        return tuple(o.reshape(self.ny, self.nx) for o in out)
+
+    def populations(self):
+        f = np.empty(9 * self.N)
+        self._check(load().lbd_get_populations(self._h, f.ctypes.data_as(_dp)))
+        return f.reshape(9, self.ny, self.nx)
+
+    def diagnostics(self, refx, refy):
+        d = lbd_diag()
+        self._check(load().lbd_diagnostics(self._h, float(refx), float(refy), ctypes.byref(d)))
+        return {k: getattr(d, k) for k, _ in lbd_diag._fields_}
+
+    @property
+    def t(self):
+        v = ctypes.c_int64()
+        self._check(load().lbd_get_time(self._h, ctypes.byref(v)))
+        return v.value
+
+    @t.setter
+    def t(self, value):
+        self._check(load().lbd_set_time(self._h, int(value)))
+
+    def set_tile(self, bx, by):
+        self._check(load().lbd_set_tile(self._h, int(bx), int(by)))
+
+    def synchronize(self):
+        self._check(load().lbd_synchronize(self._h))
+
+    def close(self):
+        if self._h:
+            load().lbd_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
