@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the coupled LB/FD droplet step on GB300.
+
+Metric: coupled-step MLUPS (million lattice-site updates per second) and the
+fraction of the HBM roofline, FP32 (shifted populations) against FP64.
+
+Workload (one GPU): the dilute emulsion, a periodic 2048 x 2048 lattice with 64
+seeded droplets of radius 25, seeded surfactant asymmetries and one source disk
+per droplet, source and sink active.  A "step" is one coupled time step of the
+whole lattice (force, LB collide-and-stream, advection, diffusion, source and
+sink); every 100 steps the FP64 diagnostics reduction (totals, centroid, minima)
+runs as well.  The FP32 state is 369 MB, larger than the 129 MB L2, so no L2
+flush is needed between steps.
+
+With --gpus N under torchrun every rank runs its own replica (different seed):
+weak scaling, no data-path collective; the timed region is bracketed by
+barriers and the maximum over ranks is reported.
+
+--impl reference times the FP64 CPU oracle (the paper's scheme written as plain
+C loops) on the host cores, on a 512 x 512 periodic sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS and % HBM roofline, FP32 vs FP64 on 1 GB300; adjoint/forward cost"
+WORKLOAD = ("dilute emulsion: periodic 2048x2048 lattice, 64 seeded droplets R=25, seeded psi "
+            "asymmetry, one source disk per droplet, source and sink on")
+N_SIDE = 2048
+DIAG_EVERY = 100
+# Algorithmic HBM bytes per site-step: 9 populations in + 9 out, phi and psi in + out.
+BYTES_PER_SITE = {1: 22 * 4, 0: 22 * 8}
+# Floating-point operations per site-step of the scheme, counted from the per-site
+# arithmetic of each stage done once (no halo recomputation): chemical
+# potentials 64, force + moments + BGK/Guo collision 315, advection 26,
+# mu* and m* 64, phi/psi updates 82.
+FLOPS_PER_SITE = 551
+# FP64 rate of GB300: 1.25 TFLOP/s nominal at the 2070 MHz maximum SM clock,
+# scaled to the median SM clock sampled during the run.
+FP64_NOMINAL_TFLOPS = 1.25
+SM_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE, help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def workload(n, seed):
+    from paper_1711_10984_gb300 import inputs
+    count = 64 if n == N_SIDE else max(1, (n // 256) ** 2)
+    return inputs.emulsion(n=n, count=count, seed=seed)
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ ours
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in ("lbd_step.cu", "lbd_internal.h"):
+        with open(os.path.join(ROOT, "paper_1711_10984_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    name = "step_kernel_%s_emulsion2048.txt" % ("fp32" if precision == 1 else "fp64")
+    path = os.path.join(ROOT, "profiles", name)
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_hash:\s*(\w+)", text)
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash():
+        return None
+    return float(t.group(1))
+
+
+def time_precision(torch, lbd, autotune, w, prec, steps, warmup, stream, dev_name, barrier):
+    n = w["nx"]
+    sim = lbd.Sim(n, n, precision=prec, sources=w["sources"], stream=stream.cuda_stream,
+                  **w["params"])
+    sim.set_fields(w["phi"], w["psi"])
+    tile = autotune.tune(sim, dev_name)
+    sim.step(warmup)
+    sim.synchronize()
+    ref = (w["droplets"][0]["x"], w["droplets"][0]["y"])
+    d0 = sim.diagnostics(*ref)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0, e1 = ev(), ev()
+    chunks = []
+    e0.record(stream)
+    done = 0
+    launches = 0
+    while done < steps:
+        c = min(DIAG_EVERY, steps - done)
+        k0, k1 = ev(), ev()
+        k0.record(stream)
+        sim.step(c)
+        k1.record(stream)
+        chunks.append((k0, k1, c))
+        done += c
+        launches += c
+        if done % DIAG_EVERY == 0 or done == steps:
+            sim.diagnostics(*ref)   # S8 reduction: two launches, synchronises
+            launches += 2
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    total_ms = e0.elapsed_time(e1)
+    kernel_ms = sum(a.elapsed_time(b) for a, b, _ in chunks)
+    d1 = sim.diagnostics(*ref)
+    drift = {k: (d1[k] - d0[k]) / abs(d0[k]) for k in ("sum_rho", "sum_phi")}
+    sim.close()
+    return dict(total_ms=total_ms, kernel_ms=kernel_ms, tile=list(tile), launches=launches,
+                drift=drift, nonfinite=d1["nonfinite"])
+
+
+def time_e2e(torch, lbd, w, steps, stream):
+    """The same FP32 job through the public API from pinned host memory: upload
+    phi, psi (H2D), run the steps, read all five fields back (D2H)."""
+    n = w["nx"]
+    N = n * n
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    phi_h, psi_h = pin(w["phi"]), pin(w["psi"])
+    outs = [torch.empty(N, dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
+    sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=w["sources"], stream=stream.cuda_stream,
+                  **w["params"])
+    sim.set_fields(phi_h, psi_h)  # untimed first call (allocates the staging area)
+    sim.step(2)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    sim.set_fields(phi_h, psi_h)
+    sim.step(steps)
+    import ctypes
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lbd.load().lbd_get_fields(sim._h, *[o.ctypes.data_as(dp) for o in outs])
+    e1.record(stream)
+    e1.synchronize()
+    wall = time.perf_counter() - t0
+    sim._check(rc)
+    sim.close()
+    ms = max(e0.elapsed_time(e1), wall * 1e3)
+    return dict(ms=ms, h2d=2 * 8 * N, d2h=5 * 8 * N)
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The FP64 oracle as it stands on the host cores, on the same 2048^2
+    workload, for as many whole steps as fit in about budget_s seconds."""
+    import oracle
+    n = w["nx"]
+    p = oracle.Params(n, n, sources=w["sources"], **w["params"])
+    s = oracle.State(p, w["phi"], w["psi"])
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        s.step(1)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or k >= 50:
+            break
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    return {"value": n * n * k / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": "%d whole steps of the %dx%d workload (FP64, C oracle, OpenMP rows)"
+                      % (k, n, n)}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_1711_10984_gb300 import autotune, lbd
+    lbd.load()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    barrier = (lambda: dist.barrier()) if dist else (lambda: None)
+    dev_name = torch.cuda.get_device_name(local)
+    w = workload(args.n, seed=5 + rank)
+    N = args.n * args.n
+    stream = torch.cuda.Stream()
+    clocks = Clocks(local)
+    clocks.start()
+    r32 = time_precision(torch, lbd, autotune, w, lbd.LBD_FP32, args.steps, args.warmup, stream,
+                         dev_name, barrier)
+    r64 = time_precision(torch, lbd, autotune, w, lbd.LBD_FP64, args.steps, args.warmup, stream,
+                         dev_name, barrier)
+    clk = clocks.stop()
+    e2e = time_e2e(torch, lbd, w, args.steps, stream)
+
+    def maxr(v):
+        if not dist:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t32, t64, te = maxr(r32["total_ms"]), maxr(r64["total_ms"]), maxr(e2e["ms"])
+    k32, k64 = maxr(r32["kernel_ms"]), maxr(r64["kernel_ms"])
+    cpu = cpu_baseline(w) if (rank == 0 and world == 1) else None
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    hbm, src = peaks()
+    mlups32 = world * N * args.steps / t32 / 1e3
+    mlups64 = world * N * args.steps / t64 / 1e3
+    ach32 = BYTES_PER_SITE[1] * N / (k32 / args.steps * 1e-3) / 1e9
+    ach64_gbs = BYTES_PER_SITE[0] * N / (k64 / args.steps * 1e-3) / 1e9
+    flops64 = FLOPS_PER_SITE * N / (k64 / args.steps * 1e-3) / 1e12
+    mhz = clk.get("sm_mhz") or SM_MAX_MHZ
+    fp64_peak = FP64_NOMINAL_TFLOPS * mhz / SM_MAX_MHZ
+    out = {
+        "metric": METRIC, "value": round(mlups32, 1), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sites_per_gpu": N, "precision": "FP32 shifted populations",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "state 369 MB > 129 MB L2, no flush", "tile": r32["tile"],
+                   "diagnostics_every": DIAG_EVERY},
+        "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm, "unit": "GB/s",
+                     "frac": round(ach32 / hbm, 4), "traffic": ncu_traffic(1),
+                     "peak_source": src, "kernel": "step_kernel<float>",
+                     "bytes_per_site": BYTES_PER_SITE[1]},
+        "fp64": {"value": round(mlups64, 1), "unit": "MLUPS", "ms_per_step": t64 / args.steps,
+                 "dtype": "f64", "tile": r64["tile"],
+                 "roofline": {"bound": "alu", "achieved": round(flops64, 4),
+                              "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                              "frac": round(flops64 / fp64_peak, 4),
+                              "peak_source": "nominal 1.25 TFLOP/s at 2070 MHz x median SM clock",
+                              "flops_per_site": FLOPS_PER_SITE,
+                              "hbm_gbs_achieved": round(ach64_gbs, 1),
+                              "hbm_frac": round(ach64_gbs / hbm, 4),
+                              "traffic": ncu_traffic(0)},
+                 "drift": r64["drift"]},
+        "fp32_over_fp64_speedup": round(t64 / t32, 2),
+        "fp32_drift": r32["drift"],
+        "adjoint_forward_cost": None,
+        "e2e": {"value": round(world * N * args.steps / te / 1e3, 1), "unit": "MLUPS",
+                "h2d_bytes_per_step": e2e["h2d"] / args.steps,
+                "d2h_bytes_per_step": e2e["d2h"] / args.steps,
+                "what": "lbd_set_fields from pinned host phi/psi, lbd_step(K), "
+                        "lbd_get_fields of rho, u, phi, psi to pinned host"},
+        "clocks": clk,
+        "gpu_launches": r32["launches"],
+    }
+    if cpu:
+        out["cpu_baseline"] = cpu
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ reference
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    n_full = args.n
+    w = workload(n_full, seed=5)
+    ns = min(512, n_full)
+    # periodic 512 x 512 sample: the window's own droplets and sources
+    phi = np.ascontiguousarray(w["phi"][:ns, :ns])
+    psi = np.ascontiguousarray(w["psi"][:ns, :ns])
+    srcs = [s for s in w["sources"] if s[0] < ns and s[1] < ns]
+    p = oracle.Params(ns, ns, sources=srcs, **w["params"])
+    s = oracle.State(p, phi, psi)
+    s.step(args.warmup)
+    t0 = time.perf_counter()
+    s.step(args.steps)
+    el = time.perf_counter() - t0
+    v = ns * ns * args.steps / el / 1e6
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count()))
+    sample = "%dx%d periodic window of the workload per step (FP64 C oracle)" % (ns, ns)
+    out = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": el * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample": sample},
+           "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": cores,
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        run_reference(args)
+    else:
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

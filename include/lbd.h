@@ -146,6 +146,13 @@ int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
  * and returns how many shapes exist. */
 int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap);
 
+/* Time every compiled tile shape on this context's current state (reps launches
+ * each, CUDA events on the context's stream) and keep the fastest; the trial
+ * launches write only the scratch half of the double-buffered state, so the
+ * state and t are unchanged.  The chosen shape is returned in *bx, *by (either
+ * may be NULL).  Synchronises. */
+int lbd_autotune(lbd_ctx *ctx, int32_t reps, int32_t *bx, int32_t *by);
+
 /* Current step count t. */
 int lbd_get_time(const lbd_ctx *ctx, int64_t *t);
 

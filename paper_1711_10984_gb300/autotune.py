@@ -1,0 +1,46 @@
+"""Tile-shape autotuner with an on-disk cache.
+
+The timing itself is native (``lbd_autotune`` times every compiled tile shape on
+the context's own state with CUDA events); this module only remembers the
+winner per (device name, nx, ny, precision) in a JSON file so that later runs
+skip the search.
+"""
+import json
+import os
+
+CACHE = os.environ.get("LBD_TUNE_CACHE",
+                       os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json"))
+
+
+def _key(device, nx, ny, precision):
+    return "%s|%dx%d|%s" % (device, nx, ny, "fp64" if precision == 0 else "fp32")
+
+
+def load_cache(path=CACHE):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def store(key, tile, path=CACHE):
+    cache = load_cache(path)
+    cache[key] = list(tile)
+    tmp = path + ".tmp.%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def tune(sim, device, reps=20, path=CACHE, refresh=False):
+    """Set sim's tile from the cache, or search, store and set it.  Returns the tile."""
+    key = _key(device, sim.nx, sim.ny, sim.params.precision)
+    cache = load_cache(path)
+    if key in cache and not refresh:
+        tile = tuple(cache[key])
+        sim.set_tile(*tile)
+        return tile
+    tile = sim.autotune(reps)
+    store(key, tile, path)
+    return tile

@@ -35,6 +35,7 @@ struct lbd_ctx {
     double *staging = nullptr;   // dense doubles, 5*N
     double *pop_staging = nullptr;  // dense doubles, 9*N (on demand)
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
+    uint32_t *theta = nullptr;      // source indicator, one bit per site
     int64_t t = 0;
     Tile tile{32, 16};
     int sticky = 0;
@@ -93,6 +94,12 @@ __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, co
             g[i * plane + o] = (T)(w[i] * ((n - 1.0) + n * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
         }
     }
+}
+
+__global__ void fill_kernel(double *a, long long n, double v) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x)
+        a[s] = v;
 }
 
 // Pre-collision populations f_i(x) = w_i + buffer_i(x - e_i) as dense doubles.
@@ -251,13 +258,8 @@ StepArgs<T> make_args(const lbd_ctx *c) {
     a.ux0 = (T)p.ux0;
     a.uy0 = (T)p.uy0;
     a.flags = p.flags;
-    a.n_src = p.n_src;
-    for (int k = 0; k < p.n_src; ++k) {
-        double x = std::fmod(p.src[k].x, (double)a.nx), y = std::fmod(p.src[k].y, (double)a.ny);
-        a.src_x[k] = x < 0 ? x + a.nx : x;
-        a.src_y[k] = y < 0 ? y + a.ny : y;
-        a.src_R[k] = p.src[k].R;
-    }
+    a.theta = p.n_src > 0 ? c->theta : nullptr;
+    a.theta_words = (a.nx + 31) / 32;
     return a;
 }
 
@@ -285,6 +287,21 @@ int run_steps(lbd_ctx *c, int64_t n) {
         c->cur = 1 - c->cur;
         c->t += 1;
     }
+    return LBD_OK;
+}
+
+// Source disks with centres wrapped into [0, nx) x [0, ny), then the bit mask.
+int update_theta(lbd_ctx *c) {
+    const lbd_params &p = c->params;
+    lbd_source src[LBD_MAX_SOURCES];
+    for (int k = 0; k < p.n_src; ++k) {
+        double x = std::fmod(p.src[k].x, (double)c->grid.nx);
+        double y = std::fmod(p.src[k].y, (double)c->grid.ny);
+        src[k].x = x < 0 ? x + c->grid.nx : x;
+        src[k].y = y < 0 ? y + c->grid.ny : y;
+        src[k].R = p.src[k].R;
+    }
+    CK(c, lbd::launch_theta_mask(c->grid.nx, c->grid.ny, p.n_src, src, c->theta, c->stream));
     return LBD_OK;
 }
 
@@ -341,6 +358,7 @@ void lbd_destroy(lbd_ctx *c) {
     cudaFree(c->pop_staging);
     cudaFree(c->red_partial);
     cudaFree(c->red_out);
+    cudaFree(c->theta);
     cudaFreeHost(c->h_red);
     cudaSetDevice(prev);
     delete c;
@@ -381,6 +399,7 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
     ok &= ok && cudaMalloc(&c->red_partial, NRED * RED_BLOCKS * sizeof(double)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->red_out, NRED * sizeof(double)) == cudaSuccess;
     ok &= ok && cudaMallocHost(&c->h_red, NRED * sizeof(double)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->theta, (size_t)((grid->nx + 31) / 32) * grid->ny * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbd_destroy(c);
@@ -397,6 +416,10 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
         }
     }
     c->tile = Tile{32, 16};
+    if (update_theta(c) != LBD_OK) {
+        lbd_destroy(c);
+        return LBD_ECUDA;
+    }
     *out = c;
     return LBD_OK;
 }
@@ -408,7 +431,8 @@ int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
     if (p->precision != c->params.precision)
         return fail(c, LBD_EINVAL, "precision cannot change after creation");
     c->params = *p;
-    return LBD_OK;
+    CK(c, cudaSetDevice(c->dev));
+    return update_theta(c);
 }
 
 int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double *uy,
@@ -431,12 +455,11 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     CK(c, cudaSetDevice(c->dev));
     double *d = c->staging;
     const size_t B = N * sizeof(double);
+    const int nb = grid_for(N);
     if (rho) CK(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
     else {
-        // rho = 1: fill with a kernel-free pattern copy from a host vector
-        std::vector<double> one(N, 1.0);
-        CK(c, cudaMemcpyAsync(d, one.data(), B, cudaMemcpyHostToDevice, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
+        fill_kernel<<<nb, 256, 0, c->stream>>>(d, (long long)N, 1.0);
+        CK(c, cudaGetLastError());
     }
     if (ux) CK(c, cudaMemcpyAsync(d + N, ux, B, cudaMemcpyHostToDevice, c->stream));
     else CK(c, cudaMemsetAsync(d + N, 0, B, c->stream));
@@ -444,7 +467,6 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     else CK(c, cudaMemsetAsync(d + 2 * N, 0, B, c->stream));
     CK(c, cudaMemcpyAsync(d + 3 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaMemcpyAsync(d + 4 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
-    const int nb = grid_for(N);
     if (p.precision == LBD_FP64)
         init_kernel<double><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
@@ -563,6 +585,53 @@ int lbd_set_tile(lbd_ctx *c, int32_t bx, int32_t by) {
         }
     }
     return fail(c, LBD_EINVAL, "tile %dx%d is not compiled into the library", bx, by);
+}
+
+int lbd_autotune(lbd_ctx *c, int32_t reps, int32_t *bx, int32_t *by) {
+    if (!c || reps < 1) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK(c, cudaSetDevice(c->dev));
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Tile keep = c->tile;
+    int rc = LBD_OK;
+    for (int k = 0; k < lbd::n_tiles() && rc == LBD_OK; ++k) {
+        const Tile t = lbd::tile_at(k);
+        // The trial launches read the current buffers and write the others; the
+        // buffers are not swapped, so the state and t are unchanged.
+        auto launch = [&]() -> cudaError_t {
+            if (c->params.precision == LBD_FP64) {
+                StepArgs<double> a = make_args<double>(c);
+                return lbd::launch_step<double>(a, lbd::MODE_STEP, t, c->stream);
+            }
+            StepArgs<float> a = make_args<float>(c);
+            return lbd::launch_step<float>(a, lbd::MODE_STEP, t, c->stream);
+        };
+        cudaError_t e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = fail(c, LBD_ECUDA, "autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            keep = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LBD_OK) return rc;
+    c->tile = keep;
+    if (bx) *bx = keep.bx;
+    if (by) *by = keep.by;
+    return LBD_OK;
 }
 
 int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap) {

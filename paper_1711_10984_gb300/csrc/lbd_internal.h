@@ -31,8 +31,10 @@ struct StepArgs {
     T gamma, c0, A;                    // activity at this step
     T fx, fy, ux0, uy0;
     uint32_t flags;
-    int n_src;
-    double src_x[LBD_MAX_SOURCES], src_y[LBD_MAX_SOURCES], src_R[LBD_MAX_SOURCES];
+    // Source indicator Theta as a bit mask: bit (x & 31) of word y*theta_words + x/32;
+    // nullptr when there is no source.
+    const uint32_t *theta;
+    int theta_words;
 };
 
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
@@ -46,6 +48,11 @@ struct Tile {
 // (MODE_FIELDS) with tile shape `tile`; returns the launch error.
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &a, int mode, Tile tile, cudaStream_t s);
+
+// Fill the source indicator bit mask (words per row = (nx + 31) / 32) for the
+// disks (x, y, R) with the exact inclusive double-precision test.
+cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, uint32_t *mask,
+                              cudaStream_t s);
 
 // Shared memory bytes the fused kernel needs for a tile shape.
 template <typename T>

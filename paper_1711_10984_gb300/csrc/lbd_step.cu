@@ -22,6 +22,10 @@
 namespace lbd {
 namespace {
 
+struct SourceList {
+    lbd_source s[LBD_MAX_SOURCES];
+};
+
 constexpr int NT = 256;   // threads per CTA
 constexpr int HALO = 5;   // phi/psi halo: u on R3 needs F on R3, which needs R5
 
@@ -51,14 +55,31 @@ struct Stencil {
     }
 };
 
-// Tile ownership of a source disk: conservative test whether any in-domain site
-// of [xa, xb) x [ya, yb) lies within R of (sx, sy) (minimum image).
-__device__ __forceinline__ double axis_gap(double s, int lo, int hi, int n) {
-    if (s >= lo && s <= hi - 1) return 0.0;
-    double d1 = lo - s, d2 = (hi - 1) - s;
-    if (d1 > 0.5 * n) d1 -= n; else if (d1 < -0.5 * n) d1 += n;
-    if (d2 > 0.5 * n) d2 -= n; else if (d2 < -0.5 * n) d2 += n;
-    return fmin(fabs(d1), fabs(d2));
+// Source indicator Theta(R - |r - r_P|), Section 2.1: inclusive, periodic minimum
+// image, union of the disks.  Evaluated once per parameter set (in double, with
+// no contraction into FMAs so that the boundary test is the plain IEEE one);
+// the step kernel reads one bit per site.
+__global__ void theta_mask_kernel(int nx, int ny, int n_src, SourceList src, uint32_t *mask) {
+    const int words = (nx + 31) / 32;
+    const long long total = (long long)words * ny;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(w / words), x0 = (int)(w - (long long)y * words) * 32;
+        uint32_t bits = 0;
+        for (int b = 0; b < 32 && x0 + b < nx; ++b) {
+            for (int k = 0; k < n_src; ++k) {
+                double dx = (double)(x0 + b) - src.s[k].x, dy = (double)y - src.s[k].y;
+                if (dx > 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
+                if (dy > 0.5 * ny) dy -= ny; else if (dy < -0.5 * ny) dy += ny;
+                if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <=
+                    __dmul_rn(src.s[k].R, src.s[k].R)) {
+                    bits |= 1u << b;
+                    break;
+                }
+            }
+        }
+        mask[w] = bits;
+    }
 }
 
 template <typename T, int BX, int BY, int MODE>
@@ -81,8 +102,6 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
     T *s_pss = s_phs + W2 * H2;
     int *s_gx = reinterpret_cast<int *>(s_pss + W2 * H2);  // wrapped x of R5 columns
     int *s_gy = s_gx + W5;                                 // wrapped y of R5 rows
-    int *s_src = s_gy + H5;                                // sources touching this tile
-    __shared__ int s_nsrc;
 
     const int tid = threadIdx.x;
     const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
@@ -91,15 +110,6 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
 
     for (int k = tid; k < W5; k += NT) s_gx[k] = pmod(x0 - HALO + k, nx);
     for (int k = tid; k < H5; k += NT) s_gy[k] = pmod(y0 - HALO + k, ny);
-    if (MODE == MODE_STEP && tid == 0) {
-        int cnt = 0;
-        const int xb = min(x0 + BX, nx), yb = min(y0 + BY, ny);
-        for (int k = 0; k < p.n_src; ++k) {
-            double gx = axis_gap(p.src_x[k], x0, xb, nx), gy = axis_gap(p.src_y[k], y0, yb, ny);
-            if (gx * gx + gy * gy <= p.src_R[k] * p.src_R[k] + 1e-9) s_src[cnt++] = k;
-        }
-        s_nsrc = cnt;
-    }
     __syncthreads();
 
     // ---- stage 0: phi^n, psi^n on R5 -------------------------------------
@@ -302,19 +312,10 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
 #undef LBD_LINK
         const T div = ax * T(2.0 / 3.0) + dg * T(1.0 / 6.0);
         T src = T(0);
-        if (s_nsrc > 0) {
-            const int gx = x0 + tx, gy = y0 + ty;
-            for (int j = 0; j < s_nsrc; ++j) {
-                const int q = s_src[j];
-                double dx = (double)gx - p.src_x[q], dy = (double)gy - p.src_y[q];
-                if (dx > 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
-                if (dy > 0.5 * ny) dy -= ny; else if (dy < -0.5 * ny) dy += ny;
-                if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <=
-                    __dmul_rn(p.src_R[q], p.src_R[q])) {
-                    src = p.A;
-                    break;
-                }
-            }
+        if (p.theta) {
+            const int gx = x0 + tx;
+            const uint32_t w = p.theta[(long long)(y0 + ty) * p.theta_words + (gx >> 5)];
+            if ((w >> (gx & 31)) & 1u) src = p.A;
         }
         const T psi_new = c0 + (p.D * div - p.gamma * (c0 - p.c0) + src);
         const long long o = (long long)(y0 + ty) * pitch + (x0 + tx);
@@ -327,7 +328,7 @@ template <typename T, int BX, int BY>
 constexpr size_t smem_for() {
     return sizeof(T) * (size_t)(2 * (BX + 10) * (BY + 10) + 2 * (BX + 8) * (BY + 8) +
                                 2 * (BX + 6) * (BY + 6) + 2 * (BX + 4) * (BY + 4)) +
-           sizeof(int) * (size_t)((BX + 10) + (BY + 10) + LBD_MAX_SOURCES);
+           sizeof(int) * (size_t)((BX + 10) + (BY + 10));
 }
 
 template <typename T, int BX, int BY>
@@ -360,6 +361,16 @@ cudaError_t launch_tile(const StepArgs<T> &a, int mode, cudaStream_t s) {
 constexpr Tile kTiles[] = {{32, 8}, {32, 16}, {64, 8}, {32, 32}, {64, 16}};
 
 }  // namespace
+
+cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, uint32_t *mask,
+                              cudaStream_t s) {
+    SourceList l;
+    for (int k = 0; k < n_src; ++k) l.s[k] = src[k];
+    const long long words = (long long)((nx + 31) / 32) * ny;
+    const int nb = (int)((words + 255) / 256 < 4096 ? (words + 255) / 256 : 4096);
+    theta_mask_kernel<<<nb, 256, 0, s>>>(nx, ny, n_src, l, mask);
+    return cudaGetLastError();
+}
 
 int n_tiles() { return (int)(sizeof(kTiles) / sizeof(kTiles[0])); }
 Tile tile_at(int k) { return kTiles[k]; }

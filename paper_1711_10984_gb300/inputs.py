@@ -56,27 +56,36 @@ def droplet_fields(nx, ny, droplets, *, a=-0.001, b=0.001, B0=0.006, B1=-0.05,
     """
     xi = interface_width(a, B0, B1, psi_bg) if xi is None else xi
     phieq = math.sqrt(-a / b)
-    X, Y = np.meshgrid(np.arange(nx, dtype=np.float64), np.arange(ny, dtype=np.float64))
     best = np.full((ny, nx), -np.inf)
     owner = np.full((ny, nx), -1)
-    rel = []
+    windows = []
     for k, d in enumerate(droplets):
-        dx = _min_image(X - d["x"], nx)
-        dy = _min_image(Y - d["y"], ny)
+        # tanh(-20) rounds to -1 in double: beyond R + 20 xi a droplet changes nothing
+        half = d["R"] + 20.0 * xi
+        xs = np.arange(math.floor(d["x"] - half), math.ceil(d["x"] + half) + 1)
+        ys = np.arange(math.floor(d["y"] - half), math.ceil(d["y"] + half) + 1)
+        if len(xs) >= nx:
+            xs = np.arange(nx)
+        if len(ys) >= ny:
+            ys = np.arange(ny)
+        xs, ys = xs % nx, ys % ny
+        dx = _min_image(xs[None, :].astype(np.float64) - d["x"], nx)
+        dy = _min_image(ys[:, None].astype(np.float64) - d["y"], ny)
         s = d["R"] - np.sqrt(dx * dx + dy * dy)
-        rel.append((dx, dy))
-        better = s > best
-        best = np.where(better, s, best)
-        owner = np.where(better, k, owner)
+        sub = np.ix_(ys, xs)
+        better = s > best[sub]
+        best[sub] = np.where(better, s, best[sub])
+        owner[sub] = np.where(better, k, owner[sub])
+        windows.append((sub, dx, dy))
     phi = phieq * np.tanh(best / xi)
     psi = np.full((ny, nx), float(psi_bg))
     noise = 2.0 * uniform01(seed, nx * ny).reshape(ny, nx) - 1.0
     for k, d in enumerate(droplets):
-        inside = (owner == k) & (best > 0)
-        dx, dy = rel[k]
-        val = (d.get("psi_mean", psi_bg) + d.get("noise", 0.0) * noise
+        sub, dx, dy = windows[k]
+        inside = (owner[sub] == k) & (best[sub] > 0)
+        val = (d.get("psi_mean", psi_bg) + d.get("noise", 0.0) * noise[sub]
                + d.get("gx", 0.0) * dx / d["R"] + d.get("gy", 0.0) * dy / d["R"])
-        psi = np.where(inside, val, psi)
+        psi[sub] = np.where(inside, val, psi[sub])
     return phi, psi
 
 

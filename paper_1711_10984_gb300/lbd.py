@@ -66,6 +66,8 @@ SIGNATURES = {
     "lbd_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "lbd_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int32]),
+    "lbd_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)]),
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_synchronize": (ctypes.c_int, [_P]),
@@ -194,6 +196,12 @@ class Sim:
 
     def set_tile(self, bx, by):
         self._check(load().lbd_set_tile(self._h, int(bx), int(by)))
+
+    def autotune(self, reps=20):
+        """Time every compiled tile on the current state; keep and return the fastest."""
+        bx, by = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().lbd_autotune(self._h, int(reps), ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
 
     def synchronize(self):
         self._check(load().lbd_synchronize(self._h))
