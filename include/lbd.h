@@ -153,6 +153,37 @@ int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap);
  * may be NULL).  Synchronises. */
 int lbd_autotune(lbd_ctx *ctx, int32_t reps, int32_t *bx, int32_t *by);
 
+/* Diagnostics of a state that the caller keeps in its own device memory, for
+ * callers that cannot allocate device memory through cudaMalloc: code whose
+ * device memory all comes from another allocator (a framework's caching pool,
+ * a fixed arena reserved at start-up) and loops that must not pay the device
+ * synchronisation a cudaMalloc or cudaFree can cause.  It computes the same
+ * quantities as lbd_diagnostics (the paper has no counterpart of this entry
+ * point) and allocates nothing: its reduction scratch is a fixed array of
+ * 43,848 bytes (608 blocks x 9 partial sums + 9 results) compiled into the
+ * library, which every GPU that loads the library holds until the process
+ * exits.
+ *
+ * Inputs (device pointers, caller-owned, read only): g = the 9 population
+ * planes stored as deviations f_i - w_i from the rest weights, plane i at
+ * offset i*pitch*ny elements, site (x, y) at y*pitch + x (the order of the
+ * sites within a plane does not matter for the totals); phi, psi with the
+ * same site layout; element type double (LBD_FP64) or float (LBD_FP32).
+ * Output: *out, a host struct.  B0, B1: B(psi) = B0 + B1 psi for min_B.
+ * Limits: 1 <= nx, ny <= 2^20 and pitch >= nx, ref in [0,nx) x [0,ny);
+ * anything else returns LBD_EINVAL before any work.  Works on the current
+ * CUDA device and the given stream (NULL = legacy default); synchronises it.
+ *
+ * The first call on each device looks up the device address of the scratch
+ * array (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (different streams or host threads) race on it and must
+ * be serialised by the caller.  Every scratch slot is overwritten on each call,
+ * so nothing needs clearing. */
+int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precision,
+                           const void *g, const void *phi, const void *psi, double B0, double B1,
+                           double ref_x, double ref_y, void *stream, lbd_diag *out);
+
 /* Current step count t. */
 int lbd_get_time(const lbd_ctx *ctx, int64_t *t);
 

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -202,6 +203,38 @@ __global__ void reduce_final(int nb, const double *partial, double *out) {
     block_reduce(v, smem);
     if (threadIdx.x == 0)
         for (int k = 0; k < NRED; ++k) out[k] = v[k];
+}
+
+// -------------------------------------------- scratch of lbd_diagnostics_static
+// Partial sums of the RED_BLOCKS reduction blocks plus the NRED results:
+// 5481 doubles = 43,848 bytes.  Every GPU that loads this library holds the
+// array until the process exits.  Each call overwrites every slot it reads
+// (each block writes all of its partials, the final kernel writes all results),
+// so nothing has to be cleared between calls.
+constexpr int kStaticScratchDoubles = NRED * RED_BLOCKS + NRED;
+static __device__ __align__(256) double g_diag_static_scratch[kStaticScratchDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+double *g_static_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device.  Host code only
+// sees a host-side stand-in under the array's name, so the address is looked up
+// once per device with that device current and cached.
+cudaError_t static_scratch(double **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_diag_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -641,6 +674,50 @@ int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap) {
         if (by) by[k] = lbd::tile_at(k).by;
     }
     return n;
+}
+
+int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precision,
+                           const void *g, const void *phi, const void *psi, double B0, double B1,
+                           double ref_x, double ref_y, void *stream, lbd_diag *out) {
+    if (!g || !phi || !psi || !out) return LBD_EINVAL;
+    if (nx < 1 || ny < 1 || nx > (1 << 20) || ny > (1 << 20) || pitch < nx) return LBD_EINVAL;
+    if (precision != LBD_FP64 && precision != LBD_FP32) return LBD_EINVAL;
+    if (!(ref_x >= 0 && ref_x < nx && ref_y >= 0 && ref_y < ny)) return LBD_EINVAL;
+    double *scratch = nullptr;
+    if (static_scratch(&scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return LBD_ECUDA;
+    }
+    double *partial = scratch, *res = scratch + NRED * RED_BLOCKS;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long plane = (long long)pitch * ny;
+    if (precision == LBD_FP64)
+        reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
+            nx, ny, pitch, plane, (const double *)g, (const double *)phi, (const double *)psi, B0,
+            B1, ref_x, ref_y, partial);
+    else
+        reduce_partial<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
+            nx, ny, pitch, plane, (const float *)g, (const float *)phi, (const float *)psi, B0, B1,
+            ref_x, ref_y, partial);
+    if (cudaGetLastError() != cudaSuccess) return LBD_ECUDA;
+    reduce_final<<<1, RED_THREADS, 0, s>>>(RED_BLOCKS, partial, res);
+    if (cudaGetLastError() != cudaSuccess) return LBD_ECUDA;
+    double r[NRED];
+    if (cudaMemcpyAsync(r, res, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return LBD_ECUDA;
+    }
+    out->sum_rho = (double)nx * (double)ny + r[0];
+    out->sum_phi = r[1];
+    out->sum_psi = r[2];
+    out->mass_pos = r[5];
+    out->cm_x = r[5] > 0 ? ref_x + r[3] / r[5] : NAN;
+    out->cm_y = r[5] > 0 ? ref_y + r[4] / r[5] : NAN;
+    out->min_B = r[6];
+    out->min_psi = r[7];
+    out->nonfinite = (int64_t)r[8];
+    return LBD_OK;
 }
 
 int lbd_get_time(const lbd_ctx *c, int64_t *t) {

@@ -68,6 +68,10 @@ SIGNATURES = {
                                  ctypes.c_int32]),
     "lbd_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                     ctypes.POINTER(ctypes.c_int32)]),
+    "lbd_diagnostics_static": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                              ctypes.c_int32, _P, _P, _P, ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              _P, ctypes.POINTER(lbd_diag)]),
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_synchronize": (ctypes.c_int, [_P]),
