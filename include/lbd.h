@@ -137,9 +137,11 @@ int lbd_get_populations(lbd_ctx *ctx, double *f);
  * previous centre to follow a moving droplet).  Synchronises. */
 int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
 
-/* Select the tile shape (output sites per CTA) of the fused step kernel.
- * Only shapes compiled into the library are accepted (see lbd_tiles); the
- * result of a step does not depend on the tile, only its speed does. */
+/* Select the launch shape of the step.  bx <= 64: the tiled kernel with bx x by
+ * output sites per CTA; bx >= 128: the stripe-marching kernel with bx threads
+ * per CTA (bx - 10 output columns) marching down segments of by rows.  Only
+ * shapes compiled into the library are accepted (see lbd_tiles).  All shapes of
+ * one kernel give bit-identical results; the two kernels agree to rounding. */
 int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
 
 /* Tile shapes compiled into the library: writes up to cap pairs into bx[], by[]

@@ -38,7 +38,7 @@ struct lbd_ctx {
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
     uint32_t *theta = nullptr;      // source indicator, one bit per site
     int64_t t = 0;
-    Tile tile{32, 16};
+    Tile tile{128, 64};
     int sticky = 0;
     std::string msg;
 };
@@ -448,7 +448,7 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             return LBD_ECUDA;
         }
     }
-    c->tile = Tile{32, 16};
+    c->tile = Tile{128, 64};
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
         return LBD_ECUDA;

@@ -39,7 +39,10 @@ struct StepArgs {
 
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 
-// Tile shape of the fused kernel (output sites per CTA).
+// Launch shape of the step.  bx <= 64: the tiled kernel (lbd_step.cu) with
+// bx x by output sites per CTA.  bx >= 128: the stripe-marching kernel
+// (lbd_stripe.cu) with bx threads (bx - 10 output columns) and segments of by
+// rows.
 struct Tile {
     int bx, by;
 };
@@ -48,6 +51,13 @@ struct Tile {
 // (MODE_FIELDS) with tile shape `tile`; returns the launch error.
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &a, int mode, Tile tile, cudaStream_t s);
+
+// Launch one coupled step with the stripe-marching kernel (nt threads, seg rows).
+template <typename T>
+cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s);
+
+template <typename T>
+size_t stripe_smem_bytes(int nt);
 
 // Fill the source indicator bit mask (words per row = (nx + 31) / 32) for the
 // disks (x, y, R) with the exact inclusive double-precision test.

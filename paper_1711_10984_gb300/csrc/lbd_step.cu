@@ -358,7 +358,8 @@ cudaError_t launch_tile(const StepArgs<T> &a, int mode, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-constexpr Tile kTiles[] = {{32, 8}, {32, 16}, {64, 8}, {32, 32}, {64, 16}};
+constexpr Tile kTiles[] = {{32, 8},    {32, 16},   {64, 8},    {32, 32},   {64, 16},
+                           {128, 32},  {128, 64},  {128, 128}, {256, 32},  {256, 64}};
 
 }  // namespace
 
@@ -377,6 +378,7 @@ Tile tile_at(int k) { return kTiles[k]; }
 
 template <typename T>
 size_t step_smem_bytes(Tile t) {
+    if (t.bx >= 128) return stripe_smem_bytes<T>(t.bx);
     if (t.bx == 32 && t.by == 8) return smem_for<T, 32, 8>();
     if (t.bx == 32 && t.by == 16) return smem_for<T, 32, 16>();
     if (t.bx == 64 && t.by == 8) return smem_for<T, 64, 8>();
@@ -387,6 +389,10 @@ size_t step_smem_bytes(Tile t) {
 
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &a, int mode, Tile t, cudaStream_t s) {
+    if (t.bx >= 128) {
+        if (mode == MODE_STEP) return launch_stripe<T>(a, t.bx, t.by, s);
+        t = Tile{32, 16};  // the fields evaluation always uses the tiled kernel
+    }
     if (t.bx == 32 && t.by == 8) return launch_tile<T, 32, 8>(a, mode, s);
     if (t.bx == 32 && t.by == 16) return launch_tile<T, 32, 16>(a, mode, s);
     if (t.bx == 64 && t.by == 8) return launch_tile<T, 64, 8>(a, mode, s);

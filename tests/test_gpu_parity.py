@@ -52,13 +52,18 @@ def droplet(nx, ny, seed=1, R=None):
     return d, phi, psi
 
 
-def test_fp64_single_droplet_1000_steps():
+KERNELS = [(32, 16), (128, 64), (256, 32)]
+
+
+@pytest.mark.parametrize("tile", KERNELS, ids=lambda t: "%dx%d" % t)
+def test_fp64_single_droplet_1000_steps(tile):
     """128^2 droplet with source, sink and schedule on: FP64 GPU matches the
-    oracle to 1e-10 relative per field after 1000 steps."""
+    oracle to 1e-10 relative per field after 1000 steps (tiled kernel and
+    stripe-marching kernel)."""
     n = 128
     d, phi, psi = droplet(n, n, seed=1, R=20)
     src = [inputs.default_source(d, n, n)]
-    sim, ref = run_both(n, n, phi, psi, 1000, sources=src, **ACTIVE)
+    sim, ref = run_both(n, n, phi, psi, 1000, sources=src, tile=tile, **ACTIVE)
     for g, r, name in zip(sim.fields(), ref.fields(), NAMES):
         assert rel_err(g, r) <= 1e-10, name
     f = sim.populations()
@@ -75,20 +80,23 @@ def test_fp64_config1_2000_steps():
         assert rel_err(g, r) <= 1e-10, name
 
 
-@pytest.mark.parametrize("nx,ny", [(100, 37), (37, 100), (8, 8), (5, 4), (161, 23)])
-def test_fp64_ragged_and_small_grids(nx, ny):
-    """Grids that span several tiles with a ragged tail, and grids smaller than
-    one tile (the halo wraps several times)."""
+@pytest.mark.parametrize("tile", KERNELS, ids=lambda t: "%dx%d" % t)
+@pytest.mark.parametrize("nx,ny", [(100, 37), (37, 100), (8, 8), (5, 4), (161, 23), (300, 130)])
+def test_fp64_ragged_and_small_grids(nx, ny, tile):
+    """Grids that span several tiles or stripes with a ragged tail, and grids
+    smaller than one tile (the halo wraps several times)."""
     d, phi, psi = droplet(nx, ny, seed=nx * 1000 + ny, R=max(2.0, min(nx, ny) / 4))
     src = [(nx / 3, ny / 2, max(1.0, min(nx, ny) / 8))]
-    sim, ref = run_both(nx, ny, phi, psi, 150, sources=src, **dict(ACTIVE, t_on=20, A0=1e-6))
+    sim, ref = run_both(nx, ny, phi, psi, 150, sources=src, tile=tile,
+                        **dict(ACTIVE, t_on=20, A0=1e-6))
     for g, r, name in zip(sim.fields(), ref.fields(), NAMES):
         assert rel_err(g, r) <= 1e-10, name
 
 
 def test_tiles_give_identical_results():
-    """Each site's arithmetic does not depend on the tile shape: all compiled
-    tiles produce bit-identical states."""
+    """Each site's arithmetic does not depend on the launch shape: all shapes of
+    one kernel produce bit-identical states, and the tiled and stripe-marching
+    kernels (different operation order) agree to rounding."""
     nx, ny = 150, 70
     d, phi, psi = droplet(nx, ny, seed=5)
     src = [inputs.default_source(d, nx, ny)]
@@ -101,19 +109,27 @@ def test_tiles_give_identical_results():
             sim.step(60)
             outs.append((prec, t, sim.fields(), sim.populations()))
     for prec in (lbd.LBD_FP64, lbd.LBD_FP32):
-        base = [o for o in outs if o[0] == prec]
-        for o in base[1:]:
-            for a, b in zip(o[2], base[0][2]):
-                assert np.array_equal(a, b), (prec, o[1])
-            assert np.array_equal(o[3], base[0][3])
+        for fam in (lambda t: t[0] <= 64, lambda t: t[0] >= 128):
+            base = [o for o in outs if o[0] == prec and fam(o[1])]
+            for o in base[1:]:
+                for a, b in zip(o[2], base[0][2]):
+                    assert np.array_equal(a, b), (prec, o[1])
+                assert np.array_equal(o[3], base[0][3])
+        tiled = [o for o in outs if o[0] == prec and o[1][0] <= 64][0]
+        stripe = [o for o in outs if o[0] == prec and o[1][0] >= 128][0]
+        tol = 1e-12 if prec == lbd.LBD_FP64 else 1e-5
+        for a, b in zip(tiled[2], stripe[2]):
+            assert np.abs(a - b).max() <= tol * max(np.abs(a).max(), 1e-3)
 
 
-def test_fp32_shifted_populations_tolerance():
+@pytest.mark.parametrize("tile", KERNELS, ids=lambda t: "%dx%d" % t)
+def test_fp32_shifted_populations_tolerance(tile):
     """FP32 form over the 2000-step single-droplet workload: phi, psi, u within
     1e-4 absolute of the FP64 oracle, and the centroid within 0.02."""
     w = inputs.single_droplet()
     n = w["nx"]
     sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=w["sources"], **w["params"])
+    sim.set_tile(*tile)
     sim.set_fields(w["phi"], w["psi"])
     ref = oracle.State(oracle.Params(n, n, sources=w["sources"], **w["params"]), w["phi"], w["psi"])
     for _ in range(4):
