@@ -137,11 +137,13 @@ int lbd_get_populations(lbd_ctx *ctx, double *f);
  * previous centre to follow a moving droplet).  Synchronises. */
 int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
 
-/* Select the launch shape of the step.  bx <= 64: the tiled kernel with bx x by
- * output sites per CTA; bx >= 128: the stripe-marching kernel with bx threads
- * per CTA (bx - 10 output columns) marching down segments of by rows.  Only
- * shapes compiled into the library are accepted (see lbd_tiles).  All shapes of
- * one kernel give bit-identical results; the two kernels agree to rounding. */
+/* Select the launch shape of the step: bx output columns x by output rows per
+ * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
+ * column per thread, segments of by rows); bx 240: FP32 column-pair kernel
+ * with packed FP32x2 arithmetic (needs nx % 4 == 0 and nx >= 264).  Shapes not
+ * compiled in, or not valid for the context's precision and lattice, return
+ * LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
+ * kernels agree to rounding. */
 int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
 
 /* Tile shapes compiled into the library: writes up to cap pairs into bx[], by[]

@@ -38,7 +38,7 @@ struct lbd_ctx {
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
     uint32_t *theta = nullptr;      // source indicator, one bit per site
     int64_t t = 0;
-    Tile tile{128, 64};
+    Tile tile{118, 64};
     int sticky = 0;
     std::string msg;
 };
@@ -448,7 +448,7 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             return LBD_ECUDA;
         }
     }
-    c->tile = Tile{128, 64};
+    c->tile = Tile{118, 64};  // fastest measured default; lbd_autotune refines it
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
         return LBD_ECUDA;
@@ -610,14 +610,12 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
 
 int lbd_set_tile(lbd_ctx *c, int32_t bx, int32_t by) {
     if (!c) return LBD_EINVAL;
-    for (int k = 0; k < lbd::n_tiles(); ++k) {
-        const Tile t = lbd::tile_at(k);
-        if (t.bx == bx && t.by == by) {
-            c->tile = t;
-            return LBD_OK;
-        }
-    }
-    return fail(c, LBD_EINVAL, "tile %dx%d is not compiled into the library", bx, by);
+    const Tile t{bx, by};
+    if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx))
+        return fail(c, LBD_EINVAL, "launch shape %dx%d is not available for this precision and lattice",
+                    bx, by);
+    c->tile = t;
+    return LBD_OK;
 }
 
 int lbd_autotune(lbd_ctx *c, int32_t reps, int32_t *bx, int32_t *by) {
@@ -632,6 +630,7 @@ int lbd_autotune(lbd_ctx *c, int32_t reps, int32_t *bx, int32_t *by) {
     int rc = LBD_OK;
     for (int k = 0; k < lbd::n_tiles() && rc == LBD_OK; ++k) {
         const Tile t = lbd::tile_at(k);
+        if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx)) continue;
         // The trial launches read the current buffers and write the others; the
         // buffers are not swapped, so the state and t are unchanged.
         auto launch = [&]() -> cudaError_t {

@@ -39,13 +39,18 @@ struct StepArgs {
 
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 
-// Launch shape of the step.  bx <= 64: the tiled kernel (lbd_step.cu) with
-// bx x by output sites per CTA.  bx >= 128: the stripe-marching kernel
-// (lbd_stripe.cu) with bx threads (bx - 10 output columns) and segments of by
-// rows.
+// Launch shape of the step: bx output columns by by output rows per CTA.
+//   bx in {32, 64}:   tiled kernel (lbd_step.cu), bx x by tiles;
+//   bx in {118, 246}: stripe-marching kernel (lbd_stripe.cu), bx + 10 threads,
+//                     segments of by rows;
+//   bx == 240:        FP32 column-pair kernel (lbd_stripe2.cu), 128 threads,
+//                     segments of by rows (nx % 4 == 0 and nx >= 264 only).
 struct Tile {
     int bx, by;
 };
+
+// Whether a launch shape can run a step of this precision on an nx-wide lattice.
+bool tile_valid(Tile t, bool fp32, int nx);
 
 // Launch one coupled step (mode MODE_STEP) or the fields evaluation
 // (MODE_FIELDS) with tile shape `tile`; returns the launch error.
@@ -58,6 +63,11 @@ cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s)
 
 template <typename T>
 size_t stripe_smem_bytes(int nt);
+
+// FP32 column-pair stripe kernel.
+cudaError_t launch_pair(const StepArgs<float> &a, int seg, cudaStream_t s);
+bool pair_supported(int nx);
+size_t pair_smem_bytes();
 
 // Fill the source indicator bit mask (words per row = (nx + 31) / 32) for the
 // disks (x, y, R) with the exact inclusive double-precision test.

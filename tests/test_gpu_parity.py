@@ -52,7 +52,7 @@ def droplet(nx, ny, seed=1, R=None):
     return d, phi, psi
 
 
-KERNELS = [(32, 16), (128, 64), (256, 32)]
+KERNELS = [(32, 16), (118, 64), (246, 32)]   # tiled, stripe (1 column per thread)
 
 
 @pytest.mark.parametrize("tile", KERNELS, ids=lambda t: "%dx%d" % t)
@@ -93,33 +93,42 @@ def test_fp64_ragged_and_small_grids(nx, ny, tile):
         assert rel_err(g, r) <= 1e-10, name
 
 
+def family(t):
+    return "tiled" if t[0] <= 64 else ("pair" if t[0] == 240 else "stripe")
+
+
 def test_tiles_give_identical_results():
     """Each site's arithmetic does not depend on the launch shape: all shapes of
-    one kernel produce bit-identical states, and the tiled and stripe-marching
-    kernels (different operation order) agree to rounding."""
-    nx, ny = 150, 70
+    one kernel produce bit-identical states, and the kernels (different
+    operation order) agree to rounding."""
+    nx, ny = 300, 70
     d, phi, psi = droplet(nx, ny, seed=5)
     src = [inputs.default_source(d, nx, ny)]
     outs = []
     for t in lbd.tiles():
         for prec in (lbd.LBD_FP64, lbd.LBD_FP32):
+            if family(t) == "pair" and prec == lbd.LBD_FP64:
+                continue
             sim = lbd.Sim(nx, ny, precision=prec, sources=src, **dict(ACTIVE, t_on=10, A0=1e-6))
             sim.set_tile(*t)
             sim.set_fields(phi, psi)
             sim.step(60)
             outs.append((prec, t, sim.fields(), sim.populations()))
     for prec in (lbd.LBD_FP64, lbd.LBD_FP32):
-        for fam in (lambda t: t[0] <= 64, lambda t: t[0] >= 128):
-            base = [o for o in outs if o[0] == prec and fam(o[1])]
+        fams = ["tiled", "stripe"] + (["pair"] if prec == lbd.LBD_FP32 else [])
+        for fam in fams:
+            base = [o for o in outs if o[0] == prec and family(o[1]) == fam]
+            assert base, fam
             for o in base[1:]:
                 for a, b in zip(o[2], base[0][2]):
                     assert np.array_equal(a, b), (prec, o[1])
                 assert np.array_equal(o[3], base[0][3])
-        tiled = [o for o in outs if o[0] == prec and o[1][0] <= 64][0]
-        stripe = [o for o in outs if o[0] == prec and o[1][0] >= 128][0]
+        tiled = [o for o in outs if o[0] == prec and family(o[1]) == "tiled"][0]
         tol = 1e-12 if prec == lbd.LBD_FP64 else 1e-5
-        for a, b in zip(tiled[2], stripe[2]):
-            assert np.abs(a - b).max() <= tol * max(np.abs(a).max(), 1e-3)
+        for fam in fams[1:]:
+            other = [o for o in outs if o[0] == prec and family(o[1]) == fam][0]
+            for a, b in zip(tiled[2], other[2]):
+                assert np.abs(a - b).max() <= tol * max(np.abs(a).max(), 1e-3), fam
 
 
 @pytest.mark.parametrize("tile", KERNELS, ids=lambda t: "%dx%d" % t)
@@ -140,6 +149,48 @@ def test_fp32_shifted_populations_tolerance(tile):
             assert np.abs(g[k] - r[k]).max() <= 1e-4, NAMES[k]
         dg, dr = sim.diagnostics(64, 64), ref.diagnostics(64, 64)
         assert abs(dg["cm_x"] - dr["cm_x"]) <= 0.02 and abs(dg["cm_y"] - dr["cm_y"]) <= 0.02
+
+
+@pytest.mark.parametrize("tile", [(240, 64), (240, 32), (118, 64)], ids=lambda t: "%dx%d" % t)
+def test_fp32_two_droplets_512x256(tile):
+    """FP32 on the 512x256 two-droplet workload (the column-pair kernel needs
+    nx >= 264): phi, psi, u within 1e-4 of the FP64 oracle after 600 steps with
+    source and sink on, and both centroids within 0.02."""
+    w = inputs.two_droplets(sep=80.0, offset=20.0)
+    nx, ny = w["nx"], w["ny"]
+    sim = lbd.Sim(nx, ny, precision=lbd.LBD_FP32, sources=w["sources"], **w["params"])
+    sim.set_tile(*tile)
+    sim.set_fields(w["phi"], w["psi"])
+    ref = oracle.State(oracle.Params(nx, ny, sources=w["sources"], **w["params"]), w["phi"], w["psi"])
+    for _ in range(2):
+        sim.step(300)
+        ref.step(300)
+        g, r = sim.fields(), ref.fields()
+        for k in (1, 2, 3, 4):
+            assert np.abs(g[k] - r[k]).max() <= 1e-4, NAMES[k]
+        for d in w["droplets"]:
+            dg, dr = sim.diagnostics(d["x"], d["y"]), ref.diagnostics(d["x"], d["y"])
+            assert abs(dg["cm_x"] - dr["cm_x"]) <= 0.02 and abs(dg["cm_y"] - dr["cm_y"]) <= 0.02
+
+
+@pytest.mark.parametrize("nx,ny", [(268, 37), (520, 130), (264, 8)])
+def test_fp32_pair_kernel_ragged(nx, ny):
+    """Column-pair kernel on lattices at its size limits and with ragged tails."""
+    d, phi, psi = droplet(nx, ny, seed=nx + ny, R=max(2.0, min(nx, ny) / 4))
+    src = [(nx / 3, ny / 2, max(1.0, min(nx, ny) / 8))]
+    sim, ref = run_both(nx, ny, phi, psi, 200, precision=lbd.LBD_FP32, sources=src,
+                        tile=(240, 64), **dict(ACTIVE, t_on=20, A0=1e-6))
+    g, r = sim.fields(), ref.fields()
+    for k in (1, 2, 3, 4):
+        assert np.abs(g[k] - r[k]).max() <= 1e-4, NAMES[k]
+
+
+def test_pair_kernel_rejected_where_unsupported():
+    for nx, prec in [(128, lbd.LBD_FP32), (266, lbd.LBD_FP32), (512, lbd.LBD_FP64)]:
+        sim = lbd.Sim(nx, 16, precision=prec)
+        with pytest.raises(lbd.LbdError) as e:
+            sim.set_tile(240, 64)
+        assert e.value.code == lbd.LBD_EINVAL
 
 
 @pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
