@@ -1,0 +1,592 @@
+// lbd_adjoint.cu -- hand-written adjoint (reverse mode) of the coupled step of
+// arXiv 1711.10984, Sections 2.1-2.3, for the loss
+//     L = X_cm(t0 + T) - X_cm(t0),
+// X_cm the x centre of mass of the phi >= 0 region (Section 4), with respect to
+// the initial surfactant field psi(t0) and the coupling B1 of B(psi) = B0 + B1 psi.
+//
+// Forward: the step kernel advances the state, with a checkpoint every K steps.
+// Reverse: for each segment (last first) the checkpoint is restored, the K
+// states of the segment are recomputed and kept, and the step is reversed one
+// at a time.  Reversing a step recomputes its intermediates (gradients,
+// Laplacians, chemical potentials, force, pulled populations, moments,
+// advected fields) in double precision and applies the transposed operators:
+//   psi update  (Eq. 19, link form)          -> lambda psi*, lambda m*
+//   phi update  (Eq. 18)                     -> lambda mu*, lambda phi*
+//   mu*, m*     (Eq. 3 on phi*, psi*)        -> lambda phi*, lambda psi*, lambda phi^n
+//   advection   (donor cell, Eqs. 16-17)     -> lambda phi, lambda psi, lambda u
+//   collision   (Eqs. 10-13) and u (Eq. 11)  -> lambda f_i, lambda F
+//   streaming   (pull)                       -> lambda buffer (push)
+//   force       (Eq. 14)                     -> lambda phi, lambda psi, lambda mu, lambda m
+//   mu, m       (Eqs. 3, 5)                  -> lambda phi, lambda psi
+// with dL/dB1 accumulated per site.  The transposes use that the isotropic
+// gradient stencil is antisymmetric (G^T = -G) and the Laplacian symmetric.
+// The upwind choices and the phi >= 0 mask of the centroid are taken from the
+// forward state (they are piecewise constant).
+#include <cmath>
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "lbd_internal.h"
+
+namespace lbd {
+namespace {
+
+struct Nbr {
+    long long c, e, w, n, s, ne, nw, se, sw;
+};
+
+__device__ __forceinline__ Nbr nbr(long long s, int nx, int ny) {
+    const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+    const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
+    const int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
+    const long long r0 = (long long)y * nx, rm = (long long)ym * nx, rp = (long long)yp * nx;
+    return Nbr{s, r0 + xp, r0 + xm, rp + x, rm + x, rp + xp, rp + xm, rm + xp, rm + xm};
+}
+
+// isotropic D2Q9 stencils on dense arrays
+__device__ __forceinline__ double Gx(const double *A, const Nbr &q) {
+    return (A[q.e] - A[q.w]) / 3.0 + ((A[q.ne] - A[q.nw]) + (A[q.se] - A[q.sw])) / 12.0;
+}
+__device__ __forceinline__ double Gy(const double *A, const Nbr &q) {
+    return (A[q.n] - A[q.s]) / 3.0 + ((A[q.ne] - A[q.se]) + (A[q.nw] - A[q.sw])) / 12.0;
+}
+__device__ __forceinline__ double Lap(const double *A, const Nbr &q) {
+    const double c = A[q.c];
+    return (2.0 / 3.0) * ((A[q.e] - c) + (A[q.w] - c) + (A[q.n] - c) + (A[q.s] - c)) +
+           (1.0 / 6.0) * ((A[q.ne] - c) + (A[q.nw] - c) + (A[q.se] - c) + (A[q.sw] - c));
+}
+// sum_alpha G_alpha(V_alpha)
+__device__ __forceinline__ double Div(const double *Vx, const double *Vy, const Nbr &q) {
+    return Gx(Vx, q) + Gy(Vy, q);
+}
+
+#define LBD_SITES(N)                                                                   \
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (N);       \
+         s += (long long)gridDim.x * blockDim.x)
+
+// D2Q9 velocity components of direction i (order (0,0) (1,0) (0,1) (-1,0) (0,-1)
+// (1,1) (-1,1) (-1,-1) (1,-1))
+__device__ __forceinline__ int EX(int i) {
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__device__ __forceinline__ int EY(int i) {
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+__device__ __forceinline__ double wgt(int i) {
+    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Scalars of one step.
+struct AdjPar {
+    int nx, ny;
+    long long N, pitch, plane;
+    double a, b, B0, B1, M, D, omega, guo, gamma, c0, fx, fy;
+    int body;
+};
+
+// Dense double work arrays of one reversed step.
+struct Work {
+    // forward intermediates
+    double *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy, *MU, *MM;
+    double *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *FP, *RHO, *UX, *UY;
+    double *PHS, *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
+    // adjoints
+    double *Lphi, *Lpsi, *Lbuf;       // of the step output (9 planes for Lbuf)
+    double *Lphi0, *Lpsi0, *Lbuf0;    // of the step input
+    double *LMUS, *LMS, *LPHS, *LPSS, *LUX, *LUY, *LFX, *LFY, *LMU, *LMM;
+    double *T1, *T2, *T3, *T4, *T5, *T6, *T7;  // products for the transposed stencils
+    double *dB1;                                // per-site accumulator of dL/dB1
+};
+
+// ---- forward intermediates ----------------------------------------------------
+template <typename T>
+__global__ void fwd1(AdjPar p, const T *phi, const T *psi, Work w) {
+    LBD_SITES(p.N) {
+        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
+        const long long o = (long long)y * p.pitch + x;
+        w.PH[s] = (double)phi[o];
+        w.PS[s] = (double)psi[o];
+    }
+}
+
+__global__ void fwd2(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        const double px = Gx(w.PH, q), py = Gy(w.PH, q), lp = Lap(w.PH, q);
+        const double cx = Gx(w.PS, q), cy = Gy(w.PS, q);
+        const double ph = w.PH[s];
+        w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
+        w.MU[s] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * w.PS[s]) * lp -
+                  p.B1 * (px * cx + py * cy);
+        w.MM[s] = 0.5 * p.B1 * (px * px + py * py);
+    }
+}
+
+template <typename T>
+__global__ void fwd3(AdjPar p, const T *g, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
+        const double gmx = Gx(w.MU, q), gmy = Gy(w.MU, q), gnx = Gx(w.MM, q), gny = Gy(w.MM, q);
+        w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
+        const double ph = w.PH[s], c = w.PS[s];
+        double Fx = -ph * gmx - (w.GSx[s] + c * gnx);
+        double Fy = -ph * gmy - (w.GSy[s] + c * gny);
+        if (p.body) { Fx += p.fx; Fy += p.fy; }
+        w.Fx[s] = Fx; w.Fy[s] = Fy;
+        double n = 0, jx = 0, jy = 0;
+        for (int i = 0; i < 9; ++i) {
+            int xs = x - EX(i), ys = y - EY(i);
+            xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+            ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+            const double f = wgt(i) + (double)g[i * p.plane + (long long)ys * p.pitch + xs];
+            w.FP[i * p.N + s] = f;
+            n += f; jx += f * EX(i); jy += f * EY(i);
+        }
+        w.RHO[s] = n;
+        w.UX[s] = (jx + 0.5 * Fx) / n;
+        w.UY[s] = (jy + 0.5 * Fy) / n;
+    }
+}
+
+__device__ __forceinline__ double up(double u, double a, double b) { return u > 0.0 ? a : b; }
+
+__global__ void fwd4(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        const double *UX = w.UX, *UY = w.UY;
+        const double ue = 0.5 * (UX[s] + UX[q.e]), uw = 0.5 * (UX[q.w] + UX[s]);
+        const double un = 0.5 * (UY[s] + UY[q.n]), us = 0.5 * (UY[q.s] + UY[s]);
+        const double *P = w.PH, *C = w.PS;
+        const double fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
+        const double fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
+        const double ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
+        const double gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
+        w.PHS[s] = P[s] - ((fe - fw) + (fn - fs));
+        w.PSS[s] = C[s] - ((ge - gw) + (gn - gs));
+    }
+}
+
+__global__ void fwd5(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        const double px = Gx(w.PHS, q), py = Gy(w.PHS, q);
+        w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(w.PHS, q);
+        w.GRx[s] = Gx(w.PSS, q); w.GRy[s] = Gy(w.PSS, q);
+        w.MS[s] = 0.5 * p.B1 * (px * px + py * py);
+    }
+}
+
+// ---- reverse of the phi and psi updates (Eqs. 18, 19) ---------------------------
+__global__ void adj_e(AdjPar p, double gamma, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        w.LMUS[s] = p.M * Lap(w.Lphi, q);
+        const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
+        const double *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
+        double lpss = Lp[s] * (1.0 - gamma), lms = 0.0;
+        for (int k = 0; k < 8; ++k) {
+            const double lam = k < 4 ? 2.0 / 3.0 : 1.0 / 6.0;
+            const long long j = nb[k];
+            // psi'_s's own link to j, and psi'_j's link back to s
+            lpss += p.D * lam * (Lp[s] * (-1.0 + 0.5 * (m[j] - m[s])) +
+                                 Lp[j] * (1.0 + 0.5 * (m[s] - m[j])));
+            lms += p.D * lam * 0.5 * (c[s] + c[j]) * (Lp[j] - Lp[s]);
+        }
+        w.LPSS[s] = lpss;
+        w.LMS[s] = lms;
+    }
+}
+
+// products for the transposed stencils of mu*, m*; local terms; dB1
+__global__ void adj_d1(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const double lmu = w.LMUS[s], lm = w.LMS[s];
+        const double qx = w.GQx[s], qy = w.GQy[s], rx = w.GRx[s], ry = w.GRy[s];
+        w.T1[s] = (p.B0 + p.B1 * w.PSS[s]) * lmu;  // for -L(.)
+        w.T2[s] = lmu * rx; w.T3[s] = lmu * ry;    // B1 div(lambda mu* grad psi*)  -> phi*
+        w.T4[s] = lmu * qx; w.T5[s] = lmu * qy;    // B1 div(lambda mu* grad phi*)  -> psi*
+        w.T6[s] = lm * qx;  w.T7[s] = lm * qy;     // -B1 div(lambda m* grad phi*)  -> phi*
+        const double ph = w.PH[s];
+        w.Lphi0[s] = 3.0 * p.b * ph * ph * lmu;     // cubic term uses phi^n
+        w.LPSS[s] += -p.B1 * w.LQ[s] * lmu;
+        w.dB1[s] += lmu * (-w.PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
+                    lm * 0.5 * (qx * qx + qy * qy);
+    }
+}
+
+__global__ void adj_d2(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        w.LPHS[s] = w.Lphi[s] + p.a * w.LMUS[s] - Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) -
+                    p.B1 * Div(w.T6, w.T7, q);
+        w.LPSS[s] += p.B1 * Div(w.T4, w.T5, q);
+    }
+}
+
+// ---- reverse of the donor-cell advection (Eqs. 16-17) ---------------------------
+__global__ void adj_c(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        const double *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
+        const double *LP = w.LPHS, *LC = w.LPSS;
+        const double ue = 0.5 * (UX[s] + UX[q.e]), uw = 0.5 * (UX[q.w] + UX[s]);
+        const double un = 0.5 * (UY[s] + UY[q.n]), us = 0.5 * (UY[q.s] + UY[s]);
+        // adjoint of each face flux: (lambda at the right/upper site) - (left/lower)
+        const double lpe = LP[q.e] - LP[s], lpw = LP[s] - LP[q.w];
+        const double lpn = LP[q.n] - LP[s], lps = LP[s] - LP[q.s];
+        const double lce = LC[q.e] - LC[s], lcw = LC[s] - LC[q.w];
+        const double lcn = LC[q.n] - LC[s], lcs = LC[s] - LC[q.s];
+        double lphi = LP[s], lpsi = LC[s];
+        // this site is upwind of the east / north face when u_f > 0, of west / south when u_f <= 0
+        if (ue > 0) { lphi += lpe * ue; lpsi += lce * ue; }
+        if (!(uw > 0)) { lphi += lpw * uw; lpsi += lcw * uw; }
+        if (un > 0) { lphi += lpn * un; lpsi += lcn * un; }
+        if (!(us > 0)) { lphi += lps * us; lpsi += lcs * us; }
+        w.Lphi0[s] += lphi;
+        w.Lpsi0[s] = lpsi;
+        w.LUX[s] = 0.5 * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
+                          lpw * up(uw, P[q.w], P[s]) + lcw * up(uw, C[q.w], C[s]));
+        w.LUY[s] = 0.5 * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
+                          lps * up(us, P[q.s], P[s]) + lcs * up(us, C[q.s], C[s]));
+    }
+}
+
+// ---- reverse of the collision (Eqs. 10-13), moments (Eq. 11) and streaming -------
+__global__ void adj_b(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
+        const double n = w.RHO[s], ux = w.UX[s], uy = w.UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
+        const double om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
+        double ln = 0, lux = w.LUX[s], luy = w.LUY[s], lFx = 0, lFy = 0;
+        double lpost[9];
+        for (int i = 0; i < 9; ++i) {
+            const double lp = w.Lbuf[i * p.N + s];
+            lpost[i] = lp;
+            const double ex = EX(i), ey = EY(i), wi = wgt(i);
+            const double eu = ex * ux + ey * uy, eF = ex * Fx + ey * Fy;
+            ln += lp * om * wi * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+            // d feq/du and d F_i/du
+            lux += lp * (om * wi * n * (3.0 * ex + 9.0 * eu * ex - 3.0 * ux) +
+                         gk * wi * (-3.0 * Fx + 9.0 * eF * ex));
+            luy += lp * (om * wi * n * (3.0 * ey + 9.0 * eu * ey - 3.0 * uy) +
+                         gk * wi * (-3.0 * Fy + 9.0 * eF * ey));
+            lFx += lp * gk * wi * (3.0 * (ex - ux) + 9.0 * eu * ex);
+            lFy += lp * gk * wi * (3.0 * (ey - uy) + 9.0 * eu * ey);
+        }
+        // u = (j + F/2) / n
+        const double ljx = lux / n, ljy = luy / n;
+        lFx += 0.5 * lux / n;
+        lFy += 0.5 * luy / n;
+        ln += -(lux * ux + luy * uy) / n;
+        w.LFX[s] = lFx;
+        w.LFY[s] = lFy;
+        for (int i = 0; i < 9; ++i) {
+            const double lf = (1.0 - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
+            // f_i(x) was pulled from buffer_i(x - e_i)
+            int xs = x - EX(i), ys = y - EY(i);
+            xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+            ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+            w.Lbuf0[i * p.N + (long long)ys * p.nx + xs] = lf;
+        }
+    }
+}
+
+// ---- reverse of the force (Eq. 14) and of mu, m (Eqs. 3, 5) ----------------------
+__global__ void adj_a1(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const double lfx = w.LFX[s], lfy = w.LFY[s];
+        w.T1[s] = w.PH[s] * lfx; w.T2[s] = w.PH[s] * lfy;   // -> lambda mu
+        w.T3[s] = w.PS[s] * lfx; w.T4[s] = w.PS[s] * lfy;   // -> lambda m
+        w.Lphi0[s] += -(lfx * w.GMx[s] + lfy * w.GMy[s]);
+        w.Lpsi0[s] += -(lfx * w.GNx[s] + lfy * w.GNy[s]);
+    }
+}
+
+__global__ void adj_a2(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        w.LMU[s] = Div(w.T1, w.T2, q);
+        w.LMM[s] = Div(w.T3, w.T4, q);
+        w.Lpsi0[s] += Div(w.LFX, w.LFY, q);
+    }
+}
+
+__global__ void adj_a3(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const double lmu = w.LMU[s], lm = w.LMM[s];
+        const double px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
+        const double ph = w.PH[s];
+        w.T1[s] = (p.B0 + p.B1 * w.PS[s]) * lmu;
+        w.T2[s] = lmu * cx; w.T3[s] = lmu * cy;
+        w.T4[s] = lmu * px; w.T5[s] = lmu * py;
+        w.T6[s] = lm * px;  w.T7[s] = lm * py;
+        w.Lphi0[s] += (p.a + 3.0 * p.b * ph * ph) * lmu;
+        w.Lpsi0[s] += -p.B1 * w.LP[s] * lmu;
+        w.dB1[s] += lmu * (-w.PS[s] * w.LP[s] - (px * cx + py * cy)) + lm * 0.5 * (px * px + py * py);
+    }
+}
+
+__global__ void adj_a4(AdjPar p, Work w) {
+    LBD_SITES(p.N) {
+        const Nbr q = nbr(s, p.nx, p.ny);
+        w.Lphi0[s] += -Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) - p.B1 * Div(w.T6, w.T7, q);
+        w.Lpsi0[s] += p.B1 * Div(w.T4, w.T5, q);
+    }
+}
+
+// ---- loss: centroid x of the phi >= 0 region and its gradient ---------------------
+template <typename T>
+__global__ void centroid_partial(int nx, int ny, long long pitch, const T *phi, double refx,
+                                 double *partial) {
+    __shared__ double sa[256], sb[256];
+    double wx = 0, w0 = 0;
+    for (int y = blockIdx.x; y < ny; y += gridDim.x)
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) {
+            const double ph = (double)phi[(long long)y * pitch + x];
+            if (ph >= 0.0) {
+                double dx = x - refx;
+                if (dx >= 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
+                wx += ph * dx;
+                w0 += ph;
+            }
+        }
+    sa[threadIdx.x] = wx;
+    sb[threadIdx.x] = w0;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            sa[threadIdx.x] += sa[threadIdx.x + k];
+            sb[threadIdx.x] += sb[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = sa[0];
+        partial[2 * blockIdx.x + 1] = sb[0];
+    }
+}
+
+template <typename T>
+__global__ void centroid_seed(int nx, int ny, long long pitch, const T *phi, double refx,
+                              double X, double W, double *Lphi) {
+    const long long N = (long long)nx * ny;
+    LBD_SITES(N) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        const double ph = (double)phi[(long long)y * pitch + x];
+        double dx = x - refx;
+        if (dx >= 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
+        Lphi[s] = ph >= 0.0 ? (dx - (X - refx)) / W : 0.0;
+    }
+}
+
+__global__ void sum_kernel(long long n, const double *a, double *partial) {
+    __shared__ double sa[256];
+    double v = 0;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x)
+        v += a[s];
+    sa[threadIdx.x] = v;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) sa[threadIdx.x] += sa[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sa[0];
+}
+
+constexpr int RB = 256;  // reduction blocks
+
+}  // namespace
+
+// ------------------------------------------------------------------- host driver
+
+template <typename T>
+int adjoint_run(const AdjointJob<T> &job) {
+    const int nx = job.nx, ny = job.ny;
+    const long long N = (long long)nx * ny;
+    const long long plane = job.plane, pitch = job.pitch;
+    const size_t state_elems = (size_t)11 * plane;  // 9 populations + phi + psi
+    cudaStream_t st = job.stream;
+    const int nb = (int)((N + 255) / 256 < 2048 ? (N + 255) / 256 : 2048);
+    const int64_t nsteps = job.nsteps, K = job.ckpt_every;
+    const int64_t nseg = (nsteps + K - 1) / K;
+
+    // device allocations (released before returning)
+    std::vector<void *> allocs;
+    auto dalloc = [&](size_t bytes) -> void * {
+        void *ptr = nullptr;
+        if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        allocs.push_back(ptr);
+        return ptr;
+    };
+    auto release = [&]() {
+        for (void *ptr : allocs) cudaFree(ptr);
+        allocs.clear();
+    };
+    T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
+    T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
+    const int n_dense = 75;  // dense arrays carved out below
+    double *dense = (double *)dalloc(sizeof(double) * (size_t)N * n_dense);
+    double *part = (double *)dalloc(sizeof(double) * 2 * RB);
+    if (!ckpt || !seg || !dense || !part) {
+        release();
+        return LBD_ENOMEM;
+    }
+    Work w;
+    {
+        double *d = dense;
+        auto take = [&](int k) { double *r = d; d += (size_t)k * N; return r; };
+        w.PH = take(1); w.PS = take(1); w.GPx = take(1); w.GPy = take(1); w.LP = take(1);
+        w.GSx = take(1); w.GSy = take(1); w.MU = take(1); w.MM = take(1);
+        w.GMx = take(1); w.GMy = take(1); w.GNx = take(1); w.GNy = take(1);
+        w.Fx = take(1); w.Fy = take(1); w.FP = take(9); w.RHO = take(1); w.UX = take(1);
+        w.UY = take(1); w.PHS = take(1); w.PSS = take(1); w.GQx = take(1); w.GQy = take(1);
+        w.LQ = take(1); w.GRx = take(1); w.GRy = take(1); w.MS = take(1);
+        w.Lphi = take(1); w.Lpsi = take(1); w.Lbuf = take(9);
+        w.Lphi0 = take(1); w.Lpsi0 = take(1); w.Lbuf0 = take(9);
+        w.LMUS = take(1); w.LMS = take(1); w.LPHS = take(1); w.LPSS = take(1);
+        w.LUX = take(1); w.LUY = take(1); w.LFX = take(1); w.LFY = take(1);
+        w.LMU = take(1); w.LMM = take(1);
+        w.T1 = take(1); w.T2 = take(1); w.T3 = take(1); w.T4 = take(1); w.T5 = take(1);
+        w.T6 = take(1); w.T7 = take(1); w.dB1 = take(1);
+        if (d - dense != (ptrdiff_t)n_dense * N) {  // carve-out must match the allocation
+            release();
+            return LBD_EINVAL;
+        }
+    }
+#define ACK(call)                                     \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            release();                                \
+            return LBD_ECUDA;                         \
+        }                                             \
+    } while (0)
+    auto slot = [&](T *base, int64_t k) { return base + (size_t)k * state_elems; };
+    auto copy_state = [&](T *dst, const T *g, const T *phi, const T *psi) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, g, sizeof(T) * 9 * plane, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dst + 9 * plane, phi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dst + 10 * plane, psi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st);
+        return e;
+    };
+    auto step_between = [&](const T *in, T *out, int64_t t) -> cudaError_t {
+        StepArgs<T> a = job.args;
+        a.g_in = in; a.phi_in = in + 9 * plane; a.psi_in = in + 10 * plane;
+        a.g_out = out; a.phi_out = out + 9 * plane; a.psi_out = out + 10 * plane;
+        double A, gm;
+        activity_at(*job.params, t, &A, &gm);
+        a.A = (T)A;
+        a.gamma = (T)gm;
+        return launch_step<T>(a, MODE_STEP, job.tile, st);
+    };
+    auto centroid = [&](const T *phi, double *X, double *W) -> cudaError_t {
+        centroid_partial<T><<<RB, 256, 0, st>>>(nx, ny, pitch, phi, job.refx, part);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        std::vector<double> h(2 * RB);
+        e = cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * RB, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        double a = 0, b = 0;
+        for (int k = 0; k < RB; ++k) { a += h[2 * k]; b += h[2 * k + 1]; }
+        *X = job.refx + a / b;
+        *W = b;
+        return e;
+    };
+
+    // ---- forward with checkpoints ----
+    ACK(copy_state(slot(ckpt, 0), job.g0, job.phi0, job.psi0));
+    double X0, W0;
+    ACK(centroid(job.phi0, &X0, &W0));
+    for (int64_t sgi = 0; sgi < nseg; ++sgi) {
+        const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
+        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
+                       slot(ckpt, sgi) + 10 * plane));
+        for (int64_t k = k0; k < k1; ++k) {
+            const int64_t j = k - k0;
+            ACK(step_between(slot(seg, j % 2), slot(seg, (j + 1) % 2), job.t0 + k));
+        }
+        const T *endp = slot(seg, (k1 - k0) % 2);
+        ACK(copy_state(slot(ckpt, sgi + 1), endp, endp + 9 * plane, endp + 10 * plane));
+    }
+    const T *fin = slot(ckpt, nseg);
+    double XT, WT;
+    ACK(centroid(fin + 9 * plane, &XT, &WT));
+    *job.loss = XT - X0;
+    // final state back into the context
+    ACK(cudaMemcpyAsync(job.g_final, fin, sizeof(T) * 9 * plane, cudaMemcpyDeviceToDevice, st));
+    ACK(cudaMemcpyAsync(job.phi_final, fin + 9 * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st));
+    ACK(cudaMemcpyAsync(job.psi_final, fin + 10 * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st));
+
+    // ---- seed: lambda phi = dX/dphi at T, lambda psi = lambda populations = 0 ----
+    centroid_seed<T><<<nb, 256, 0, st>>>(nx, ny, pitch, fin + 9 * plane, job.refx, XT, WT, w.Lphi);
+    ACK(cudaGetLastError());
+    ACK(cudaMemsetAsync(w.Lpsi, 0, sizeof(double) * N, st));
+    ACK(cudaMemsetAsync(w.Lbuf, 0, sizeof(double) * 9 * N, st));
+    ACK(cudaMemsetAsync(w.dB1, 0, sizeof(double) * N, st));
+
+    AdjPar ap;
+    ap.nx = nx; ap.ny = ny; ap.N = N; ap.pitch = pitch; ap.plane = plane;
+    ap.a = job.a; ap.b = job.b; ap.B0 = job.B0; ap.B1 = job.B1; ap.M = job.M; ap.D = job.D;
+    ap.omega = 1.0 / job.tau; ap.guo = 1.0 - 0.5 / job.tau; ap.gamma = 0; ap.c0 = job.c0;
+    ap.fx = job.fx; ap.fy = job.fy; ap.body = job.body;
+
+    // ---- reverse, segment by segment ----
+    for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
+        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
+                       slot(ckpt, sgi) + 10 * plane));
+        for (int64_t k = k0; k < k1 - 1; ++k)
+            ACK(step_between(slot(seg, k - k0), slot(seg, k - k0 + 1), job.t0 + k));
+        for (int64_t k = k1 - 1; k >= k0; --k) {
+            const T *in = slot(seg, k - k0);
+            double A, gm;
+            activity_at(*job.params, job.t0 + k, &A, &gm);
+            fwd1<T><<<nb, 256, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
+            fwd2<<<nb, 256, 0, st>>>(ap, w);
+            fwd3<T><<<nb, 256, 0, st>>>(ap, in, w);
+            fwd4<<<nb, 256, 0, st>>>(ap, w);
+            fwd5<<<nb, 256, 0, st>>>(ap, w);
+            adj_e<<<nb, 256, 0, st>>>(ap, gm, w);
+            adj_d1<<<nb, 256, 0, st>>>(ap, w);
+            adj_d2<<<nb, 256, 0, st>>>(ap, w);
+            adj_c<<<nb, 256, 0, st>>>(ap, w);
+            adj_b<<<nb, 256, 0, st>>>(ap, w);
+            adj_a1<<<nb, 256, 0, st>>>(ap, w);
+            adj_a2<<<nb, 256, 0, st>>>(ap, w);
+            adj_a3<<<nb, 256, 0, st>>>(ap, w);
+            adj_a4<<<nb, 256, 0, st>>>(ap, w);
+            ACK(cudaGetLastError());
+            // the input adjoints become the output adjoints of the previous step
+            double *tp;
+            tp = w.Lphi; w.Lphi = w.Lphi0; w.Lphi0 = tp;
+            tp = w.Lpsi; w.Lpsi = w.Lpsi0; w.Lpsi0 = tp;
+            tp = w.Lbuf; w.Lbuf = w.Lbuf0; w.Lbuf0 = tp;
+        }
+    }
+    // dL/dpsi(t0) = lambda psi; dL/dB1 = sum of the per-site accumulator
+    if (job.dpsi_host)
+        ACK(cudaMemcpyAsync(job.dpsi_host, w.Lpsi, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    sum_kernel<<<RB, 256, 0, st>>>(N, w.dB1, part);
+    ACK(cudaGetLastError());
+    std::vector<double> h(RB);
+    ACK(cudaMemcpyAsync(h.data(), part, sizeof(double) * RB, cudaMemcpyDeviceToHost, st));
+    ACK(cudaStreamSynchronize(st));
+    double sb = 0;
+    for (int k = 0; k < RB; ++k) sb += h[k];
+    *job.dB1 = sb;
+#undef ACK
+    release();
+    return LBD_OK;
+}
+
+template int adjoint_run<float>(const AdjointJob<float> &);
+template int adjoint_run<double>(const AdjointJob<double> &);
+
+}  // namespace lbd

@@ -296,24 +296,13 @@ StepArgs<T> make_args(const lbd_ctx *c) {
     return a;
 }
 
-// Activity at step t: off before t_on, then gamma and A = min(A0 (t - t_on), A_max).
-void activity(const lbd_params &p, int64_t t, double *A, double *gamma) {
-    if (t < p.t_on) {
-        *A = 0.0;
-        *gamma = 0.0;
-        return;
-    }
-    const double a = p.A0 * (double)(t - p.t_on);
-    *A = a < p.A_max ? a : p.A_max;
-    *gamma = p.gamma;
-}
 
 template <typename T>
 int run_steps(lbd_ctx *c, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
         StepArgs<T> a = make_args<T>(c);
         double A, gm;
-        activity(c->params, c->t, &A, &gm);
+        lbd::activity_at(c->params, c->t, &A, &gm);
         a.A = (T)A;
         a.gamma = (T)gm;
         CK(c, lbd::launch_step<T>(a, lbd::MODE_STEP, c->tile, c->stream));
@@ -352,6 +341,46 @@ int ensure_staging(lbd_ctx *c) {
 int grid_for(size_t n) {
     size_t b = (n + 255) / 256;
     return (int)(b < 4096 ? (b ? b : 1) : 4096);
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+int adjoint_impl(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double refx, double *loss,
+                 double *dpsi, double *dB1) {
+    lbd::AdjointJob<T> job;
+    const lbd_params &p = c->params;
+    job.nx = c->grid.nx;
+    job.ny = c->grid.ny;
+    job.pitch = c->pitch;
+    job.plane = c->plane;
+    job.args = make_args<T>(c);
+    job.tile = c->tile;
+    job.stream = c->stream;
+    job.params = &c->params;
+    job.g0 = (const T *)c->g[c->cur];
+    job.phi0 = (const T *)c->phi[c->cur];
+    job.psi0 = (const T *)c->psi[c->cur];
+    job.g_final = (T *)c->g[c->cur];
+    job.phi_final = (T *)c->phi[c->cur];
+    job.psi_final = (T *)c->psi[c->cur];
+    job.t0 = c->t;
+    job.nsteps = nsteps;
+    job.ckpt_every = ckpt_every;
+    job.refx = refx;
+    job.a = p.a; job.b = p.b; job.B0 = p.B0; job.B1 = p.B1; job.M = p.M; job.D = p.D;
+    job.tau = p.tau; job.c0 = p.c0; job.fx = p.fx; job.fy = p.fy;
+    job.body = (p.flags & LBD_BODY_FORCE) ? 1 : 0;
+    job.loss = loss;
+    job.dB1 = dB1;
+    job.dpsi_host = dpsi;
+    const int rc = lbd::adjoint_run<T>(job);
+    if (rc == LBD_ECUDA) return fail(c, LBD_ECUDA, "adjoint: %s", cudaGetErrorString(cudaGetLastError()));
+    if (rc == LBD_ENOMEM) return fail(c, LBD_ENOMEM, "adjoint: device allocation failed");
+    if (rc == LBD_OK) c->t += nsteps;
+    return rc;
 }
 
 }  // namespace
@@ -717,6 +746,21 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
     out->min_psi = r[7];
     out->nonfinite = (int64_t)r[8];
     return LBD_OK;
+}
+
+int lbd_adjoint(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double ref_x, double *loss,
+                double *dL_dpsi0, double *dL_dB1) {
+    if (!c || !loss || !dL_dB1) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (nsteps < 1 || ckpt_every < 1) return fail(c, LBD_EINVAL, "nsteps and ckpt_every must be >= 1");
+    if (!(ref_x >= 0 && ref_x < c->grid.nx)) return fail(c, LBD_EINVAL, "ref_x outside the lattice");
+    if (c->params.flags & LBD_FROZEN_U)
+        return fail(c, LBD_EINVAL, "the adjoint is defined for the coupled velocity only");
+    CK(c, cudaSetDevice(c->dev));
+    const int64_t K = ckpt_every < nsteps ? ckpt_every : nsteps;
+    return c->params.precision == LBD_FP64
+               ? adjoint_impl<double>(c, nsteps, (int32_t)K, ref_x, loss, dL_dpsi0, dL_dB1)
+               : adjoint_impl<float>(c, nsteps, (int32_t)K, ref_x, loss, dL_dpsi0, dL_dB1);
 }
 
 int lbd_get_time(const lbd_ctx *c, int64_t *t) {

@@ -74,6 +74,42 @@ size_t pair_smem_bytes();
 cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, uint32_t *mask,
                               cudaStream_t s);
 
+// Activity at step t (Section 4): off before t_on, then the sink rate gamma and
+// the source strength A(t) = min(A0 (t - t_on), A_max).
+inline void activity_at(const lbd_params &p, int64_t t, double *A, double *gamma) {
+    if (t < p.t_on) {
+        *A = 0.0;
+        *gamma = 0.0;
+        return;
+    }
+    const double a = p.A0 * (double)(t - p.t_on);
+    *A = a < p.A_max ? a : p.A_max;
+    *gamma = p.gamma;
+}
+
+// One adjoint computation (lbd_adjoint): the state at t0 is read from g0, phi0,
+// psi0; the state at t0 + nsteps is written to the *_final buffers (which may
+// alias the inputs).
+template <typename T>
+struct AdjointJob {
+    int nx, ny;
+    long long pitch, plane;
+    StepArgs<T> args;  // model arguments of the step kernel; buffers are replaced
+    Tile tile;
+    cudaStream_t stream;
+    const lbd_params *params;
+    const T *g0, *phi0, *psi0;
+    T *g_final, *phi_final, *psi_final;
+    int64_t t0, nsteps, ckpt_every;
+    double refx;
+    double a, b, B0, B1, M, D, tau, c0, fx, fy;
+    int body;
+    double *loss, *dB1, *dpsi_host;
+};
+
+template <typename T>
+int adjoint_run(const AdjointJob<T> &job);
+
 // Shared memory bytes the fused kernel needs for a tile shape.
 template <typename T>
 size_t step_smem_bytes(Tile tile);

@@ -72,6 +72,8 @@ SIGNATURES = {
                                               ctypes.c_int32, _P, _P, _P, ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               _P, ctypes.POINTER(lbd_diag)]),
+    "lbd_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                   _dp, _dp, _dp]),
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_synchronize": (ctypes.c_int, [_P]),
@@ -206,6 +208,17 @@ class Sim:
         bx, by = ctypes.c_int32(), ctypes.c_int32()
         self._check(load().lbd_autotune(self._h, int(reps), ctypes.byref(bx), ctypes.byref(by)))
         return bx.value, by.value
+
+    def adjoint(self, nsteps, ckpt_every, refx, want_dpsi=True):
+        """Run nsteps from the current state; return (L, dL/dpsi0 or None, dL/dB1)
+        for L = X_cm(end) - X_cm(start) (see lbd_adjoint)."""
+        loss, dB1 = ctypes.c_double(), ctypes.c_double()
+        dpsi = np.empty(self.N) if want_dpsi else None
+        self._check(load().lbd_adjoint(self._h, int(nsteps), int(ckpt_every), float(refx),
+                                       ctypes.byref(loss),
+                                       dpsi.ctypes.data_as(_dp) if want_dpsi else None,
+                                       ctypes.byref(dB1)))
+        return loss.value, (dpsi.reshape(self.ny, self.nx) if want_dpsi else None), dB1.value
 
     def synchronize(self):
         self._check(load().lbd_synchronize(self._h))
