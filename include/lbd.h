@@ -205,6 +205,39 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
                            const void *g, const void *phi, const void *psi, double B0, double B1,
                            double ref_x, double ref_y, void *stream, lbd_diag *out);
 
+/* ---- batches of independent instances ------------------------------------
+ * A batch holds n independent lattices (each with its own size and
+ * parameters, all of one precision) whose steps run together: every step is
+ * one persistent launch of the stripe-marching kernel over a work list of
+ * (instance, stripe, row segment) items, and lbd_batch_step replays chunks of
+ * 100 such launches from a captured CUDA graph (the activity schedule is
+ * evaluated on the device from a device-side step count).  Instance k behaves
+ * exactly like a context of its own: same state layout, same results. */
+typedef struct lbd_batch lbd_batch;
+
+/* grids[k], params[k]: as for lbd_create (params[k].precision must agree).
+ * stream NULL: the batch creates and owns a non-blocking stream (graph capture
+ * needs a stream other than the legacy default stream). */
+int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params, void *stream,
+                     lbd_batch **out);
+const char *lbd_batch_last_error(const lbd_batch *b);
+/* as lbd_set_fields / lbd_get_fields / lbd_diagnostics for instance k */
+int lbd_batch_set_fields(lbd_batch *b, int32_t k, const double *rho, const double *ux,
+                         const double *uy, const double *phi, const double *psi);
+int lbd_batch_get_fields(lbd_batch *b, int32_t k, double *rho, double *ux, double *uy,
+                         double *phi, double *psi);
+int lbd_batch_diagnostics(lbd_batch *b, int32_t k, double ref_x, double ref_y, lbd_diag *out);
+/* Advance every instance by nsteps (asynchronous on the batch stream). */
+int lbd_batch_step(lbd_batch *b, int64_t nsteps);
+/* Launch shape of the batched kernel: bx 118 or 246, by 32, 64 or 128. */
+int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by);
+/* Time the batched launch for each shape (reps launches each, no state change)
+ * and keep the fastest; returns it in *bx, *by (may be NULL). */
+int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by);
+int lbd_batch_synchronize(lbd_batch *b);
+int lbd_batch_get_time(const lbd_batch *b, int64_t *t);
+void lbd_batch_destroy(lbd_batch *b);
+
 /* Current step count t. */
 int lbd_get_time(const lbd_ctx *ctx, int64_t *t);
 

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -43,7 +44,48 @@ struct lbd_ctx {
     std::string msg;
 };
 
+
+struct lbd_batch {
+    int n = 0;
+    std::vector<lbd_ctx *> ctx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int prec = LBD_FP32;
+    void *args_dev[2] = {nullptr, nullptr};  // StepArgs<T>[n] for buffer parity 0 / 1
+    lbd::BatchItem *items_dev = nullptr;
+    int n_items = 0;
+    long long *t_dev = nullptr;
+    Tile tile{118, 64};
+    int ctas = 1;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_steps = 100;
+    int64_t t = 0;
+    int sticky = 0;
+    std::string msg;
+};
+
 namespace {
+
+int bfail(lbd_batch *b, int code, const char *fmt, ...) {
+    if (b) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        b->msg = buf;
+        if (code == LBD_ECUDA) b->sticky = LBD_ECUDA;
+    }
+    return code;
+}
+
+#define BCK(b, call)                                                                      \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bfail(b, LBD_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                         __FILE__, __LINE__);                                             \
+    } while (0)
 
 int fail(lbd_ctx *c, int code, const char *fmt, ...) {
     if (c) {
@@ -263,20 +305,25 @@ int check_params(lbd_ctx *c, const lbd_grid *gr, const lbd_params *p) {
 }
 
 template <typename T>
-StepArgs<T> make_args(const lbd_ctx *c) {
+StepArgs<T> make_args(const lbd_ctx *c, int cur = -1) {
     StepArgs<T> a;
     memset(&a, 0, sizeof a);
     const lbd_params &p = c->params;
+    if (cur < 0) cur = c->cur;
     a.nx = c->grid.nx;
     a.ny = c->grid.ny;
     a.pitch = c->pitch;
     a.plane = c->plane;
-    a.g_in = (const T *)c->g[c->cur];
-    a.g_out = (T *)c->g[1 - c->cur];
-    a.phi_in = (const T *)c->phi[c->cur];
-    a.psi_in = (const T *)c->psi[c->cur];
-    a.phi_out = (T *)c->phi[1 - c->cur];
-    a.psi_out = (T *)c->psi[1 - c->cur];
+    a.g_in = (const T *)c->g[cur];
+    a.g_out = (T *)c->g[1 - cur];
+    a.phi_in = (const T *)c->phi[cur];
+    a.psi_in = (const T *)c->psi[cur];
+    a.phi_out = (T *)c->phi[1 - cur];
+    a.psi_out = (T *)c->psi[1 - cur];
+    a.A0 = p.A0;
+    a.A_max = p.A_max;
+    a.t_on = p.t_on;
+    a.gamma_on = p.gamma;
     a.a = (T)p.a;
     a.b = (T)p.b;
     a.B0 = (T)p.B0;
@@ -383,6 +430,100 @@ int adjoint_impl(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double refx, do
     return rc;
 }
 
+
+// ---------------------------------------------------------------- batches
+
+void batch_drop_graphs(lbd_batch *b) {
+    for (int p = 0; p < 2; ++p)
+        if (b->graph[p]) {
+            cudaGraphExecDestroy(b->graph[p]);
+            b->graph[p] = nullptr;
+        }
+}
+
+// Device tables of step arguments (one per buffer parity) and the work list of
+// the current launch shape.
+template <typename T>
+int batch_build(lbd_batch *b) {
+    const size_t bytes = sizeof(StepArgs<T>) * (size_t)b->n;
+    std::vector<StepArgs<T>> host(b->n);
+    for (int p = 0; p < 2; ++p) {
+        if (!b->args_dev[p]) BCK(b, cudaMalloc(&b->args_dev[p], bytes));
+        for (int k = 0; k < b->n; ++k) host[k] = make_args<T>(b->ctx[k], p);
+        BCK(b, cudaMemcpyAsync(b->args_dev[p], host.data(), bytes, cudaMemcpyHostToDevice, b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+    }
+    const int bxo = b->tile.bx, seg = b->tile.by;
+    std::vector<lbd::BatchItem> items;
+    for (int k = 0; k < b->n; ++k) {
+        const int nx = b->ctx[k]->grid.nx, ny = b->ctx[k]->grid.ny;
+        for (int y0 = 0; y0 < ny; y0 += seg)
+            for (int x0 = 0; x0 < nx; x0 += bxo)
+                items.push_back(lbd::BatchItem{k, x0, y0, seg});
+    }
+    // largest lattices first, so that the tail of the persistent walk is short
+    std::stable_sort(items.begin(), items.end(), [&](const lbd::BatchItem &u, const lbd::BatchItem &v) {
+        return b->ctx[u.k]->N > b->ctx[v.k]->N;
+    });
+    if (b->items_dev) cudaFree(b->items_dev);
+    b->items_dev = nullptr;
+    BCK(b, cudaMalloc(&b->items_dev, sizeof(lbd::BatchItem) * items.size()));
+    BCK(b, cudaMemcpyAsync(b->items_dev, items.data(), sizeof(lbd::BatchItem) * items.size(),
+                           cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->n_items = (int)items.size();
+    int sms = 0;
+    BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
+    const int per_sm = lbd::stripe_batch_ctas_per_sm<T>(bxo + 10);
+    b->ctas = std::min(b->n_items, sms * per_sm);
+    batch_drop_graphs(b);
+    return LBD_OK;
+}
+
+template <typename T>
+cudaError_t batch_launch(lbd_batch *b, int parity, int t_off) {
+    return lbd::launch_stripe_batch<T>((const StepArgs<T> *)b->args_dev[parity], b->items_dev,
+                                       b->n_items, b->tile.bx + 10, b->ctas, b->t_dev, t_off,
+                                       b->stream);
+}
+
+template <typename T>
+int batch_run(lbd_batch *b, int64_t nsteps) {
+    BCK(b, lbd::launch_time_set(b->t_dev, (long long)b->t, b->stream));
+    int parity = b->ctx[0]->cur;
+    int64_t done = 0;
+    const int G = b->graph_steps;  // even, so a replay returns to the same parity
+    while (nsteps - done >= G) {
+        if (!b->graph[parity]) {
+            cudaGraph_t g = nullptr;
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int j = 0; j < G && e == cudaSuccess; ++j)
+                e = batch_launch<T>(b, (parity + j) & 1, j);
+            if (e == cudaSuccess) e = lbd::launch_time_advance(b->t_dev, G, b->stream);
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return bfail(b, LBD_ECUDA, "graph capture: %s",
+                             cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            e = cudaGraphInstantiate(&b->graph[parity], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return bfail(b, LBD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+        }
+        BCK(b, cudaGraphLaunch(b->graph[parity], b->stream));
+        done += G;
+    }
+    const int64_t r = nsteps - done;
+    for (int64_t j = 0; j < r; ++j) BCK(b, batch_launch<T>(b, (int)((parity + j) & 1), (int)j));
+    if (r) BCK(b, lbd::launch_time_advance(b->t_dev, r, b->stream));
+    for (lbd_ctx *c : b->ctx) {
+        if (nsteps & 1) c->cur = 1 - c->cur;
+        c->t += nsteps;
+    }
+    b->t += nsteps;
+    return LBD_OK;
+}
 }  // namespace
 
 // ====================================================================== C ABI
@@ -761,6 +902,159 @@ int lbd_adjoint(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double ref_x, do
     return c->params.precision == LBD_FP64
                ? adjoint_impl<double>(c, nsteps, (int32_t)K, ref_x, loss, dL_dpsi0, dL_dB1)
                : adjoint_impl<float>(c, nsteps, (int32_t)K, ref_x, loss, dL_dpsi0, dL_dB1);
+}
+
+
+void lbd_batch_destroy(lbd_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (lbd_ctx *c : b->ctx) lbd_destroy(c);
+    cudaFree(b->args_dev[0]);
+    cudaFree(b->args_dev[1]);
+    cudaFree(b->items_dev);
+    cudaFree(b->t_dev);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params, void *stream,
+                     lbd_batch **out) {
+    if (!out || !grids || !params || n < 1) return LBD_EINVAL;
+    *out = nullptr;
+    for (int k = 0; k < n; ++k)
+        if (params[k].precision != params[0].precision) return LBD_EINVAL;
+    lbd_batch *b = new (std::nothrow) lbd_batch();
+    if (!b) return LBD_ENOMEM;
+    b->n = n;
+    b->prec = params[0].precision;
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            delete b;
+            return LBD_ECUDA;
+        }
+        b->own_stream = true;
+    }
+    for (int k = 0; k < n; ++k) {
+        lbd_ctx *c = nullptr;
+        const int rc = lbd_create(&grids[k], &params[k], b->stream, &c);
+        if (rc != LBD_OK) {
+            lbd_batch_destroy(b);
+            return rc;
+        }
+        b->ctx.push_back(c);
+    }
+    if (cudaMalloc(&b->t_dev, sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        lbd_batch_destroy(b);
+        return LBD_ENOMEM;
+    }
+    const int rc = b->prec == LBD_FP64 ? batch_build<double>(b) : batch_build<float>(b);
+    if (rc != LBD_OK) {
+        lbd_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBD_OK;
+}
+
+const char *lbd_batch_last_error(const lbd_batch *b) { return b ? b->msg.c_str() : ""; }
+
+int lbd_batch_set_fields(lbd_batch *b, int32_t k, const double *rho, const double *ux,
+                         const double *uy, const double *phi, const double *psi) {
+    if (!b || k < 0 || k >= b->n) return LBD_EINVAL;
+    const int rc = lbd_set_fields(b->ctx[k], rho, ux, uy, phi, psi);
+    if (rc != LBD_OK) bfail(b, rc, "instance %d: %s", k, b->ctx[k]->msg.c_str());
+    return rc;
+}
+
+int lbd_batch_get_fields(lbd_batch *b, int32_t k, double *rho, double *ux, double *uy,
+                         double *phi, double *psi) {
+    if (!b || k < 0 || k >= b->n) return LBD_EINVAL;
+    return lbd_get_fields(b->ctx[k], rho, ux, uy, phi, psi);
+}
+
+int lbd_batch_diagnostics(lbd_batch *b, int32_t k, double ref_x, double ref_y, lbd_diag *out) {
+    if (!b || k < 0 || k >= b->n) return LBD_EINVAL;
+    return lbd_diagnostics(b->ctx[k], ref_x, ref_y, out);
+}
+
+int lbd_batch_step(lbd_batch *b, int64_t nsteps) {
+    if (!b || nsteps < 0) return LBD_EINVAL;
+    if (b->sticky) return b->sticky;
+    if (nsteps == 0) return LBD_OK;
+    BCK(b, cudaSetDevice(b->ctx[0]->dev));
+    return b->prec == LBD_FP64 ? batch_run<double>(b, nsteps) : batch_run<float>(b, nsteps);
+}
+
+int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by) {
+    if (!b) return LBD_EINVAL;
+    if (!((bx == 118 || bx == 246) && (by == 32 || by == 64 || by == 128)))
+        return bfail(b, LBD_EINVAL, "batched steps use the stripe kernel: bx 118 or 246, by 32, 64 or 128");
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->tile = Tile{bx, by};
+    return b->prec == LBD_FP64 ? batch_build<double>(b) : batch_build<float>(b);
+}
+
+int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by) {
+    if (!b || reps < 1) return LBD_EINVAL;
+    if (b->sticky) return b->sticky;
+    const Tile cand[] = {{118, 32}, {118, 64}, {118, 128}, {246, 32}, {246, 64}};
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    Tile keep = b->tile;
+    int rc = LBD_OK;
+    for (const Tile &t : cand) {
+        rc = lbd_batch_set_tile(b, t.bx, t.by);
+        if (rc != LBD_OK) break;
+        // trial launches read the current buffers and write the others: no state change
+        const int parity = b->ctx[0]->cur;
+        cudaError_t e = cudaSuccess;
+        e = lbd::launch_time_set(b->t_dev, (long long)b->t, b->stream);
+        auto go = [&]() {
+            return b->prec == LBD_FP64 ? batch_launch<double>(b, parity, 0)
+                                       : batch_launch<float>(b, parity, 0);
+        };
+        if (e == cudaSuccess) e = go();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        for (int r = 0; r < reps && e == cudaSuccess; ++r) e = go();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            rc = bfail(b, LBD_ECUDA, "batch autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            keep = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != LBD_OK) return rc;
+    rc = lbd_batch_set_tile(b, keep.bx, keep.by);
+    if (bx) *bx = keep.bx;
+    if (by) *by = keep.by;
+    return rc;
+}
+
+int lbd_batch_synchronize(lbd_batch *b) {
+    if (!b) return LBD_EINVAL;
+    if (b->sticky) return b->sticky;
+    BCK(b, cudaStreamSynchronize(b->stream));
+    return LBD_OK;
+}
+
+int lbd_batch_get_time(const lbd_batch *b, int64_t *t) {
+    if (!b || !t) return LBD_EINVAL;
+    *t = b->t;
+    return LBD_OK;
 }
 
 int lbd_get_time(const lbd_ctx *c, int64_t *t) {

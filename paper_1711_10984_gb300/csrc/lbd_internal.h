@@ -35,6 +35,17 @@ struct StepArgs {
     // nullptr when there is no source.
     const uint32_t *theta;
     int theta_words;
+    // Activity schedule, used by the batched kernel, which reads the step count
+    // from device memory: A(t) = min(A0 (t - t_on), A_max), gamma(t) = gamma_on
+    // for t >= t_on, both 0 before.
+    double A0, A_max;
+    long long t_on;
+    double gamma_on;
+};
+
+// Work item of the batched step: instance, first output column, first row, rows.
+struct BatchItem {
+    int k, x0, y0, rows;
 };
 
 enum { MODE_STEP = 0, MODE_FIELDS = 1 };
@@ -63,6 +74,22 @@ cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s)
 
 template <typename T>
 size_t stripe_smem_bytes(int nt);
+
+// One step of every instance of a batch: a persistent grid of ctas CTAs walks
+// the work list; instance k reads its arguments from args[k]; the step count of
+// this launch is *t_dev + t_off.
+template <typename T>
+cudaError_t launch_stripe_batch(const StepArgs<T> *args, const BatchItem *items, int n_items,
+                                int nt, int ctas, const long long *t_dev, int t_off,
+                                cudaStream_t s);
+
+// Resident CTAs per SM of the batched kernel (occupancy calculator).
+template <typename T>
+int stripe_batch_ctas_per_sm(int nt);
+
+// t_dev += add (one thread)
+cudaError_t launch_time_advance(long long *t_dev, long long add, cudaStream_t s);
+cudaError_t launch_time_set(long long *t_dev, long long value, cudaStream_t s);
 
 // FP32 column-pair stripe kernel.
 cudaError_t launch_pair(const StepArgs<float> &a, int seg, cudaStream_t s);

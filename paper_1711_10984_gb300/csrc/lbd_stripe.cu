@@ -108,10 +108,9 @@ struct StripeOcc {
 };
 
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
-    stripe_kernel(const StepArgs<T> p, const int seg) {
-    constexpr int BXO = NT - 10;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, const int y0,
+                                            const int seg, const T A_t, const T gamma_t,
+                                            unsigned char *smem_raw) {
     T *s_phi = reinterpret_cast<T *>(smem_raw);  // [LD][NT]
     T *s_psi = s_phi + LD * NT;                   // [LD][NT]
     T *s_mu = s_psi + LD * NT;                    // [RD][NT]  mu_phi      (A -> B)
@@ -127,8 +126,6 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
     const int c = threadIdx.x;
     const int nx = p.nx, ny = p.ny;
     const long long pitch = p.pitch, plane = p.plane;
-    const int x0 = blockIdx.x * BXO;
-    const int y0 = blockIdx.y * seg;
     const int xg = wrapi(x0 - 5 + c, nx);
     const int xm = xg == 0 ? nx - 1 : xg - 1;
     const int xp = xg == nx - 1 ? 0 : xg + 1;
@@ -221,9 +218,9 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
                     if (p.theta) {
                         const int gx = x0 + c - 5;
                         const uint32_t w = p.theta[(long long)r * p.theta_words + (gx >> 5)];
-                        if ((w >> (gx & 31)) & 1u) src = p.A;
+                        if ((w >> (gx & 31)) & 1u) src = A_t;
                     }
-                    const T psi_new = psc + (p.D * div - p.gamma * (psc - p.c0) + src);
+                    const T psi_new = psc + (p.D * div - gamma_t * (psc - p.c0) + src);
                     const long long o = (long long)r * pitch + (x0 + c - 5);
                     p.phi_out[o] = phi_new;
                     p.psi_out[o] = psi_new;
@@ -363,6 +360,46 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
+    stripe_kernel(const StepArgs<T> p, const int seg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    stripe_body<T, NT>(p, blockIdx.x * (NT - 10), blockIdx.y * seg, seg, p.A, p.gamma, smem_raw);
+}
+
+// Batched step: CTAs walk the work list; the arguments of the item's instance
+// are staged in shared memory and the activity is evaluated from the device
+// step count (so that the launch can be replayed from a CUDA graph).
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
+    stripe_batch_kernel(const StepArgs<T> *args, const BatchItem *items, const int n_items,
+                        const long long *t_dev, const int t_off) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ StepArgs<T> sp;
+    __shared__ T s_A, s_gamma;
+    const long long t = *t_dev + t_off;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        if (threadIdx.x == 0) {
+            sp = args[item.k];
+            double A = 0.0, g = 0.0;
+            if (t >= sp.t_on) {
+                A = sp.A0 * (double)(t - sp.t_on);
+                A = A < sp.A_max ? A : sp.A_max;
+                g = sp.gamma_on;
+            }
+            s_A = (T)A;
+            s_gamma = (T)g;
+        }
+        __syncthreads();
+        stripe_body<T, NT>(sp, item.x0, item.y0, item.rows, s_A, s_gamma, smem_raw);
+        __syncthreads();
+    }
+}
+
+__global__ void time_advance_kernel(long long *t, long long add) { *t += add; }
+__global__ void time_set_kernel(long long *t, long long v) { *t = v; }
+
 }  // namespace
 
 template <typename T>
@@ -397,6 +434,65 @@ cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s)
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_stripe_batch(const StepArgs<T> *args, const BatchItem *items, int n_items,
+                                int nt, int ctas, const long long *t_dev, int t_off,
+                                cudaStream_t s) {
+    const size_t smem = stripe_smem_bytes<T>(nt);
+    static unsigned long long configured[2] = {0, 0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int which = nt == 128 ? 0 : 1;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured[which] & bit)) {
+        e = nt == 128
+                ? cudaFuncSetAttribute(stripe_batch_kernel<T, 128>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                : cudaFuncSetAttribute(stripe_batch_kernel<T, 256>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured[which] |= bit;
+    }
+    if (nt == 128)
+        stripe_batch_kernel<T, 128><<<ctas, 128, smem, s>>>(args, items, n_items, t_dev, t_off);
+    else if (nt == 256)
+        stripe_batch_kernel<T, 256><<<ctas, 256, smem, s>>>(args, items, n_items, t_dev, t_off);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+template <typename T>
+int stripe_batch_ctas_per_sm(int nt) {
+    int n = 0;
+    const size_t smem = stripe_smem_bytes<T>(nt);
+    cudaError_t e = nt == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, stripe_batch_kernel<T, 128>, 128, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                                    &n, stripe_batch_kernel<T, 256>, 256, smem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
+}
+template int stripe_batch_ctas_per_sm<float>(int);
+template int stripe_batch_ctas_per_sm<double>(int);
+
+cudaError_t launch_time_advance(long long *t_dev, long long add, cudaStream_t s) {
+    time_advance_kernel<<<1, 1, 0, s>>>(t_dev, add);
+    return cudaGetLastError();
+}
+cudaError_t launch_time_set(long long *t_dev, long long value, cudaStream_t s) {
+    time_set_kernel<<<1, 1, 0, s>>>(t_dev, value);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_stripe_batch<float>(const StepArgs<float> *, const BatchItem *, int,
+                                                int, int, const long long *, int, cudaStream_t);
+template cudaError_t launch_stripe_batch<double>(const StepArgs<double> *, const BatchItem *, int,
+                                                 int, int, const long long *, int, cudaStream_t);
 template cudaError_t launch_stripe<float>(const StepArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_stripe<double>(const StepArgs<double> &, int, int, cudaStream_t);
 template size_t stripe_smem_bytes<float>(int);

@@ -164,3 +164,25 @@ def emulsion(n=2048, count=64, R=25.0, seed=5):
     phi, psi = droplet_fields(n, n, drops, seed=seed)
     params = dict(PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
     return dict(nx=n, ny=n, phi=phi, psi=psi, params=params, sources=srcs, droplets=drops)
+
+
+def batch_sweep(count=256, seed=3, side_lo=128, side_hi=384):
+    """Independent single-droplet instances: square lattices with sides uniform in
+    [side_lo, side_hi], radii uniform in [15, 40] (at most a quarter of the side),
+    |B1| log-uniform in [0.01, 0.05] (B1 < 0) and the psi asymmetry amplitude
+    log-uniform in [1e-3, 2e-2]; source and sink on from step 0."""
+    out = []
+    for k in range(count):
+        u = uniform01(seed * 1000003 + k, 6)
+        n = int(side_lo + (side_hi - side_lo + 1) * u[0]) // 4 * 4
+        n = max(side_lo, min(side_hi, n))
+        R = min(15.0 + 25.0 * float(u[1]), n / 4.0)
+        B1 = -math.exp(math.log(0.01) + (math.log(0.05) - math.log(0.01)) * float(u[2]))
+        amp = math.exp(math.log(1e-3) + (math.log(2e-2) - math.log(1e-3)) * float(u[3]))
+        d = dict(x=n / 2 + float(u[4]) - 0.5, y=n / 2 + float(u[5]) - 0.5, R=R, psi_mean=0.1,
+                 noise=amp / 2, gx=amp)
+        phi, psi = droplet_fields(n, n, [d], B1=B1, seed=seed * 7919 + k)
+        params = dict(PAPER, B1=B1, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+        out.append(dict(nx=n, ny=n, phi=phi, psi=psi, params=params,
+                        sources=[default_source(d, n, n)], droplets=[d]))
+    return out

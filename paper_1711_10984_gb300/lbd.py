@@ -74,6 +74,20 @@ SIGNATURES = {
                                               _P, ctypes.POINTER(lbd_diag)]),
     "lbd_adjoint": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                                    _dp, _dp, _dp]),
+    "lbd_batch_create": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(lbd_grid),
+                                        ctypes.POINTER(lbd_params), _P, ctypes.POINTER(_P)]),
+    "lbd_batch_last_error": (ctypes.c_char_p, [_P]),
+    "lbd_batch_set_fields": (ctypes.c_int, [_P, ctypes.c_int32, _dp, _dp, _dp, _dp, _dp]),
+    "lbd_batch_get_fields": (ctypes.c_int, [_P, ctypes.c_int32, _dp, _dp, _dp, _dp, _dp]),
+    "lbd_batch_diagnostics": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                             ctypes.POINTER(lbd_diag)]),
+    "lbd_batch_step": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lbd_batch_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
+    "lbd_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "lbd_batch_synchronize": (ctypes.c_int, [_P]),
+    "lbd_batch_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lbd_batch_destroy": (None, [_P]),
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_synchronize": (ctypes.c_int, [_P]),
@@ -226,6 +240,75 @@ class Sim:
     def close(self):
         if self._h:
             load().lbd_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent instances (own lattice and parameters each) stepped together
+    by one persistent launch per step, replayed from CUDA graphs."""
+
+    def __init__(self, grids, params, stream=None):
+        self.n = len(grids)
+        self.grids = [(int(nx), int(ny)) for nx, ny in grids]
+        g = (lbd_grid * self.n)(*[lbd_grid(nx, ny) for nx, ny in self.grids])
+        p = (lbd_params * self.n)(*params)
+        self._h = _P()
+        rc = load().lbd_batch_create(self.n, g, p, ctypes.c_void_p(stream or 0),
+                                     ctypes.byref(self._h))
+        if rc != LBD_OK:
+            raise LbdError(rc, "lbd_batch_create failed")
+
+    def _check(self, rc):
+        if rc != LBD_OK:
+            raise LbdError(rc, load().lbd_batch_last_error(self._h).decode())
+
+    def set_fields(self, k, phi, psi, rho=None, ux=None, uy=None):
+        N = self.grids[k][0] * self.grids[k][1]
+        arrs = [_arr(a, N) for a in (rho, ux, uy, phi, psi)]
+        self._check(load().lbd_batch_set_fields(self._h, int(k), *[q for _, q in arrs]))
+
+    def fields(self, k):
+        nx, ny = self.grids[k]
+        out = [np.empty(nx * ny) for _ in range(5)]
+        self._check(load().lbd_batch_get_fields(self._h, int(k), *[o.ctypes.data_as(_dp) for o in out]))
+        return tuple(o.reshape(ny, nx) for o in out)
+
+    def diagnostics(self, k, refx, refy):
+        d = lbd_diag()
+        self._check(load().lbd_batch_diagnostics(self._h, int(k), float(refx), float(refy),
+                                                 ctypes.byref(d)))
+        return {kk: getattr(d, kk) for kk, _ in lbd_diag._fields_}
+
+    def step(self, n=1):
+        self._check(load().lbd_batch_step(self._h, int(n)))
+        return self
+
+    def set_tile(self, bx, by):
+        self._check(load().lbd_batch_set_tile(self._h, int(bx), int(by)))
+
+    def autotune(self, reps=5):
+        bx, by = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().lbd_batch_autotune(self._h, int(reps), ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
+
+    def synchronize(self):
+        self._check(load().lbd_batch_synchronize(self._h))
+
+    @property
+    def t(self):
+        v = ctypes.c_int64()
+        self._check(load().lbd_batch_get_time(self._h, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self._h:
+            load().lbd_batch_destroy(self._h)
             self._h = _P()
 
     def __del__(self):
