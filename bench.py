@@ -68,6 +68,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def max_over_ranks(v, dist, device):
+    """Maximum of a per-rank scalar over all ranks (v itself without a process group)."""
+    if not dist:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(sites_per_rank, world, steps, max_ms):
+    """Sites updated by all ranks divided by the slowest rank's time (weak scaling)."""
+    return world * sites_per_rank * steps / max_ms / 1e3
+
+
+def replica_seed(rank):
+    return 5 + rank
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -226,6 +245,58 @@ def time_e2e(torch, lbd, w, steps, stream):
     return dict(ms=ms, h2d=2 * 8 * N, d2h=5 * 8 * N)
 
 
+def time_batch(torch, lbd, steps, warmup, count=256):
+    """Batched parameter sweep: count independent FP32 single-droplet instances
+    (sides 128-384, radii 15-40, B1 and psi amplitude log-uniform), all stepped
+    together (persistent launch per step, CUDA-graph replay)."""
+    from paper_1711_10984_gb300 import inputs
+    ws = inputs.batch_sweep(count=count)
+    params = [lbd.make_params(lbd.LBD_FP32, w["sources"], **w["params"]) for w in ws]
+    b = lbd.Batch([(w["nx"], w["ny"]) for w in ws], params)
+    for k, w in enumerate(ws):
+        b.set_fields(k, w["phi"], w["psi"])
+    tile = b.autotune(3)
+    b.step(max(warmup, 2))
+    b.synchronize()
+    t0 = time.perf_counter()
+    b.step(steps)
+    b.synchronize()
+    el = time.perf_counter() - t0
+    sites = sum(w["nx"] * w["ny"] for w in ws)
+    b.close()
+    return dict(sites=sites, seconds=el, tile=list(tile), count=count,
+                mlups=sites * steps / el / 1e6)
+
+
+def time_adjoint(lbd, steps=4000, ckpt=100):
+    """Adjoint workload: 256x256 droplet R=30, FP32 forward, gradient of the
+    centroid x-shift w.r.t. psi(0) and B1, checkpoint every 100 steps."""
+    from paper_1711_10984_gb300 import inputs
+    n = 256
+    d = dict(x=n / 2, y=n / 2, R=30.0, psi_mean=0.1, noise=0.01, gx=0.005)
+    phi, psi = inputs.droplet_fields(n, n, [d], seed=4)
+    kw = dict(inputs.PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+    src = [inputs.default_source(d, n, n)]
+    sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=src, **kw)
+    sim.set_fields(phi, psi)
+    sim.step(10)
+    sim.synchronize()
+    sim.set_fields(phi, psi)
+    sim.t = 0
+    t0 = time.perf_counter()
+    sim.step(steps)
+    sim.synchronize()
+    fwd = time.perf_counter() - t0
+    sim.set_fields(phi, psi)
+    sim.t = 0
+    t0 = time.perf_counter()
+    L, dpsi, dB1 = sim.adjoint(steps, ckpt, n / 2)
+    adj = time.perf_counter() - t0
+    sim.close()
+    return dict(forward_s=fwd, adjoint_s=adj, ratio=adj / fwd, steps=steps, ckpt_every=ckpt,
+                loss=L, dL_dB1=dB1, max_abs_dL_dpsi0=float(np.abs(dpsi).max()))
+
+
 def cpu_baseline(w, budget_s=12.0):
     """The FP64 oracle as it stands on the host cores, on the same 2048^2
     workload, for as many whole steps as fit in about budget_s seconds."""
@@ -259,7 +330,7 @@ def run_ours(args):
         dist.init_process_group("nccl")
     barrier = (lambda: dist.barrier()) if dist else (lambda: None)
     dev_name = torch.cuda.get_device_name(local)
-    w = workload(args.n, seed=5 + rank)
+    w = workload(args.n, seed=replica_seed(rank))
     N = args.n * args.n
     stream = torch.cuda.Stream()
     clocks = Clocks(local)
@@ -270,13 +341,10 @@ def run_ours(args):
                          dev_name, barrier)
     clk = clocks.stop()
     e2e = time_e2e(torch, lbd, w, args.steps, stream)
+    batch = time_batch(torch, lbd, min(args.steps, 500), args.warmup)
+    adj = time_adjoint(lbd) if rank == 0 else None
 
-    def maxr(v):
-        if not dist:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
     t32, t64, te = maxr(r32["total_ms"]), maxr(r64["total_ms"]), maxr(e2e["ms"])
     k32, k64 = maxr(r32["kernel_ms"]), maxr(r64["kernel_ms"])
@@ -286,8 +354,8 @@ def run_ours(args):
     if rank != 0:
         return
     hbm, src = peaks()
-    mlups32 = world * N * args.steps / t32 / 1e3
-    mlups64 = world * N * args.steps / t64 / 1e3
+    mlups32 = whole_job_mlups(N, world, args.steps, t32)
+    mlups64 = whole_job_mlups(N, world, args.steps, t64)
     ach32 = BYTES_PER_SITE[1] * N / (k32 / args.steps * 1e-3) / 1e9
     ach64_gbs = BYTES_PER_SITE[0] * N / (k64 / args.steps * 1e-3) / 1e9
     flops64 = FLOPS_PER_SITE * N / (k64 / args.steps * 1e-3) / 1e12
@@ -319,7 +387,13 @@ def run_ours(args):
                  "drift": r64["drift"]},
         "fp32_over_fp64_speedup": round(t64 / t32, 2),
         "fp32_drift": r32["drift"],
-        "adjoint_forward_cost": None,
+        "adjoint_forward_cost": adj,
+        "batch": {"workload": "256 FP32 single-droplet instances, sides 128-384, radii 15-40, "
+                              "B1 and psi amplitude log-uniform, source and sink on",
+                  "value": round(world * batch["mlups"], 1), "unit": "MLUPS",
+                  "sites": batch["sites"], "steps": min(args.steps, 500), "tile": batch["tile"],
+                  "hbm_frac": round(batch["mlups"] * 1e6 * BYTES_PER_SITE[1] / 1e9 / hbm, 4),
+                  "timing": "wall clock around lbd_batch_step + synchronize (graph replays)"},
         "e2e": {"value": round(world * N * args.steps / te / 1e3, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps,

@@ -618,7 +618,19 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             return LBD_ECUDA;
         }
     }
-    c->tile = Tile{118, 64};  // fastest measured default; lbd_autotune refines it
+    // Default launch shape: the stripe kernel (fastest measured on large
+    // lattices) unless it would leave most SMs idle, then the tiled kernel with
+    // its smallest tiles; lbd_autotune refines the choice.
+    c->tile = Tile{118, 64};
+    {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
+            cudaGetLastError();
+            sms = 1;
+        }
+        const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
+        if (stripe_ctas < 2LL * sms) c->tile = Tile{32, 8};
+    }
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
         return LBD_ECUDA;
