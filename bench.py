@@ -152,7 +152,7 @@ class Clocks:
 # ------------------------------------------------------------------ ours
 def kernel_source_hash():
     h = hashlib.sha256()
-    for name in ("lbd_step.cu", "lbd_internal.h"):
+    for name in ("lbd_step.cu", "lbd_stripe.cu", "lbd_stripe2.cu", "lbd_internal.h"):
         with open(os.path.join(ROOT, "paper_1711_10984_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -342,7 +342,7 @@ def run_ours(args):
     clk = clocks.stop()
     e2e = time_e2e(torch, lbd, w, args.steps, stream)
     batch = time_batch(torch, lbd, min(args.steps, 500), args.warmup)
-    adj = time_adjoint(lbd) if rank == 0 else None
+    adj = time_adjoint(lbd, steps=min(4000, 4 * args.steps)) if rank == 0 else None
 
     maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
