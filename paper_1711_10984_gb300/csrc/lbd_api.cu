@@ -629,7 +629,9 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             sms = 1;
         }
         const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
-        if (stripe_ctas < 2LL * sms) c->tile = Tile{32, 8};
+        if (stripe_ctas < 2LL * sms ||
+            !lbd::tile_valid(c->tile, params->precision == LBD_FP32, grid->nx, c->plane))
+            c->tile = Tile{32, 8};
     }
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
@@ -793,7 +795,7 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
 int lbd_set_tile(lbd_ctx *c, int32_t bx, int32_t by) {
     if (!c) return LBD_EINVAL;
     const Tile t{bx, by};
-    if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx))
+    if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane))
         return fail(c, LBD_EINVAL, "launch shape %dx%d is not available for this precision and lattice",
                     bx, by);
     c->tile = t;
@@ -812,7 +814,7 @@ int lbd_autotune(lbd_ctx *c, int32_t reps, int32_t *bx, int32_t *by) {
     int rc = LBD_OK;
     for (int k = 0; k < lbd::n_tiles() && rc == LBD_OK; ++k) {
         const Tile t = lbd::tile_at(k);
-        if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx)) continue;
+        if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane)) continue;
         // The trial launches read the current buffers and write the others; the
         // buffers are not swapped, so the state and t are unchanged.
         auto launch = [&]() -> cudaError_t {
@@ -958,6 +960,11 @@ int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params,
         }
         b->ctx.push_back(c);
     }
+    for (lbd_ctx *c : b->ctx)
+        if (!lbd::tile_valid(b->tile, b->prec == LBD_FP32, c->grid.nx, c->plane)) {
+            lbd_batch_destroy(b);
+            return LBD_EINVAL;
+        }
     if (cudaMalloc(&b->t_dev, sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         lbd_batch_destroy(b);
@@ -1005,6 +1012,9 @@ int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by) {
     if (!b) return LBD_EINVAL;
     if (!((bx == 118 || bx == 246) && (by == 32 || by == 64 || by == 128)))
         return bfail(b, LBD_EINVAL, "batched steps use the stripe kernel: bx 118 or 246, by 32, 64 or 128");
+    for (lbd_ctx *c : b->ctx)
+        if (!lbd::tile_valid(Tile{bx, by}, b->prec == LBD_FP32, c->grid.nx, c->plane))
+            return bfail(b, LBD_EINVAL, "an instance is too large for the batched stripe kernel");
     BCK(b, cudaStreamSynchronize(b->stream));
     b->tile = Tile{bx, by};
     return b->prec == LBD_FP64 ? batch_build<double>(b) : batch_build<float>(b);

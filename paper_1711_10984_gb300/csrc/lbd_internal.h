@@ -60,8 +60,10 @@ struct Tile {
     int bx, by;
 };
 
-// Whether a launch shape can run a step of this precision on an nx-wide lattice.
-bool tile_valid(Tile t, bool fp32, int nx);
+// Whether a launch shape can run a step of this precision on an nx-wide lattice
+// whose population planes hold `plane` elements (the stripe kernels address the
+// nine planes with 32-bit byte offsets).
+bool tile_valid(Tile t, bool fp32, int nx, long long plane);
 
 // Launch one coupled step (mode MODE_STEP) or the fields evaluation
 // (MODE_FIELDS) with tile shape `tile`; returns the launch error.

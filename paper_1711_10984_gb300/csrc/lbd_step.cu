@@ -389,10 +389,11 @@ size_t step_smem_bytes(Tile t) {
     return 0;
 }
 
-bool tile_valid(Tile t, bool fp32, int nx) {
+bool tile_valid(Tile t, bool fp32, int nx, long long plane) {
     bool known = false;
     for (const Tile &k : kTiles) known |= (k.bx == t.bx && k.by == t.by);
     if (!known) return false;
+    if (t.bx >= 118 && 9.0 * (double)plane * (fp32 ? 4.0 : 8.0) >= 4294967295.0) return false;
     if (t.bx == 240) return fp32 && pair_supported(nx);
     return true;
 }

@@ -27,6 +27,7 @@
 // sum_j (2/3 or 1/6)[(psi_j - psi) + (psi + psi_j)(m_j - m)/2], is evaluated
 // through the identity  lap psi + (psi lap m + lap(psi m) - m lap psi) / 2.
 #include <cstdint>
+#include <type_traits>
 
 #include "lbd_internal.h"
 
@@ -95,8 +96,10 @@ struct WinFull {
 
 template <typename T>
 struct StripeSmem {
+    // rings of padded rows (NT + 2 elements: a pad on each side, so that the
+    // x-neighbours of every thread are in bounds) plus the population staging
     static constexpr size_t floats(int nt) {
-        return (size_t)nt * (2 * LD + 6 * RD + 2 * CD + PS * 9);
+        return (size_t)(nt + 2) * (2 * LD + 6 * RD + 2 * CD) + (size_t)nt * PS * 9;
     }
 };
 
@@ -107,78 +110,107 @@ struct StripeOcc {
     static constexpr int value = (sizeof(T) == 4 ? 512 : 256) / NT;
 };
 
+template <int OFF>
+__device__ __forceinline__ void cp4(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0+%2], [%1], 4;\n" ::"r"(dst), "l"(src), "n"(OFF));
+}
+template <int OFF>
+__device__ __forceinline__ void cp8(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0+%2], [%1], 8;\n" ::"r"(dst), "l"(src), "n"(OFF));
+}
+
 template <typename T, int NT>
 __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, const int y0,
                                             const int seg, const T A_t, const T gamma_t,
                                             unsigned char *smem_raw) {
-    T *s_phi = reinterpret_cast<T *>(smem_raw);  // [LD][NT]
-    T *s_psi = s_phi + LD * NT;                   // [LD][NT]
-    T *s_mu = s_psi + LD * NT;                    // [RD][NT]  mu_phi      (A -> B)
-    T *s_m = s_mu + RD * NT;                      // [RD][NT]  m           (A -> B)
-    T *s_ux = s_m + RD * NT;                      // [RD][NT]  u_x         (B -> C)
-    T *s_mus = s_ux + RD * NT;                    // [RD][NT]  mu*         (D -> E)
-    T *s_ms = s_mus + RD * NT;                    // [RD][NT]  m*          (D -> E)
-    T *s_ps = s_ms + RD * NT;                     // [RD][NT]  psi* m*     (D -> E)
-    T *s_phs = s_ps + RD * NT;                    // [CD][NT]  phi*        (C -> D, E)
-    T *s_pss = s_phs + CD * NT;                   // [CD][NT]  psi*        (C -> D, E)
-    T *s_pop = s_pss + CD * NT;                   // [PS][9][NT] pulled populations
-
+    constexpr int RS = NT + 2;  // padded ring row
     const int c = threadIdx.x;
+    // this thread's element in slot 0 of each ring (x-neighbours at -1, +1)
+    T *const s_phi = reinterpret_cast<T *>(smem_raw) + 1 + c;  // [LD] rows
+    T *const s_psi = s_phi + LD * RS;                            // [LD]
+    T *const s_mu = s_psi + LD * RS;                             // [RD]  mu_phi   (A -> B)
+    T *const s_m = s_mu + RD * RS;                               // [RD]  m        (A -> B)
+    T *const s_ux = s_m + RD * RS;                               // [RD]  u_x      (B -> C)
+    T *const s_mus = s_ux + RD * RS;                             // [RD]  mu*      (D -> E)
+    T *const s_ms = s_mus + RD * RS;                             // [RD]  m*       (D -> E)
+    T *const s_ps = s_ms + RD * RS;                              // [RD]  psi* m*  (D -> E)
+    T *const s_phs = s_ps + RD * RS;                             // [CD]  phi*     (C -> D, E)
+    T *const s_pss = s_phs + CD * RS;                            // [CD]  psi*     (C -> D, E)
+    T *const s_pop = reinterpret_cast<T *>(smem_raw) + (2 * LD + 6 * RD + 2 * CD) * RS + c;
+    const unsigned u_phi = (unsigned)__cvta_generic_to_shared(s_phi);
+    const unsigned u_psi = (unsigned)__cvta_generic_to_shared(s_psi);
+    const unsigned u_pop = (unsigned)__cvta_generic_to_shared(s_pop);
+
     const int nx = p.nx, ny = p.ny;
-    const long long pitch = p.pitch, plane = p.plane;
+    constexpr unsigned TB = sizeof(T);
+    // byte offsets fit 32 bits (the host routes larger lattices to the tiled kernel)
+    const unsigned pitch_b = (unsigned)p.pitch * TB, plane_b = (unsigned)p.plane * TB;
+    const unsigned rows_b = (unsigned)ny * pitch_b;
     const int xg = wrapi(x0 - 5 + c, nx);
-    const int xm = xg == 0 ? nx - 1 : xg - 1;
-    const int xp = xg == nx - 1 ? 0 : xg + 1;
-    const int cl = c > 0 ? c - 1 : 0, cr = c < NT - 1 ? c + 1 : NT - 1;
+    const unsigned xg_b = (unsigned)xg * TB;
+    const unsigned xm_b = (unsigned)(xg == 0 ? nx - 1 : xg - 1) * TB;
+    const unsigned xp_b = (unsigned)(xg == nx - 1 ? 0 : xg + 1) * TB;
     const bool inA = c >= 1 && c < NT - 1;
     const bool inB = c >= 2 && c < NT - 2;
     const bool inC = c >= 3 && c < NT - 3;
     const bool inD = c >= 4 && c < NT - 4;
-    const bool inE = c >= 5 && c < NT - 5 && (x0 + c - 5) < nx;
+    const int xo = x0 + c - 5;  // output column of this thread
+    const bool inE = c >= 5 && c < NT - 5 && xo < nx;
+    const unsigned xo_b = (unsigned)xo * TB;
     const int yend = min(y0 + seg, ny);  // owned rows [y0, yend)
 
-    // Wrapped lattice rows of the asynchronous loads, advanced by one per
-    // iteration (no integer division in the loop): loader row y0 - 5 + k and the
-    // rows rb - 1, rb, rb + 1 around stage-B row rb = y0 - 9 + k.
-    int yl = wrapi(y0 - 5, ny);
-    int ybm = wrapi(y0 - 10, ny), yb0 = wrapi(y0 - 9, ny), ybp = wrapi(y0 - 8, ny);
-    auto adv = [&](int &y) { y = (y + 1 == ny) ? 0 : y + 1; };
-    const T *gcm = p.g_in + xm, *gc0 = p.g_in + xg, *gcp = p.g_in + xp;
+    // Byte offsets of the asynchronously loaded rows, advanced by one row per
+    // iteration: loader row y0 - 5 + k and the rows rb - 1, rb, rb + 1 around
+    // stage-B row rb = y0 - 9 + k.
+    unsigned lo_b = (unsigned)wrapi(y0 - 5, ny) * pitch_b + xg_b;
+    unsigned rm_b = (unsigned)wrapi(y0 - 10, ny) * pitch_b;
+    unsigned r0_b = (unsigned)wrapi(y0 - 9, ny) * pitch_b;
+    unsigned rp_b = (unsigned)wrapi(y0 - 8, ny) * pitch_b;
+    auto adv = [&](unsigned &o) {
+        o += pitch_b;
+        if (o >= rows_b) o -= rows_b;
+    };
+    const char *const phi_in = reinterpret_cast<const char *>(p.phi_in);
+    const char *const psi_in = reinterpret_cast<const char *>(p.psi_in);
+    const char *const g_in = reinterpret_cast<const char *>(p.g_in);
 
     // Issue the asynchronous loads of iteration k: phi^n, psi^n of loader row
-    // y0 - 5 + k, and the pulled populations of stage-B row y0 - 9 + k.
+    // y0 - 5 + k, and the pulled populations f_i(x - e_i) of stage-B row y0 - 9 + k.
     auto issue = [&](int k) {
         const int rl = y0 - 5 + k;
         if (rl < yend + 5) {
-            const long long o = (long long)yl * pitch + xg;
-            const int so = (rl & (LD - 1)) * NT + c;
-            cp_async(s_phi + so, p.phi_in + o);
-            cp_async(s_psi + so, p.psi_in + o);
+            const unsigned so = (unsigned)((rl & (LD - 1)) * RS) * TB;
+            if (TB == 8) {
+                cp8<0>(u_phi + so, phi_in + lo_b);
+                cp8<0>(u_psi + so, psi_in + lo_b);
+            } else {
+                cp4<0>(u_phi + so, phi_in + lo_b);
+                cp4<0>(u_psi + so, psi_in + lo_b);
+            }
         }
         const int rb = y0 - 9 + k;
         if (inB && rb >= y0 - 3 && rb < yend + 3) {
-            const long long om = (long long)ybm * pitch, o0 = (long long)yb0 * pitch,
-                            op = (long long)ybp * pitch;
-            T *dst = s_pop + (k % PS) * 9 * NT + c;
-            // plane i of the pull source f_i(x - e_i): walk the planes
-            const T *q0 = gc0 + o0, *qm = gcm + o0, *qp = gcp + o0;
-            const T *q0m = gc0 + om, *qmm = gcm + om, *qpm = gcp + om;
-            const T *q0p = gc0 + op, *qmp = gcm + op, *qpp = gcp + op;
-            cp_async(dst + 0 * NT, q0);                // e = ( 0, 0)
-            cp_async(dst + 1 * NT, qm + plane);        // e = ( 1, 0) from x - 1
-            cp_async(dst + 2 * NT, q0m + 2 * plane);   // e = ( 0, 1) from y - 1
-            cp_async(dst + 3 * NT, qp + 3 * plane);    // e = (-1, 0) from x + 1
-            cp_async(dst + 4 * NT, q0p + 4 * plane);   // e = ( 0,-1) from y + 1
-            cp_async(dst + 5 * NT, qmm + 5 * plane);   // e = ( 1, 1)
-            cp_async(dst + 6 * NT, qpm + 6 * plane);   // e = (-1, 1)
-            cp_async(dst + 7 * NT, qpp + 7 * plane);   // e = (-1,-1)
-            cp_async(dst + 8 * NT, qmp + 8 * plane);   // e = ( 1,-1)
+            const unsigned d = u_pop + (unsigned)((k % PS) * 9 * NT) * TB;
+            constexpr int P = NT * (int)sizeof(T);
+#define LBD_PULL(I, ROW, COL)                                                              \
+    if (TB == 8) cp8<(I) * P>(d, g_in + ((I) * plane_b + ROW + COL));                     \
+    else cp4<(I) * P>(d, g_in + ((I) * plane_b + ROW + COL));
+            LBD_PULL(0, r0_b, xg_b)  // e = ( 0, 0)
+            LBD_PULL(1, r0_b, xm_b)  // e = ( 1, 0) from x - 1
+            LBD_PULL(2, rm_b, xg_b)  // e = ( 0, 1) from y - 1
+            LBD_PULL(3, r0_b, xp_b)  // e = (-1, 0) from x + 1
+            LBD_PULL(4, rp_b, xg_b)  // e = ( 0,-1) from y + 1
+            LBD_PULL(5, rm_b, xm_b)  // e = ( 1, 1)
+            LBD_PULL(6, rm_b, xp_b)  // e = (-1, 1)
+            LBD_PULL(7, rp_b, xp_b)  // e = (-1,-1)
+            LBD_PULL(8, rp_b, xm_b)  // e = ( 1,-1)
+#undef LBD_PULL
         }
         cp_commit();
-        adv(yl);
-        adv(ybm);
-        adv(yb0);
-        adv(ybp);
+        adv(lo_b);
+        adv(rm_b);
+        adv(r0_b);
+        adv(rp_b);
     };
 
     WinFull<T> wPhiA, wPsiA, wMuB, wMB, wPhsD, wPssD;
@@ -189,10 +221,16 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     T ux1 = 0, ux2 = 0, uy1 = 0, uy2 = 0, uy3 = 0;  // own u from B, 1..3 iterations old
 
     const T a = p.a, b = p.b, B0 = p.B0, B1 = p.B1;
+    char *const g_out = reinterpret_cast<char *>(p.g_out);
+    char *const phi_out = reinterpret_cast<char *>(p.phi_out);
+    char *const psi_out = reinterpret_cast<char *>(p.psi_out);
     issue(0);
     issue(1);
     const int iters = (yend - y0) + 15;
-    for (int i = 0; i < iters; ++i) {
+    // One pipeline iteration; with GUARD false (steady state: every stage active,
+    // every row written is owned) the row conditions vanish at compile time.
+    auto body = [&](auto guard_tag, const int i) {
+        constexpr bool GUARD = decltype(guard_tag)::value;
         cp_wait1();
         __syncthreads();
         issue(i + 2);
@@ -200,47 +238,50 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         // ---- E: phi^{n+1}, psi^{n+1} at row y0 - 15 + i --------------------------
         {
             const int r = y0 - 15 + i;   // output row; pushes row r + 1
-            if (i >= 13 && inE) {
-                const int s1 = ((r + 1) & (RD - 1)) * NT, s1c = ((r + 1) & (CD - 1)) * NT;
-                const T lmu = wMusE.push(s_mus[s1 + c], s_mus[s1 + cl], s_mus[s1 + cr]);
+            if ((!GUARD || i >= 13) && inE) {
+                const T *M1 = s_mus + ((r + 1) & (RD - 1)) * RS;
+                const T *N1 = s_ms + ((r + 1) & (RD - 1)) * RS;
+                const T *P1 = s_ps + ((r + 1) & (RD - 1)) * RS;
+                const T *C1 = s_pss + ((r + 1) & (CD - 1)) * RS;
+                const T lmu = wMusE.push(M1[0], M1[-1], M1[1]);
                 const T mc = wMsE.c0;
-                const T lm = wMsE.push(s_ms[s1 + c], s_ms[s1 + cl], s_ms[s1 + cr]);
+                const T lm = wMsE.push(N1[0], N1[-1], N1[1]);
                 const T psc = wPssE.c0;
-                const T lps = wPssE.push(s_pss[s1c + c], s_pss[s1c + cl], s_pss[s1c + cr]);
-                const T lp = wPsE.push(s_ps[s1 + c], s_ps[s1 + cl], s_ps[s1 + cr]);
-                if (r >= y0) {
-                    const T phs = s_phs[(r & (CD - 1)) * NT + c];
+                const T lps = wPssE.push(C1[0], C1[-1], C1[1]);
+                const T lp = wPsE.push(P1[0], P1[-1], P1[1]);
+                if (!GUARD || r >= y0) {
+                    const T phs = s_phs[(r & (CD - 1)) * RS];
                     // Eq. (18): phi* + M lap mu*
                     const T phi_new = phs + p.M * lmu;
                     // Eq. (19): div(D psi grad mu_psi) in the log-free form
                     const T div = lps + T(0.5) * ((psc * lm + lp) - mc * lps);
                     T src = T(0);
                     if (p.theta) {
-                        const int gx = x0 + c - 5;
-                        const uint32_t w = p.theta[(long long)r * p.theta_words + (gx >> 5)];
-                        if ((w >> (gx & 31)) & 1u) src = A_t;
+                        const uint32_t w = p.theta[r * p.theta_words + (xo >> 5)];
+                        if ((w >> (xo & 31)) & 1u) src = A_t;
                     }
                     const T psi_new = psc + (p.D * div - gamma_t * (psc - p.c0) + src);
-                    const long long o = (long long)r * pitch + (x0 + c - 5);
-                    p.phi_out[o] = phi_new;
-                    p.psi_out[o] = psi_new;
+                    const unsigned o = (unsigned)r * pitch_b + xo_b;
+                    *reinterpret_cast<T *>(phi_out + o) = phi_new;
+                    *reinterpret_cast<T *>(psi_out + o) = psi_new;
                 }
             }
         }
         // ---- D: mu*, m*, p* at row y0 - 13 + i -----------------------------------
         {
             const int r = y0 - 13 + i;
-            if (i >= 10 && inD && r < yend + 1) {
-                const int s1 = ((r + 1) & (CD - 1)) * NT;
+            if ((!GUARD || (i >= 10 && r < yend + 1)) && inD) {
+                const T *F1 = s_phs + ((r + 1) & (CD - 1)) * RS;
+                const T *S1 = s_pss + ((r + 1) & (CD - 1)) * RS;
                 T px, py, plap, ph, cx, cy, cs;
-                wPhsD.push(s_phs[s1 + c], s_phs[s1 + cl], s_phs[s1 + cr], px, py, plap, ph);
-                wPssD.push_grad(s_pss[s1 + c], s_pss[s1 + cl], s_pss[s1 + cr], cx, cy, cs);
-                if (i >= 12) {
-                    const T pn = s_phi[(r & (LD - 1)) * NT + c];  // phi^n for the cubic
+                wPhsD.push(F1[0], F1[-1], F1[1], px, py, plap, ph);
+                wPssD.push_grad(S1[0], S1[-1], S1[1], cx, cy, cs);
+                if (!GUARD || i >= 12) {
+                    const T pn = s_phi[(r & (LD - 1)) * RS];  // phi^n for the cubic
                     const T mus = a * ph + b * (pn * pn * pn) - (B0 + B1 * cs) * plap -
                                   B1 * (px * cx + py * cy);
                     const T ms = T(0.5) * B1 * (px * px + py * py);
-                    const int so = (r & (RD - 1)) * NT + c;
+                    const int so = (r & (RD - 1)) * RS;
                     s_mus[so] = mus;
                     s_ms[so] = ms;
                     s_ps[so] = cs * ms;
@@ -250,25 +291,24 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         // ---- C: phi*, psi* at row y0 - 11 + i ------------------------------------
         {
             const int r = y0 - 11 + i;
-            if (i >= 9 && inC && r < yend + 2) {
-                const int sr = (r & (LD - 1)) * NT;
-                const int srm = ((r - 1) & (LD - 1)) * NT, srp = ((r + 1) & (LD - 1)) * NT;
-                const int su = (r & (RD - 1)) * NT;
+            if ((!GUARD || (i >= 9 && r < yend + 2)) && inC) {
+                const T *P = s_phi + (r & (LD - 1)) * RS, *Q = s_psi + (r & (LD - 1)) * RS;
+                const T *Pn = s_phi + ((r + 1) & (LD - 1)) * RS, *Qn = s_psi + ((r + 1) & (LD - 1)) * RS;
+                const T *Ps = s_phi + ((r - 1) & (LD - 1)) * RS, *Qs = s_psi + ((r - 1) & (LD - 1)) * RS;
+                const T *U = s_ux + (r & (RD - 1)) * RS;
                 const T uxc = ux2;
-                const T ue = T(0.5) * (uxc + s_ux[su + c + 1]);
-                const T uw = T(0.5) * (s_ux[su + c - 1] + uxc);
+                const T ue = T(0.5) * (uxc + U[1]);
+                const T uw = T(0.5) * (U[-1] + uxc);
                 const T un = T(0.5) * (uy2 + uy1);
                 const T us = T(0.5) * (uy3 + uy2);
-                const T P0 = s_phi[sr + c], PE = s_phi[sr + c + 1], PW = s_phi[sr + c - 1];
-                const T PN = s_phi[srp + c], PS_ = s_phi[srm + c];
-                const T C0 = s_psi[sr + c], CE = s_psi[sr + c + 1], CW = s_psi[sr + c - 1];
-                const T CN = s_psi[srp + c], CS = s_psi[srm + c];
+                const T P0 = P[0], PE = P[1], PW = P[-1], PN = Pn[0], PS_ = Ps[0];
+                const T C0 = Q[0], CE = Q[1], CW = Q[-1], CN = Qn[0], CS = Qs[0];
                 const bool pe = ue > T(0), pw = uw > T(0), pn = un > T(0), ps = us > T(0);
                 const T fe = ue * (pe ? P0 : PE), fw = uw * (pw ? PW : P0);
                 const T fn = un * (pn ? P0 : PN), fs = us * (ps ? PS_ : P0);
                 const T ge = ue * (pe ? C0 : CE), gw = uw * (pw ? CW : C0);
                 const T gn = un * (pn ? C0 : CN), gs = us * (ps ? CS : C0);
-                const int so = (r & (CD - 1)) * NT + c;
+                const int so = (r & (CD - 1)) * RS;
                 s_phs[so] = P0 - ((fe - fw) + (fn - fs));
                 s_pss[so] = C0 - ((ge - gw) + (gn - gs));
             }
@@ -277,13 +317,14 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         {
             const int r = y0 - 9 + i;
             T ux = T(0), uy = T(0);
-            if (i >= 4 && inB && r < yend + 3) {
-                const int s1 = ((r + 1) & (RD - 1)) * NT;
+            if ((!GUARD || (i >= 4 && r < yend + 3)) && inB) {
+                const T *M1 = s_mu + ((r + 1) & (RD - 1)) * RS;
+                const T *N1 = s_m + ((r + 1) & (RD - 1)) * RS;
                 T mx, my, mc, nx_, ny_, nc;
-                wMuB.push_grad(s_mu[s1 + c], s_mu[s1 + cl], s_mu[s1 + cr], mx, my, mc);
-                wMB.push_grad(s_m[s1 + c], s_m[s1 + cl], s_m[s1 + cr], nx_, ny_, nc);
-                if (i >= 6) {
-                    const int sr = (r & (LD - 1)) * NT + c;
+                wMuB.push_grad(M1[0], M1[-1], M1[1], mx, my, mc);
+                wMB.push_grad(N1[0], N1[-1], N1[1], nx_, ny_, nc);
+                if (!GUARD || i >= 6) {
+                    const int sr = (r & (LD - 1)) * RS;
                     const T ph = s_phi[sr], ps = s_psi[sr];
                     // Eq. (14) with psi grad mu_psi = grad psi + psi grad m
                     T Fx = -ph * mx - (gpx2 + ps * nx_);
@@ -292,7 +333,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                         Fx += p.fx;
                         Fy += p.fy;
                     }
-                    const T *G = s_pop + (i % PS) * 9 * NT + c;
+                    const T *G = s_pop + (i % PS) * 9 * NT;
                     const T g0 = G[0], g1 = G[NT], g2 = G[2 * NT], g3 = G[3 * NT], g4 = G[4 * NT];
                     const T g5 = G[5 * NT], g6 = G[6 * NT], g7 = G[7 * NT], g8 = G[8 * NT];
                     // Eq. (11) on the deviations g = f - w
@@ -303,7 +344,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                     const T inv = T(1) / n;
                     ux = (jx + T(0.5) * Fx) * inv;
                     uy = (jy + T(0.5) * Fy) * inv;
-                    if (r >= y0 && r < yend && inE) {
+                    if ((!GUARD || (r >= y0 && r < yend)) && inE) {
                         // BGK + Guo (Eqs. 10, 12, 13), opposite directions paired:
                         // post_i = (1-w) g_i + W (K + eu (c1 eu + c2 eF)) +- W (c3 eu + c4 eF)
                         const T om = p.omega, gk = p.guo, om1 = T(1) - om;
@@ -311,27 +352,29 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                         const T K = om * (dn - T(1.5) * n * usq) - T(3) * gk * uF;
                         const T c1 = T(4.5) * om * n, c2 = T(9) * gk;
                         const T c3 = T(3) * om * n, c4 = T(3) * gk;
-                        T *Go = p.g_out + (long long)r * pitch + (x0 + c - 5);
-                        Go[0] = om1 * g0 + T(4.0 / 9.0) * K;
+                        char *Go = g_out + ((unsigned)r * pitch_b + xo_b);
+#define LBD_OUT(I) (*reinterpret_cast<T *>(Go + (I) * plane_b))
+                        LBD_OUT(0) = om1 * g0 + T(4.0 / 9.0) * K;
 #define LBD_PAIR(I, J, W, EU, EF)                                       \
     {                                                                   \
         const T eu = (EU), eF = (EF);                                   \
         const T sym = T(W) * (K + eu * (c1 * eu + c2 * eF));            \
         const T anti = T(W) * (c3 * eu + c4 * eF);                      \
-        Go[(I) * plane] = om1 * g##I + (sym + anti);                    \
-        Go[(J) * plane] = om1 * g##J + (sym - anti);                    \
+        LBD_OUT(I) = om1 * g##I + (sym + anti);                         \
+        LBD_OUT(J) = om1 * g##J + (sym - anti);                         \
     }
                         LBD_PAIR(1, 3, 1.0 / 9.0, ux, Fx)
                         LBD_PAIR(2, 4, 1.0 / 9.0, uy, Fy)
                         LBD_PAIR(5, 7, 1.0 / 36.0, ux + uy, Fx + Fy)
                         LBD_PAIR(6, 8, 1.0 / 36.0, uy - ux, Fy - Fx)
 #undef LBD_PAIR
+#undef LBD_OUT
                     }
                     if (p.flags & LBD_FROZEN_U) {
                         ux = p.ux0;
                         uy = p.uy0;
                     }
-                    s_ux[(r & (RD - 1)) * NT + c] = ux;
+                    s_ux[(r & (RD - 1)) * RS] = ux;
                 }
             }
             // own-column u history for stage C (rows r-1, r-2, r-3 next iteration)
@@ -342,13 +385,14 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         {
             const int r = y0 - 7 + i;
             T gx = T(0), gy = T(0);
-            if (i >= 1 && inA && r < yend + 4) {
-                const int s1 = ((r + 1) & (LD - 1)) * NT;
+            if ((!GUARD || (i >= 1 && r < yend + 4)) && inA) {
+                const T *F1 = s_phi + ((r + 1) & (LD - 1)) * RS;
+                const T *S1 = s_psi + ((r + 1) & (LD - 1)) * RS;
                 T px, py, plap, ph, cs;
-                wPhiA.push(s_phi[s1 + c], s_phi[s1 + cl], s_phi[s1 + cr], px, py, plap, ph);
-                wPsiA.push_grad(s_psi[s1 + c], s_psi[s1 + cl], s_psi[s1 + cr], gx, gy, cs);
-                if (i >= 3) {
-                    const int so = (r & (RD - 1)) * NT + c;
+                wPhiA.push(F1[0], F1[-1], F1[1], px, py, plap, ph);
+                wPsiA.push_grad(S1[0], S1[-1], S1[1], gx, gy, cs);
+                if (!GUARD || i >= 3) {
+                    const int so = (r & (RD - 1)) * RS;
                     s_mu[so] = a * ph + b * (ph * ph * ph) - (B0 + B1 * cs) * plap -
                                B1 * (px * gx + py * gy);
                     s_m[so] = T(0.5) * B1 * (px * px + py * py);
@@ -356,7 +400,15 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
             }
             gpx2 = gpx1; gpy2 = gpy1; gpx1 = gx; gpy1 = gy;
         }
-    }
+    };
+    const std::integral_constant<bool, true> guarded;
+    const std::integral_constant<bool, false> steady;
+    const int s1 = (yend - y0) + 9;
+    int i = 0;
+    for (; i < 15 && i < iters; ++i) body(guarded, i);
+#pragma unroll 1
+    for (; i < s1; ++i) body(steady, i);
+    for (; i < iters; ++i) body(guarded, i);
     asm volatile("cp.async.wait_all;\n" ::);
 }
 

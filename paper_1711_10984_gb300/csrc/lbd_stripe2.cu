@@ -12,6 +12,7 @@
 // which needs nx to be a multiple of 4 and at least W + 8 (otherwise the
 // library uses the one-column kernel).
 #include <cstdint>
+#include <type_traits>
 
 #include "lbd_internal.h"
 
@@ -174,7 +175,11 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
     issue(0);
     issue(1);
     const int iters = (yend - y0) + 15;
-    for (int i = 0; i < iters; ++i) {
+    // One pipeline iteration.  With GUARD false (the steady state, where every
+    // stage is active and every row it writes is owned) the stage conditions
+    // vanish at compile time, so the compiler can interleave the stages.
+    auto body = [&](auto guard_tag, const int i) {
+        constexpr bool GUARD = decltype(guard_tag)::value;
         asm volatile("cp.async.wait_group 1;\n" ::);
         __syncthreads();
         issue(i + 2);
@@ -182,7 +187,7 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
         // ---- E: phi^{n+1}, psi^{n+1} ---------------------------------------------
         {
             const int r = y0 - 15 + i;
-            if (i >= 13 && r < yend) {
+            if (!GUARD || (i >= 13 && r < yend)) {
                 const Nb mu = nb(s_mus + ((r + 1) & (RD2 - 1)) * W2C, t);
                 const Nb ms = nb(s_ms + ((r + 1) & (RD2 - 1)) * W2C, t);
                 const Nb ps = nb(s_pss + ((r + 1) & (CD2 - 1)) * W2C, t);
@@ -192,7 +197,7 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
                 const float2 lm = wMsE.push(ms.c, ms.l, ms.r);
                 const float2 lps = wPssE.push(ps.c, ps.l, ps.r);
                 const float2 lp = wPsE.push(pp.c, pp.l, pp.r);
-                if (r >= y0 && out) {
+                if ((!GUARD || r >= y0) && out) {
                     const float2 phs = ld2(s_phs + (r & (CD2 - 1)) * W2C, t);
                     const float2 phi_new = fma2(S2(p.M), lmu, phs);
                     // lap psi + (psi lap m + lap(psi m) - m lap psi) / 2
@@ -214,13 +219,13 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
         // ---- D: mu*, m*, p* ----------------------------------------------------------
         {
             const int r = y0 - 13 + i;
-            if (i >= 10 && r < yend + 1) {
+            if (!GUARD || (i >= 10 && r < yend + 1)) {
                 const Nb ph = nb(s_phs + ((r + 1) & (CD2 - 1)) * W2C, t);
                 const Nb cs = nb(s_pss + ((r + 1) & (CD2 - 1)) * W2C, t);
                 float2 px, py, plap, phm, cx, cy, csm;
                 wPhsD.push(ph.c, ph.l, ph.r, px, py, plap, phm);
                 wPssD.push_grad(cs.c, cs.l, cs.r, cx, cy, csm);
-                if (i >= 12) {
+                if (!GUARD || i >= 12) {
                     const float2 pn = ld2(s_phi + (r & (LD2 - 1)) * W2C, t);
                     const float2 B = fma2(B12, csm, B02);
                     const float2 mus = fma2(a2, phm, b2 * (pn * pn * pn)) - B * plap -
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
         // ---- C: phi*, psi* (donor-cell fluxes) ----------------------------------------
         {
             const int r = y0 - 11 + i;
-            if (i >= 9 && r < yend + 2) {
+            if (!GUARD || (i >= 9 && r < yend + 2)) {
                 const float *urow = s_ux + (r & (RD2 - 1)) * W2C;
                 const float ulo = urow[t > 0 ? 2 * t - 1 : 0];
                 const float uhi = urow[t < NT2 - 1 ? 2 * t + 2 : W2C - 1];
@@ -267,13 +272,13 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
         {
             const int r = y0 - 9 + i;
             float2 ux = S2(0.f), uy = S2(0.f);
-            if (i >= 4 && r < yend + 3) {
+            if (!GUARD || (i >= 4 && r < yend + 3)) {
                 const Nb mu = nb(s_mu + ((r + 1) & (RD2 - 1)) * W2C, t);
                 const Nb mm = nb(s_m + ((r + 1) & (RD2 - 1)) * W2C, t);
                 float2 mx, my, mc, nx2, ny2, nc;
                 wMuB.push_grad(mu.c, mu.l, mu.r, mx, my, mc);
                 wMB.push_grad(mm.c, mm.l, mm.r, nx2, ny2, nc);
-                if (i >= 6) {
+                if (!GUARD || i >= 6) {
                     const float2 ph = ld2(s_phi + (r & (LD2 - 1)) * W2C, t);
                     const float2 ps = ld2(s_psi + (r & (LD2 - 1)) * W2C, t);
                     // Eq. (14): F = -phi grad mu - (grad psi + psi grad m)
@@ -301,7 +306,7 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
                     const float2 inv = make_float2(__frcp_rn(n.x), __frcp_rn(n.y));
                     ux = fma2(S2(0.5f), Fx, jx) * inv;
                     uy = fma2(S2(0.5f), Fy, jy) * inv;
-                    if (r >= y0 && r < yend && out) {
+                    if ((!GUARD || (r >= y0 && r < yend)) && out) {
                         const float om = p.omega, gk = p.guo;
                         const float2 om1 = S2(1.f - om);
                         const float2 usq = fma2(ux, ux, uy * uy);
@@ -339,13 +344,13 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
         {
             const int r = y0 - 7 + i;
             float2 gx = S2(0.f), gy = S2(0.f);
-            if (i >= 1 && r < yend + 4) {
+            if (!GUARD || (i >= 1 && r < yend + 4)) {
                 const Nb ph = nb(s_phi + ((r + 1) & (LD2 - 1)) * W2C, t);
                 const Nb cs = nb(s_psi + ((r + 1) & (LD2 - 1)) * W2C, t);
                 float2 px, py, plap, phm, csm;
                 wPhiA.push(ph.c, ph.l, ph.r, px, py, plap, phm);
                 wPsiA.push_grad(cs.c, cs.l, cs.r, gx, gy, csm);
-                if (i >= 3) {
+                if (!GUARD || i >= 3) {
                     const int so = (r & (RD2 - 1)) * W2C;
                     const float2 B = fma2(B12, csm, B02);
                     st2(s_mu + so, t,
@@ -355,7 +360,16 @@ __global__ void __launch_bounds__(NT2, 2) pair_kernel(const StepArgs<float> p, c
             }
             gpx2 = gpx1; gpy2 = gpy1; gpx1 = gx; gpy1 = gy;
         }
-    }
+    };
+    // prologue and epilogue guarded, steady state [15, rows + 9) unguarded
+    const std::integral_constant<bool, true> guarded;
+    const std::integral_constant<bool, false> steady;
+    const int s1 = (yend - y0) + 9;
+    int i = 0;
+    for (; i < 15 && i < iters; ++i) body(guarded, i);
+#pragma unroll 1
+    for (; i < s1; ++i) body(steady, i);
+    for (; i < iters; ++i) body(guarded, i);
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
