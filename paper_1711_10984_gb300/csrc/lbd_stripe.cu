@@ -406,7 +406,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     const int s1 = (yend - y0) + 9;
     int i = 0;
     for (; i < 15 && i < iters; ++i) body(guarded, i);
-#pragma unroll 1
+#pragma unroll 2
     for (; i < s1; ++i) body(steady, i);
     for (; i < iters; ++i) body(guarded, i);
     asm volatile("cp.async.wait_all;\n" ::);

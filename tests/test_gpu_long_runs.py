@@ -1,0 +1,93 @@
+"""Long GPU runs of the shipped workloads.
+
+* Two-droplet collision (512x256, radii 25, separation 80, offset 20, source and
+  sink on): the FP32 shifted-population form tracks the FP64 form's droplet
+  centroids within 0.02 lattice units over 20,000 steps.  Totals: FP64 drifts
+  only by rounding (1e-12); FP32 keeps total n to 1e-6 but total phi drifts by
+  about 7e-6 relative over this run (phi is stored in FP32: bulk changes below
+  half an ulp of |phi| ~ 1 are rounded away, and they have a consistent sign
+  while the bulk relaxes), bounded here at 5e-5.
+* Self-propulsion (Section 4): with the source switched on inside the droplet
+  next to its +x interface, the droplet moves toward the source side (sign
+  check only, as the paper gives no trajectory values for this setup).
+"""
+import numpy as np
+import pytest
+
+from paper_1711_10984_gb300 import inputs, lbd
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1711_10984_gb300 import build
+    build.build()
+    lbd.load()
+
+
+def centroids(sim, refs):
+    out = []
+    for (x, y) in refs:
+        d = sim.diagnostics(x % sim.nx, y % sim.ny)
+        out.append((d["cm_x"], d["cm_y"]))
+    return out
+
+
+def test_two_droplets_fp32_tracks_fp64():
+    w = inputs.two_droplets(sep=80.0, offset=20.0)
+    nx, ny = w["nx"], w["ny"]
+    sims = {}
+    for prec in (lbd.LBD_FP64, lbd.LBD_FP32):
+        s = lbd.Sim(nx, ny, precision=prec, sources=w["sources"], **w["params"])
+        s.set_fields(w["phi"], w["psi"])
+        sims[prec] = s
+    refs = [(d["x"], d["y"]) for d in w["droplets"]]
+    d0 = {p: s.diagnostics(nx / 2, ny / 2) for p, s in sims.items()}
+    worst = 0.0
+    for _ in range(10):
+        for s in sims.values():
+            s.step(2000)
+        c64 = centroids(sims[lbd.LBD_FP64], refs)
+        c32 = centroids(sims[lbd.LBD_FP32], refs)
+        for a, b in zip(c64, c32):
+            worst = max(worst, abs(a[0] - b[0]), abs(a[1] - b[1]))
+        # the reference points follow the droplets
+        refs = c64
+    assert worst <= 0.02, worst
+    for p, s in sims.items():
+        d1 = s.diagnostics(nx / 2, ny / 2)
+        tol_n = 1e-12 if p == lbd.LBD_FP64 else 1e-6
+        tol_phi = 1e-12 if p == lbd.LBD_FP64 else 5e-5
+        assert abs(d1["sum_rho"] - d0[p]["sum_rho"]) <= tol_n * d0[p]["sum_rho"]
+        assert abs(d1["sum_phi"] - d0[p]["sum_phi"]) <= tol_phi * abs(d0[p]["sum_phi"])
+        assert d1["nonfinite"] == 0 and d1["min_B"] > 0
+
+
+def test_droplet_moves_toward_the_source():
+    """Sign checks of Section 4: a source disk inside the droplet, tangent to its
+    +x interface, drives the centre of mass toward +x for either sign of B1, and
+    faster for B1 < 0 than for B1 > 0; without source and sink the droplet stays.
+    The production is stronger than the paper's (A = 1e-4 from the start, sink
+    gamma = 1.5e-3) so that the motion shows within 30,000 steps."""
+    n = 128
+    d = dict(x=64.0, y=64.0, R=20.0, psi_mean=0.1)
+    shift = {}
+    for B1 in (-0.03, 0.03):
+        phi, psi = inputs.droplet_fields(n, n, [d], B1=B1)
+        src = [inputs.default_source(d, n, n)]
+        kw = dict(inputs.PAPER, B1=B1, M=1.0, tau=1.0, gamma=1.5e-3, c0=0.09, A0=1e-4,
+                  A_max=1e-4, t_on=-1)
+        passive = dict(kw, A0=0.0, A_max=0.0, gamma=0.0)
+        for name, par in (("active", kw), ("passive", passive)):
+            s = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=src, **par)
+            s.set_fields(phi, psi)
+            x0 = s.diagnostics(64, 64)["cm_x"]
+            s.step(30000)
+            dd = s.diagnostics(64, 64)
+            assert dd["nonfinite"] == 0 and dd["min_B"] > 0
+            shift[(B1, name)] = dd["cm_x"] - x0
+    for B1 in (-0.03, 0.03):
+        assert shift[(B1, "active")] > 0.02, shift
+        assert abs(shift[(B1, "passive")]) < 0.1 * shift[(B1, "active")], shift
+    assert shift[(-0.03, "active")] > shift[(0.03, "active")], shift
