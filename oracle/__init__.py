@@ -12,7 +12,7 @@ independent restatements live here:
 Parity status per function (pins in ``tests/test_oracle_*.py``):
   stencils, equilibrium, Guo forcing, advection, diffusion, source/sink,
   conservation, flat-interface profile, Laplace law, shear-wave decay,
-  Galilean invariance: pinned.  The full nonlinear coupled trajectory has no
+  Galilean invariance, free-energy density (Table 1 sigma_num): pinned.  The full nonlinear coupled trajectory has no
   printed values to compare with; it is pinned only through the invariants and
   the agreement of the two restatements.
 """
