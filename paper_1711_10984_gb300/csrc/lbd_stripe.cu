@@ -34,9 +34,9 @@
 namespace lbd {
 namespace {
 
-constexpr int LD = 16;  // rows in the phi^n / psi^n ring
-constexpr int RD = 4;   // rows in the mu, m, u, mu*, m*, p* rings
-constexpr int CD = 8;   // rows in the phi* / psi* ring
+constexpr int LD = 16;  // rows in the (phi^n, psi^n) ring
+constexpr int RD = 4;   // rows in the (mu, m), u_x, (mu*, m*), (psi*, p*) rings
+constexpr int CD = 8;   // rows in the (phi*, psi*) ring
 constexpr int PS = 3;   // population staging depth (rows in flight)
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -44,62 +44,102 @@ __device__ __forceinline__ int wrapi(int v, int n) {
     return r < 0 ? r + n : r;
 }
 
-template <typename T>
-__device__ __forceinline__ void cp_async(T *dst_smem, const T *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
-    if (sizeof(T) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src));
-}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::); }
 
-// Stencil history of one column: rows r-1 and r are kept; push(r+1) yields the
-// derivatives at row r and then advances.
+// Two fields of one site in the two lanes of a vector: FP32 pairs use the packed
+// FP32x2 instructions of sm_100+ (FADD2 / FMUL2 / FFMA2); FP64 pairs are plain
+// component-wise arithmetic.
 template <typename T>
-struct WinLap {
-    T cm, c0, tm, t0;
-    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = T(0); }
-    // returns lap at the middle row
-    __device__ __forceinline__ T push(T c, T l, T r) {
-        const T t = (l + r) - T(2) * c;
-        const T lap = T(2.0 / 3.0) * t0 + T(1.0 / 6.0) * (tm + t) + ((c - c0) - (c0 - cm));
+struct V2t;
+template <>
+struct V2t<float> {
+    using type = float2;
+};
+template <>
+struct V2t<double> {
+    using type = double2;
+};
+
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, rounded once
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 vsplat(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 vmake(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) {
+    return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+    return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 vsplat(double s) { return make_double2(s, s); }
+__device__ __forceinline__ double2 vmake(double a, double b) { return make_double2(a, b); }
+
+// Stencil history of one column for a pair of fields: rows r-1 and r are kept in
+// the well-conditioned form T = L + R - 2C, D = R - L and the centre C; push(r+1)
+// gives the derivatives at row r and advances:
+//   d/dx = (4 D_r + D_{r-1} + D_{r+1}) / 12
+//   d/dy = (C_{r+1} - C_{r-1}) / 2 + (T_{r+1} - T_{r-1}) / 12
+//   lap  = (2/3) T_r + (T_{r-1} + T_{r+1}) / 6 + (C_{r+1} - 2 C_r + C_{r-1})
+// i.e. the isotropic D2Q9 stencils (1/3, 1/12 gradient weights; 2/3, 1/6
+// Laplacian link weights).
+template <typename V>
+struct Win2 {
+    V cm, c0, tm, t0, dm, d0;
+    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = dm = d0 = vsplat(decltype(cm.x)(0)); }
+    __device__ __forceinline__ void push(V c, V l, V r, V &gx, V &gy, V &lap, V &mid) {
+        using S = decltype(cm.x);
+        const V t = vfma(c, vsplat(S(-2)), l + r);
+        const V d = r - l;
+        gx = vfma(d0, vsplat(S(4)), dm + d) * vsplat(S(1.0 / 12.0));
+        gy = vfma(c - cm, vsplat(S(0.5)), (t - tm) * vsplat(S(1.0 / 12.0)));
+        lap = vfma(t0, vsplat(S(2.0 / 3.0)),
+                   vfma(tm + t, vsplat(S(1.0 / 6.0)), (c - c0) - (c0 - cm)));
+        mid = c0;
+        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
+    }
+    __device__ __forceinline__ void push_grad(V c, V l, V r, V &gx, V &gy, V &mid) {
+        using S = decltype(cm.x);
+        const V t = vfma(c, vsplat(S(-2)), l + r);
+        const V d = r - l;
+        gx = vfma(d0, vsplat(S(4)), dm + d) * vsplat(S(1.0 / 12.0));
+        gy = vfma(c - cm, vsplat(S(0.5)), (t - tm) * vsplat(S(1.0 / 12.0)));
+        mid = c0;
+        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
+    }
+};
+
+template <typename V>
+struct WinLap2 {
+    V cm, c0, tm, t0;
+    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = vsplat(decltype(cm.x)(0)); }
+    __device__ __forceinline__ V push(V c, V l, V r) {
+        using S = decltype(cm.x);
+        const V t = vfma(c, vsplat(S(-2)), l + r);
+        const V lap = vfma(t0, vsplat(S(2.0 / 3.0)),
+                           vfma(tm + t, vsplat(S(1.0 / 6.0)), (c - c0) - (c0 - cm)));
         cm = c0; c0 = c; tm = t0; t0 = t;
         return lap;
     }
 };
 
 template <typename T>
-struct WinFull {
-    T cm, c0, tm, t0, dm, d0;
-    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = dm = d0 = T(0); }
-    // gradient and Laplacian at the middle row; `mid` receives its centre value
-    __device__ __forceinline__ void push(T c, T l, T r, T &gx, T &gy, T &lap, T &mid) {
-        const T t = (l + r) - T(2) * c;
-        const T d = r - l;
-        gx = (T(4) * d0 + (dm + d)) * T(1.0 / 12.0);
-        gy = T(0.5) * (c - cm) + T(1.0 / 12.0) * (t - tm);
-        lap = T(2.0 / 3.0) * t0 + T(1.0 / 6.0) * (tm + t) + ((c - c0) - (c0 - cm));
-        mid = c0;
-        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
-    }
-    __device__ __forceinline__ void push_grad(T c, T l, T r, T &gx, T &gy, T &mid) {
-        const T t = (l + r) - T(2) * c;
-        const T d = r - l;
-        gx = (T(4) * d0 + (dm + d)) * T(1.0 / 12.0);
-        gy = T(0.5) * (c - cm) + T(1.0 / 12.0) * (t - tm);
-        mid = c0;
-        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
-    }
-};
-
-template <typename T>
 struct StripeSmem {
-    // rings of padded rows (NT + 2 elements: a pad on each side, so that the
-    // x-neighbours of every thread are in bounds) plus the population staging
+    // Pair rings (two fields interleaved per column) and one scalar ring, each row
+    // padded by one column on each side so the x-neighbours of every thread are in
+    // bounds; then the population staging.
     static constexpr size_t floats(int nt) {
-        return (size_t)(nt + 2) * (2 * LD + 6 * RD + 2 * CD) + (size_t)nt * PS * 9;
+        return (size_t)(nt + 2) * (2 * (LD + RD + RD + RD + CD) + RD) + (size_t)nt * PS * 9;
     }
 };
 
@@ -123,22 +163,18 @@ template <typename T, int NT>
 __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, const int y0,
                                             const int seg, const T A_t, const T gamma_t,
                                             unsigned char *smem_raw) {
-    constexpr int RS = NT + 2;  // padded ring row
+    using V = typename V2t<T>::type;
+    constexpr int RS = NT + 2;  // padded ring row (columns)
     const int c = threadIdx.x;
     // this thread's element in slot 0 of each ring (x-neighbours at -1, +1)
-    T *const s_phi = reinterpret_cast<T *>(smem_raw) + 1 + c;  // [LD] rows
-    T *const s_psi = s_phi + LD * RS;                            // [LD]
-    T *const s_mu = s_psi + LD * RS;                             // [RD]  mu_phi   (A -> B)
-    T *const s_m = s_mu + RD * RS;                               // [RD]  m        (A -> B)
-    T *const s_ux = s_m + RD * RS;                               // [RD]  u_x      (B -> C)
-    T *const s_mus = s_ux + RD * RS;                             // [RD]  mu*      (D -> E)
-    T *const s_ms = s_mus + RD * RS;                             // [RD]  m*       (D -> E)
-    T *const s_ps = s_ms + RD * RS;                              // [RD]  psi* m*  (D -> E)
-    T *const s_phs = s_ps + RD * RS;                             // [CD]  phi*     (C -> D, E)
-    T *const s_pss = s_phs + CD * RS;                            // [CD]  psi*     (C -> D, E)
-    T *const s_pop = reinterpret_cast<T *>(smem_raw) + (2 * LD + 6 * RD + 2 * CD) * RS + c;
-    const unsigned u_phi = (unsigned)__cvta_generic_to_shared(s_phi);
-    const unsigned u_psi = (unsigned)__cvta_generic_to_shared(s_psi);
+    V *const r_ps = reinterpret_cast<V *>(smem_raw) + 1 + c;  // [LD] (phi^n, psi^n)
+    V *const r_mm = r_ps + LD * RS;                             // [RD] (mu, m)       A -> B
+    V *const r_ms = r_mm + RD * RS;                             // [RD] (mu*, m*)     D -> E
+    V *const r_pp = r_ms + RD * RS;                             // [RD] (psi*, p*)    D -> E
+    V *const r_st = r_pp + RD * RS;                             // [CD] (phi*, psi*)  C -> D, E
+    T *const r_ux = reinterpret_cast<T *>(r_st - 1 - c + CD * RS) + 1 + c;  // [RD] u_x  B -> C
+    T *const s_pop = reinterpret_cast<T *>(smem_raw) + 2 * (LD + 3 * RD + CD) * RS + RD * RS + c;
+    const unsigned u_ps = (unsigned)__cvta_generic_to_shared(r_ps);
     const unsigned u_pop = (unsigned)__cvta_generic_to_shared(s_pop);
 
     const int nx = p.nx, ny = p.ny;
@@ -159,9 +195,9 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     const unsigned xo_b = (unsigned)xo * TB;
     const int yend = min(y0 + seg, ny);  // owned rows [y0, yend)
 
-    // Byte offsets of the asynchronously loaded rows, advanced by one row per
-    // iteration: loader row y0 - 5 + k and the rows rb - 1, rb, rb + 1 around
-    // stage-B row rb = y0 - 9 + k.
+    // Byte offsets of the asynchronously loaded rows, advanced one row per
+    // iteration: loader row y0 - 5 + k and rows rb - 1, rb, rb + 1 around stage-B
+    // row rb = y0 - 9 + k.
     unsigned lo_b = (unsigned)wrapi(y0 - 5, ny) * pitch_b + xg_b;
     unsigned rm_b = (unsigned)wrapi(y0 - 10, ny) * pitch_b;
     unsigned r0_b = (unsigned)wrapi(y0 - 9, ny) * pitch_b;
@@ -174,18 +210,19 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     const char *const psi_in = reinterpret_cast<const char *>(p.psi_in);
     const char *const g_in = reinterpret_cast<const char *>(p.g_in);
 
-    // Issue the asynchronous loads of iteration k: phi^n, psi^n of loader row
-    // y0 - 5 + k, and the pulled populations f_i(x - e_i) of stage-B row y0 - 9 + k.
+    // Asynchronous loads of iteration k: (phi^n, psi^n) of loader row y0 - 5 + k
+    // into the two lanes of the pair ring, and the pulled populations f_i(x - e_i)
+    // of stage-B row y0 - 9 + k.
     auto issue = [&](int k) {
         const int rl = y0 - 5 + k;
         if (rl < yend + 5) {
-            const unsigned so = (unsigned)((rl & (LD - 1)) * RS) * TB;
+            const unsigned so = (unsigned)((rl & (LD - 1)) * RS) * (2 * TB);
             if (TB == 8) {
-                cp8<0>(u_phi + so, phi_in + lo_b);
-                cp8<0>(u_psi + so, psi_in + lo_b);
+                cp8<0>(u_ps + so, phi_in + lo_b);
+                cp8<8>(u_ps + so, psi_in + lo_b);
             } else {
-                cp4<0>(u_phi + so, phi_in + lo_b);
-                cp4<0>(u_psi + so, psi_in + lo_b);
+                cp4<0>(u_ps + so, phi_in + lo_b);
+                cp4<4>(u_ps + so, psi_in + lo_b);
             }
         }
         const int rb = y0 - 9 + k;
@@ -213,11 +250,10 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         adv(rp_b);
     };
 
-    WinFull<T> wPhiA, wPsiA, wMuB, wMB, wPhsD, wPssD;
-    WinLap<T> wMusE, wMsE, wPssE, wPsE;
-    wPhiA.reset(); wPsiA.reset(); wMuB.reset(); wMB.reset(); wPhsD.reset(); wPssD.reset();
-    wMusE.reset(); wMsE.reset(); wPssE.reset(); wPsE.reset();
-    T gpx1 = 0, gpy1 = 0, gpx2 = 0, gpy2 = 0;  // grad psi from A, 1 and 2 iterations old
+    Win2<V> wA, wB, wD;           // (phi, psi), (mu, m), (phi*, psi*)
+    WinLap2<V> wEm, wEp;          // (mu*, m*), (psi*, p*)
+    wA.reset(); wB.reset(); wD.reset(); wEm.reset(); wEp.reset();
+    V gps1 = vsplat(T(0)), gps2 = vsplat(T(0));  // grad psi (x, y) from A, 1 and 2 iterations old
     T ux1 = 0, ux2 = 0, uy1 = 0, uy2 = 0, uy3 = 0;  // own u from B, 1..3 iterations old
 
     const T a = p.a, b = p.b, B0 = p.B0, B1 = p.B1;
@@ -235,26 +271,21 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         __syncthreads();
         issue(i + 2);
 
-        // ---- E: phi^{n+1}, psi^{n+1} at row y0 - 15 + i --------------------------
+        // ---- E: phi^{n+1} (Eq. 18), psi^{n+1} (Eq. 19 + source, sink), row y0 - 15 + i
         {
             const int r = y0 - 15 + i;   // output row; pushes row r + 1
             if ((!GUARD || i >= 13) && inE) {
-                const T *M1 = s_mus + ((r + 1) & (RD - 1)) * RS;
-                const T *N1 = s_ms + ((r + 1) & (RD - 1)) * RS;
-                const T *P1 = s_ps + ((r + 1) & (RD - 1)) * RS;
-                const T *C1 = s_pss + ((r + 1) & (CD - 1)) * RS;
-                const T lmu = wMusE.push(M1[0], M1[-1], M1[1]);
-                const T mc = wMsE.c0;
-                const T lm = wMsE.push(N1[0], N1[-1], N1[1]);
-                const T psc = wPssE.c0;
-                const T lps = wPssE.push(C1[0], C1[-1], C1[1]);
-                const T lp = wPsE.push(P1[0], P1[-1], P1[1]);
+                const V *M1 = r_ms + ((r + 1) & (RD - 1)) * RS;
+                const V *P1 = r_pp + ((r + 1) & (RD - 1)) * RS;
+                const V mc = wEm.c0, pc = wEp.c0;            // (mu*, m*), (psi*, p*) at r
+                const V lm = wEm.push(M1[0], M1[-1], M1[1]);  // (lap mu*, lap m*)
+                const V lp = wEp.push(P1[0], P1[-1], P1[1]);  // (lap psi*, lap p*)
                 if (!GUARD || r >= y0) {
-                    const T phs = s_phs[(r & (CD - 1)) * RS];
-                    // Eq. (18): phi* + M lap mu*
-                    const T phi_new = phs + p.M * lmu;
-                    // Eq. (19): div(D psi grad mu_psi) in the log-free form
-                    const T div = lps + T(0.5) * ((psc * lm + lp) - mc * lps);
+                    const T phs = r_st[(r & (CD - 1)) * RS].x;
+                    const T phi_new = phs + p.M * lm.x;
+                    // lap psi + (psi lap m + lap(psi m) - m lap psi) / 2
+                    const T psc = pc.x;
+                    const T div = lp.x + T(0.5) * ((psc * lm.y + lp.y) - mc.y * lp.x);
                     T src = T(0);
                     if (p.theta) {
                         const uint32_t w = p.theta[r * p.theta_words + (xo >> 5)];
@@ -267,138 +298,138 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 }
             }
         }
-        // ---- D: mu*, m*, p* at row y0 - 13 + i -----------------------------------
+        // ---- D: mu*, m*, p* at row y0 - 13 + i (Eq. 3 on phi*, psi*; Eq. 5) ----
         {
             const int r = y0 - 13 + i;
             if ((!GUARD || (i >= 10 && r < yend + 1)) && inD) {
-                const T *F1 = s_phs + ((r + 1) & (CD - 1)) * RS;
-                const T *S1 = s_pss + ((r + 1) & (CD - 1)) * RS;
-                T px, py, plap, ph, cx, cy, cs;
-                wPhsD.push(F1[0], F1[-1], F1[1], px, py, plap, ph);
-                wPssD.push_grad(S1[0], S1[-1], S1[1], cx, cy, cs);
+                const V *S1 = r_st + ((r + 1) & (CD - 1)) * RS;
+                V gx, gy, lap, mid;
+                wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);  // lanes: phi*, psi*
                 if (!GUARD || i >= 12) {
-                    const T pn = s_phi[(r & (LD - 1)) * RS];  // phi^n for the cubic
-                    const T mus = a * ph + b * (pn * pn * pn) - (B0 + B1 * cs) * plap -
-                                  B1 * (px * cx + py * cy);
-                    const T ms = T(0.5) * B1 * (px * px + py * py);
+                    const T pn = r_ps[(r & (LD - 1)) * RS].x;  // phi^n for the cubic
+                    const T mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
+                                  B1 * (gx.x * gx.y + gy.x * gy.y);
+                    const T ms = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
                     const int so = (r & (RD - 1)) * RS;
-                    s_mus[so] = mus;
-                    s_ms[so] = ms;
-                    s_ps[so] = cs * ms;
+                    r_ms[so] = vmake(mus, ms);
+                    r_pp[so] = vmake(mid.y, mid.y * ms);
                 }
             }
         }
-        // ---- C: phi*, psi* at row y0 - 11 + i ------------------------------------
+        // ---- C: phi*, psi* at row y0 - 11 + i (donor-cell fluxes, Eqs. 16-17) ----
         {
             const int r = y0 - 11 + i;
             if ((!GUARD || (i >= 9 && r < yend + 2)) && inC) {
-                const T *P = s_phi + (r & (LD - 1)) * RS, *Q = s_psi + (r & (LD - 1)) * RS;
-                const T *Pn = s_phi + ((r + 1) & (LD - 1)) * RS, *Qn = s_psi + ((r + 1) & (LD - 1)) * RS;
-                const T *Ps = s_phi + ((r - 1) & (LD - 1)) * RS, *Qs = s_psi + ((r - 1) & (LD - 1)) * RS;
-                const T *U = s_ux + (r & (RD - 1)) * RS;
+                const V *Q = r_ps + (r & (LD - 1)) * RS;
+                const V QN = r_ps[((r + 1) & (LD - 1)) * RS], QS = r_ps[((r - 1) & (LD - 1)) * RS];
+                const T *U = r_ux + (r & (RD - 1)) * RS;
                 const T uxc = ux2;
                 const T ue = T(0.5) * (uxc + U[1]);
                 const T uw = T(0.5) * (U[-1] + uxc);
                 const T un = T(0.5) * (uy2 + uy1);
                 const T us = T(0.5) * (uy3 + uy2);
-                const T P0 = P[0], PE = P[1], PW = P[-1], PN = Pn[0], PS_ = Ps[0];
-                const T C0 = Q[0], CE = Q[1], CW = Q[-1], CN = Qn[0], CS = Qs[0];
-                const bool pe = ue > T(0), pw = uw > T(0), pn = un > T(0), ps = us > T(0);
-                const T fe = ue * (pe ? P0 : PE), fw = uw * (pw ? PW : P0);
-                const T fn = un * (pn ? P0 : PN), fs = us * (ps ? PS_ : P0);
-                const T ge = ue * (pe ? C0 : CE), gw = uw * (pw ? CW : C0);
-                const T gn = un * (pn ? C0 : CN), gs = us * (ps ? CS : C0);
-                const int so = (r & (CD - 1)) * RS;
-                s_phs[so] = P0 - ((fe - fw) + (fn - fs));
-                s_pss[so] = C0 - ((ge - gw) + (gn - gs));
+                const V Q0 = Q[0], QE = Q[1], QW = Q[-1];
+                // face flux = u_f * upwind value, both fields of the pair at once
+                const V fe = vsplat(ue) * (ue > T(0) ? Q0 : QE);
+                const V fw = vsplat(uw) * (uw > T(0) ? QW : Q0);
+                const V fn = vsplat(un) * (un > T(0) ? Q0 : QN);
+                const V fs = vsplat(us) * (us > T(0) ? QS : Q0);
+                r_st[(r & (CD - 1)) * RS] = Q0 - ((fe - fw) + (fn - fs));
             }
         }
-        // ---- B: force, moments, collision at row y0 - 9 + i -----------------------
+        // ---- B: force (Eq. 14), moments (Eq. 11), collision (Eqs. 10, 12, 13) ----
         {
             const int r = y0 - 9 + i;
             T ux = T(0), uy = T(0);
             if ((!GUARD || (i >= 4 && r < yend + 3)) && inB) {
-                const T *M1 = s_mu + ((r + 1) & (RD - 1)) * RS;
-                const T *N1 = s_m + ((r + 1) & (RD - 1)) * RS;
-                T mx, my, mc, nx_, ny_, nc;
-                wMuB.push_grad(M1[0], M1[-1], M1[1], mx, my, mc);
-                wMB.push_grad(N1[0], N1[-1], N1[1], nx_, ny_, nc);
+                const V *M1 = r_mm + ((r + 1) & (RD - 1)) * RS;
+                V gx, gy, mid;
+                wB.push_grad(M1[0], M1[-1], M1[1], gx, gy, mid);  // lanes: mu, m
                 if (!GUARD || i >= 6) {
-                    const int sr = (r & (LD - 1)) * RS;
-                    const T ph = s_phi[sr], ps = s_psi[sr];
-                    // Eq. (14) with psi grad mu_psi = grad psi + psi grad m
-                    T Fx = -ph * mx - (gpx2 + ps * nx_);
-                    T Fy = -ph * my - (gpy2 + ps * ny_);
-                    if (p.flags & LBD_BODY_FORCE) {
-                        Fx += p.fx;
-                        Fy += p.fy;
-                    }
+                    const V pp = r_ps[(r & (LD - 1)) * RS];  // (phi, psi) at r
+                    // F = -phi grad mu - (grad psi + psi grad m); lanes x, y
+                    V F = vfma(vsplat(-pp.x), vmake(gx.x, gy.x),
+                               vfma(vsplat(-pp.y), vmake(gx.y, gy.y), vsplat(T(0)) - gps2));
+                    if (p.flags & LBD_BODY_FORCE) F = F + vmake(p.fx, p.fy);
                     const T *G = s_pop + (i % PS) * 9 * NT;
-                    const T g0 = G[0], g1 = G[NT], g2 = G[2 * NT], g3 = G[3 * NT], g4 = G[4 * NT];
-                    const T g5 = G[5 * NT], g6 = G[6 * NT], g7 = G[7 * NT], g8 = G[8 * NT];
-                    // Eq. (11) on the deviations g = f - w
-                    const T dn = g0 + ((g1 + g2) + (g3 + g4)) + ((g5 + g6) + (g7 + g8));
-                    const T jx = (g1 - g3) + (g5 - g6) + (g8 - g7);
-                    const T jy = (g2 - g4) + (g5 + g6) - (g7 + g8);
+                    const T g0 = G[0];
+                    const V g12 = vmake(G[NT], G[2 * NT]), g34 = vmake(G[3 * NT], G[4 * NT]);
+                    const V g56 = vmake(G[5 * NT], G[6 * NT]), g78 = vmake(G[7 * NT], G[8 * NT]);
+                    // Eq. (11) on the deviations g = f - w; j = (jx, jy)
+                    const V s1 = (g12 + g34) + (g56 + g78);
+                    const T dn = g0 + (s1.x + s1.y);
+                    const V a13 = g12 - g34;  // (g1 - g3, g2 - g4)
+                    const T jx = a13.x + ((g56.x - g56.y) + (g78.y - g78.x));
+                    const T jy = a13.y + ((g56.x + g56.y) - (g78.x + g78.y));
                     const T n = T(1) + dn;
                     const T inv = T(1) / n;
-                    ux = (jx + T(0.5) * Fx) * inv;
-                    uy = (jy + T(0.5) * Fy) * inv;
+                    const V u = vfma(vsplat(T(0.5)), F, vmake(jx, jy)) * vsplat(inv);
+                    ux = u.x;
+                    uy = u.y;
                     if ((!GUARD || (r >= y0 && r < yend)) && inE) {
-                        // BGK + Guo (Eqs. 10, 12, 13), opposite directions paired:
-                        // post_i = (1-w) g_i + W (K + eu (c1 eu + c2 eF)) +- W (c3 eu + c4 eF)
-                        const T om = p.omega, gk = p.guo, om1 = T(1) - om;
-                        const T usq = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+                        // post_i = (1-w) g_i + W (K + eu (c1 eu + c2 eF)) +- W (c3 eu + c4 eF),
+                        // opposite directions paired; axis pairs (1,3), (2,4) in the lanes of
+                        // one vector, diagonal pairs (5,7), (6,8) in another
+                        const T om = p.omega, gk = p.guo;
+                        const V om1 = vsplat(T(1) - om);
+                        const T usq = ux * ux + uy * uy, uF = ux * F.x + uy * F.y;
                         const T K = om * (dn - T(1.5) * n * usq) - T(3) * gk * uF;
-                        const T c1 = T(4.5) * om * n, c2 = T(9) * gk;
-                        const T c3 = T(3) * om * n, c4 = T(3) * gk;
+                        const V c1 = vsplat(T(4.5) * om * n), c2 = vsplat(T(9) * gk);
+                        const V c3 = vsplat(T(3) * om * n), c4 = vsplat(T(3) * gk);
+                        const V Kv = vsplat(K);
                         char *Go = g_out + ((unsigned)r * pitch_b + xo_b);
 #define LBD_OUT(I) (*reinterpret_cast<T *>(Go + (I) * plane_b))
-                        LBD_OUT(0) = om1 * g0 + T(4.0 / 9.0) * K;
-#define LBD_PAIR(I, J, W, EU, EF)                                       \
-    {                                                                   \
-        const T eu = (EU), eF = (EF);                                   \
-        const T sym = T(W) * (K + eu * (c1 * eu + c2 * eF));            \
-        const T anti = T(W) * (c3 * eu + c4 * eF);                      \
-        LBD_OUT(I) = om1 * g##I + (sym + anti);                         \
-        LBD_OUT(J) = om1 * g##J + (sym - anti);                         \
-    }
-                        LBD_PAIR(1, 3, 1.0 / 9.0, ux, Fx)
-                        LBD_PAIR(2, 4, 1.0 / 9.0, uy, Fy)
-                        LBD_PAIR(5, 7, 1.0 / 36.0, ux + uy, Fx + Fy)
-                        LBD_PAIR(6, 8, 1.0 / 36.0, uy - ux, Fy - Fx)
-#undef LBD_PAIR
+                        LBD_OUT(0) = (T(1) - om) * g0 + T(4.0 / 9.0) * K;
+                        {   // e = (1,0) and (0,1) in the lanes, opposites (-1,0), (0,-1)
+                            const V eu = u, eF = F, W = vsplat(T(1.0 / 9.0));
+                            const V sym = W * vfma(eu, vfma(c1, eu, c2 * eF), Kv);
+                            const V anti = W * vfma(c3, eu, c4 * eF);
+                            const V pos = vfma(om1, g12, sym + anti);
+                            const V neg = vfma(om1, g34, sym - anti);
+                            LBD_OUT(1) = pos.x; LBD_OUT(2) = pos.y;
+                            LBD_OUT(3) = neg.x; LBD_OUT(4) = neg.y;
+                        }
+                        {   // e = (1,1) and (-1,1) in the lanes, opposites (-1,-1), (1,-1)
+                            const V eu = vmake(ux + uy, uy - ux), eF = vmake(F.x + F.y, F.y - F.x);
+                            const V W = vsplat(T(1.0 / 36.0));
+                            const V sym = W * vfma(eu, vfma(c1, eu, c2 * eF), Kv);
+                            const V anti = W * vfma(c3, eu, c4 * eF);
+                            const V pos = vfma(om1, g56, sym + anti);
+                            const V neg = vfma(om1, g78, sym - anti);
+                            LBD_OUT(5) = pos.x; LBD_OUT(6) = pos.y;
+                            LBD_OUT(7) = neg.x; LBD_OUT(8) = neg.y;
+                        }
 #undef LBD_OUT
                     }
                     if (p.flags & LBD_FROZEN_U) {
                         ux = p.ux0;
                         uy = p.uy0;
                     }
-                    s_ux[(r & (RD - 1)) * RS] = ux;
+                    r_ux[(r & (RD - 1)) * RS] = ux;
                 }
             }
             // own-column u history for stage C (rows r-1, r-2, r-3 next iteration)
             uy3 = uy2; uy2 = uy1; uy1 = uy;
             ux2 = ux1; ux1 = ux;
         }
-        // ---- A: mu_phi, m, grad psi at row y0 - 7 + i -----------------------------
+        // ---- A: mu_phi (Eq. 3), m (Eq. 5), grad psi at row y0 - 7 + i -----------
         {
             const int r = y0 - 7 + i;
-            T gx = T(0), gy = T(0);
+            V gp = vsplat(T(0));
             if ((!GUARD || (i >= 1 && r < yend + 4)) && inA) {
-                const T *F1 = s_phi + ((r + 1) & (LD - 1)) * RS;
-                const T *S1 = s_psi + ((r + 1) & (LD - 1)) * RS;
-                T px, py, plap, ph, cs;
-                wPhiA.push(F1[0], F1[-1], F1[1], px, py, plap, ph);
-                wPsiA.push_grad(S1[0], S1[-1], S1[1], gx, gy, cs);
+                const V *F1 = r_ps + ((r + 1) & (LD - 1)) * RS;
+                V gx, gy, lap, mid;
+                wA.push(F1[0], F1[-1], F1[1], gx, gy, lap, mid);  // lanes: phi, psi
+                gp = vmake(gx.y, gy.y);
                 if (!GUARD || i >= 3) {
-                    const int so = (r & (RD - 1)) * RS;
-                    s_mu[so] = a * ph + b * (ph * ph * ph) - (B0 + B1 * cs) * plap -
-                               B1 * (px * gx + py * gy);
-                    s_m[so] = T(0.5) * B1 * (px * px + py * py);
+                    const T ph = mid.x;
+                    const T mu = a * ph + b * (ph * ph * ph) - (B0 + B1 * mid.y) * lap.x -
+                                 B1 * (gx.x * gx.y + gy.x * gy.y);
+                    const T m = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
+                    r_mm[(r & (RD - 1)) * RS] = vmake(mu, m);
                 }
             }
-            gpx2 = gpx1; gpy2 = gpy1; gpx1 = gx; gpy1 = gy;
+            gps2 = gps1; gps1 = gp;
         }
     };
     const std::integral_constant<bool, true> guarded;
