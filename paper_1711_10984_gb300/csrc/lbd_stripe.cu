@@ -250,6 +250,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         adv(rp_b);
     };
 
+    uint32_t theta_w = 0;         // source-mask word of stage E's current row
     Win2<V> wA, wB, wD;           // (phi, psi), (mu, m), (phi*, psi*)
     WinLap2<V> wEm, wEp;          // (mu*, m*), (psi*, p*)
     wA.reset(); wB.reset(); wD.reset(); wEm.reset(); wEp.reset();
@@ -287,16 +288,18 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                     const T psc = pc.x;
                     const T div = lp.x + T(0.5) * ((psc * lm.y + lp.y) - mc.y * lp.x);
                     T src = T(0);
-                    if (p.theta) {
-                        const uint32_t w = p.theta[r * p.theta_words + (xo >> 5)];
-                        if ((w >> (xo & 31)) & 1u) src = A_t;
-                    }
+                    if (p.theta && ((theta_w >> (xo & 31)) & 1u)) src = A_t;
                     const T psi_new = psc + (p.D * div - gamma_t * (psc - p.c0) + src);
                     const unsigned o = (unsigned)r * pitch_b + xo_b;
                     *reinterpret_cast<T *>(phi_out + o) = phi_new;
                     *reinterpret_cast<T *>(psi_out + o) = psi_new;
                 }
             }
+        }
+        // source-mask word of the next output row, loaded one iteration ahead
+        if (p.theta && inE) {
+            const int rn = y0 - 14 + i;
+            theta_w = (rn >= y0 && rn < yend) ? p.theta[rn * p.theta_words + (xo >> 5)] : 0u;
         }
         // ---- D: mu*, m*, p* at row y0 - 13 + i (Eq. 3 on phi*, psi*; Eq. 5) ----
         {
