@@ -12,7 +12,8 @@ independent restatements live here:
 Parity status per function (pins in ``tests/test_oracle_*.py``):
   stencils, equilibrium, Guo forcing, advection, diffusion, source/sink,
   conservation, flat-interface profile, Laplace law, shear-wave decay,
-  Galilean invariance, free-energy density (Table 1 sigma_num): pinned.  The full nonlinear coupled trajectory has no
+  Galilean invariance, free-energy density (Table 1 sigma_num); walls (Poiseuille
+  profile, conservation, mirror equivalence of the FD part): pinned.  The full nonlinear coupled trajectory has no
   printed values to compare with; it is pinned only through the invariants and
   the agreement of the two restatements.
 """
@@ -27,6 +28,7 @@ FROZEN_U = 1
 BODY_FORCE = 2
 LITERAL_ADVECTION = 4
 LITERAL_LOG = 8
+WALLS = 16   # bounce-back plates at y = -1/2 and y = ny - 1/2 (C oracle only)
 
 # Section 2.1 / 3 parameter set used throughout the paper's equilibrium tests.
 PAPER_PARAMS = dict(a=-0.001, b=0.001, B0=0.006, B1=-0.05, M=1.0, D=0.1, tau=1.0,

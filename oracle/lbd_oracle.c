@@ -38,6 +38,15 @@
  *     image; several source disks combine as a union.
  *   - Activity schedule: for t < t_on, A = gamma = 0; afterwards gamma is on
  *     and A(t) = min(A0 (t - t_on), A_max)  (Section 4: A = A0 t, then held).
+ *   - Walls (ORC_WALLS; Section 2.2 refers them to another paper, Section 2.3
+ *     asks for n.grad mu_phi = n.grad mu_c = 0): two resting plates at
+ *     y = -1/2 and y = ny - 1/2, x stays periodic.  LB: halfway bounce-back, a
+ *     population that would stream through a plate returns to its own site
+ *     reversed, f_i(x, t+1) = f*_{-i}(x, t).  FD: every stencil sees the fields
+ *     mirrored across each plate (row -1-k is row k, row ny+k is row ny-1-k),
+ *     so mu_phi, mu_c (and phi, c) have zero normal derivative there; the
+ *     advective flux through a plate face is zero.  Source disks do not wrap
+ *     through the plates.
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,6 +57,7 @@
 #define ORC_BODY_FORCE        2u   /* add the constant body force (fx, fy) to F      */
 #define ORC_LITERAL_ADVECTION 4u   /* product-rule advection exactly as printed      */
 #define ORC_LITERAL_LOG       8u   /* differentiate ln c + 1 + m numerically         */
+#define ORC_WALLS            16u   /* plates at y = -1/2 and y = ny - 1/2            */
 
 typedef struct {
     int32_t nx, ny;
@@ -69,11 +79,17 @@ static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 static const double W[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
                             1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 static const double CS2 = 1.0 / 3.0; /* c_s^2 = e^2/3 with e = 1 */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6}; /* e_OPP[i] = -e_i */
 
 /* periodic index for v in [-n, 2n): every stencil offset here is -1, 0 or +1 */
 static int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+/* row seen by a stencil: periodic, or mirrored across the plates with walls */
+static int row(const orc_params *p, int y) {
+    if (!(p->flags & ORC_WALLS)) return wrap(y, p->ny);
+    return y < 0 ? -1 - y : (y >= p->ny ? 2 * p->ny - 1 - y : y);
+}
 static size_t site(const orc_params *p, int x, int y) {
-    return (size_t)wrap(y, p->ny) * (size_t)p->nx + (size_t)wrap(x, p->nx);
+    return (size_t)row(p, y) * (size_t)p->nx + (size_t)wrap(x, p->nx);
 }
 static size_t nsites(const orc_params *p) { return (size_t)p->nx * (size_t)p->ny; }
 static double *alloc(size_t n) { return (double *)calloc(n ? n : 1, sizeof(double)); }
@@ -208,7 +224,11 @@ static void lb_collide_stream(const orc_params *p, double *f, const double *Fx, 
             for (int i = 0; i < 9; ++i) {
                 double fi = f[(size_t)i * N + s];
                 double post = fi - (fi - feq[i]) / p->tau + Fi[i];
-                fnew[(size_t)i * N + site(p, x + EX[i], y + EY[i])] = post;
+                int yd = y + EY[i];
+                if ((p->flags & ORC_WALLS) && (yd < 0 || yd >= p->ny))
+                    fnew[(size_t)OPP[i] * N + s] = post;   /* bounce-back at a plate */
+                else
+                    fnew[(size_t)i * N + site(p, x + EX[i], yd)] = post;
             }
         }
     memcpy(f, fnew, 9 * N * sizeof(double));
@@ -249,6 +269,9 @@ static void advect(const orc_params *p, const double *g, const double *ux, const
                 size_t l = site(p, lx[k], ly[k]), r = site(p, rx[k], ry[k]);
                 double uf = (k < 2) ? 0.5 * (ux[l] + ux[r]) : 0.5 * (uy[l] + uy[r]);
                 flux[k] = uf * (uf > 0 ? g[l] : g[r]);
+                /* no flux through a plate: north face of the top row, south of row 0 */
+                if ((p->flags & ORC_WALLS) && ((k == 2 && y == p->ny - 1) || (k == 3 && y == 0)))
+                    flux[k] = 0.0;
             }
             /* east - west + north - south */
             out[s] = g[s] - ((flux[0] - flux[1]) + (flux[2] - flux[3]));
@@ -260,8 +283,10 @@ static int in_source(const orc_params *p, int x, int y) {
         double dx = x - p->src[3 * k], dy = y - p->src[3 * k + 1], R = p->src[3 * k + 2];
         while (dx > 0.5 * p->nx) dx -= p->nx;
         while (dx < -0.5 * p->nx) dx += p->nx;
-        while (dy > 0.5 * p->ny) dy -= p->ny;
-        while (dy < -0.5 * p->ny) dy += p->ny;
+        if (!(p->flags & ORC_WALLS)) {
+            while (dy > 0.5 * p->ny) dy -= p->ny;
+            while (dy < -0.5 * p->ny) dy += p->ny;
+        }
         if (dx * dx + dy * dy <= R * R) return 1;
     }
     return 0;
