@@ -58,6 +58,17 @@ extern "C" {
 
 #define LBD_FROZEN_U 1u      /* advection uses the uniform velocity (ux0, uy0)    */
 #define LBD_BODY_FORCE 2u    /* add the constant body force (fx, fy) to F         */
+/* Two resting plates at y = -1/2 and y = ny - 1/2, x stays periodic (the
+ * channel of Section 4; Section 2.2 takes its walls from another paper and
+ * Section 2.3 asks for n.grad mu_phi = n.grad mu_c = 0 there).  LB: halfway
+ * bounce-back, f_i(x, t+1) = f*_{-i}(x, t) for a population that would cross a
+ * plate.  FD: every stencil sees phi, psi and the fields derived from them
+ * mirrored across each plate (row -1-k is row k, row ny+k is row ny-1-k), so
+ * their normal derivatives vanish; no advective flux crosses a plate; source
+ * disks do not wrap through the plates.  Needs ny >= 8; steps run on the
+ * stripe launch shapes (bx 118 or 246); not available to batches or to
+ * lbd_adjoint (LBD_EINVAL). */
+#define LBD_WALLS 16u
 
 #define LBD_MAX_SOURCES 64
 
@@ -77,7 +88,7 @@ typedef struct {
     int64_t t_on;          /* activation step of source and sink                   */
     double fx, fy;         /* body force (LBD_BODY_FORCE)                          */
     double ux0, uy0;       /* frozen advection velocity (LBD_FROZEN_U)             */
-    uint32_t flags;        /* LBD_FROZEN_U | LBD_BODY_FORCE                        */
+    uint32_t flags;        /* LBD_FROZEN_U | LBD_BODY_FORCE | LBD_WALLS            */
     int32_t precision;     /* LBD_FP64 or LBD_FP32                                 */
     int32_t n_src;         /* number of entries of src used (0..LBD_MAX_SOURCES)   */
     int32_t reserved;      /* must be 0                                            */
@@ -140,7 +151,8 @@ int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
 /* Select the launch shape of the step: bx output columns x by output rows per
  * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
  * column per thread, segments of by rows); bx 240: FP32 column-pair kernel
- * with packed FP32x2 arithmetic (needs nx % 4 == 0 and nx >= 264).  Shapes not
+ * with packed FP32x2 arithmetic (needs nx % 4 == 0 and nx >= 264).  With
+ * LBD_WALLS only the stripe shapes are valid.  Shapes not
  * compiled in, or not valid for the context's precision and lattice, return
  * LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
  * kernels agree to rounding. */
@@ -169,7 +181,8 @@ int lbd_autotune(lbd_ctx *ctx, int32_t reps, int32_t *bx, int32_t *by);
  * The upwind directions of the advection and the phi >= 0 mask are those of
  * the forward run.  On return the context holds the state at t0 + nsteps.
  * Device memory: (nsteps/ckpt_every + ckpt_every + 2) states plus 75 doubles
- * per site, allocated for the call.  LBD_FROZEN_U is not supported.
+ * per site, allocated for the call.  LBD_FROZEN_U and LBD_WALLS are not
+ * supported.
  * Synchronises. */
 int lbd_adjoint(lbd_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double ref_x, double *loss,
                 double *dL_dpsi0, double *dL_dB1);

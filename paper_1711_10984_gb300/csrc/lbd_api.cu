@@ -111,11 +111,13 @@ int fail(lbd_ctx *c, int code, const char *fmt, ...) {
 // ---------------------------------------------------------------- kernels
 
 // f_i = f_i^eq(rho, u) of Eq. (12) stored as g_i = f_i - w_i in the pull
-// layout: buffer_i(x) is what site x + e_i reads, so it holds f_i^eq at x + e_i.
+// layout: buffer_i(x) is what site x + e_i reads, so it holds f_i^eq at x + e_i;
+// with walls, a buffer whose reader lies beyond a plate is read back by its own
+// site as the reversed population (bounce-back), so it holds f_{-i}^eq at x.
 template <typename T>
 __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, const double *rho,
                             const double *ux, const double *uy, const double *phi,
-                            const double *psi, T *g, T *phi_o, T *psi_o) {
+                            const double *psi, int walls, T *g, T *phi_o, T *psi_o) {
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
@@ -129,11 +131,17 @@ __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, co
         psi_o[o] = (T)psi[s];
         for (int i = 0; i < 9; ++i) {
             int xs = x + ex[i], ys = y + ey[i];
+            int k = i;  // population stored
+            if (walls && (ys < 0 || ys >= ny)) {
+                xs = x;
+                ys = y;
+                k = i == 0 ? 0 : (i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5);
+            }
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
             const long long q = (long long)ys * nx + xs;
             const double n = rho[q], u = ux[q], v = uy[q];
-            const double eu = ex[i] * u + ey[i] * v, usq = u * u + v * v;
+            const double eu = ex[k] * u + ey[k] * v, usq = u * u + v * v;
             g[i * plane + o] = (T)(w[i] * ((n - 1.0) + n * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
         }
     }
@@ -145,10 +153,11 @@ __global__ void fill_kernel(double *a, long long n, double v) {
         a[s] = v;
 }
 
-// Pre-collision populations f_i(x) = w_i + buffer_i(x - e_i) as dense doubles.
+// Pre-collision populations f_i(x) = w_i + buffer_i(x - e_i) as dense doubles
+// (with walls, w_i + buffer_{-i}(x) where x - e_i lies beyond a plate).
 template <typename T>
-__global__ void populations_kernel(int nx, int ny, long long pitch, long long plane, const T *g,
-                                   double *f) {
+__global__ void populations_kernel(int nx, int ny, long long pitch, long long plane, int walls,
+                                   const T *g, double *f) {
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
@@ -159,9 +168,15 @@ __global__ void populations_kernel(int nx, int ny, long long pitch, long long pl
         const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
         for (int i = 0; i < 9; ++i) {
             int xs = x - ex[i], ys = y - ey[i];
+            int k = i;  // buffer read
+            if (walls && (ys < 0 || ys >= ny)) {
+                xs = x;
+                ys = y;
+                k = i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5;
+            }
             xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
             ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
-            f[i * N + s] = w[i] + (double)g[i * plane + (long long)ys * pitch + xs];
+            f[i * N + s] = w[i] + (double)g[k * plane + (long long)ys * pitch + xs];
         }
     }
 }
@@ -293,7 +308,10 @@ int check_params(lbd_ctx *c, const lbd_grid *gr, const lbd_params *p) {
         return fail(c, LBD_EINVAL, "precision must be LBD_FP64 or LBD_FP32");
     if (p->n_src < 0 || p->n_src > LBD_MAX_SOURCES)
         return fail(c, LBD_EINVAL, "n_src must be in [0, %d]", LBD_MAX_SOURCES);
-    if (p->flags & ~(LBD_FROZEN_U | LBD_BODY_FORCE)) return fail(c, LBD_EINVAL, "unknown flags");
+    if (p->flags & ~(LBD_FROZEN_U | LBD_BODY_FORCE | LBD_WALLS))
+        return fail(c, LBD_EINVAL, "unknown flags");
+    const int ny = gr ? gr->ny : (c ? c->grid.ny : 0);
+    if ((p->flags & LBD_WALLS) && ny < 8) return fail(c, LBD_EINVAL, "walls need ny >= 8");
     for (int k = 0; k < p->n_src; ++k) {
         const lbd_source &s = p->src[k];
         if (!std::isfinite(s.x) || !std::isfinite(s.y) || !(s.R >= 0.0))
@@ -368,10 +386,19 @@ int update_theta(lbd_ctx *c) {
         double y = std::fmod(p.src[k].y, (double)c->grid.ny);
         src[k].x = x < 0 ? x + c->grid.nx : x;
         src[k].y = y < 0 ? y + c->grid.ny : y;
+        if (p.flags & LBD_WALLS) src[k].y = p.src[k].y;  // no periodic image across a plate
         src[k].R = p.src[k].R;
     }
-    CK(c, lbd::launch_theta_mask(c->grid.nx, c->grid.ny, p.n_src, src, c->theta, c->stream));
+    CK(c, lbd::launch_theta_mask(c->grid.nx, c->grid.ny, p.n_src, src, (p.flags & LBD_WALLS) == 0,
+                                 c->theta, c->stream));
     return LBD_OK;
+}
+
+// Whether launch shape t can run this context's steps: compiled in, valid for
+// its precision and lattice, and a stripe shape when the lattice has walls.
+bool tile_ok(const lbd_ctx *c, Tile t) {
+    if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane)) return false;
+    return !(c->params.flags & LBD_WALLS) || t.bx == 118 || t.bx == 246;
 }
 
 int ensure_staging(lbd_ctx *c) {
@@ -629,9 +656,14 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             sms = 1;
         }
         const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
-        if (stripe_ctas < 2LL * sms ||
-            !lbd::tile_valid(c->tile, params->precision == LBD_FP32, grid->nx, c->plane))
+        if (params->flags & LBD_WALLS) {
+            if (!tile_ok(c, c->tile)) {
+                lbd_destroy(c);
+                return LBD_EINVAL;  // too large for the stripe kernel's 32-bit offsets
+            }
+        } else if (stripe_ctas < 2LL * sms || !tile_ok(c, c->tile)) {
             c->tile = Tile{32, 8};
+        }
     }
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
@@ -647,7 +679,15 @@ int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
     if (rc != LBD_OK) return rc;
     if (p->precision != c->params.precision)
         return fail(c, LBD_EINVAL, "precision cannot change after creation");
+    const lbd_params keep = c->params;
     c->params = *p;
+    if ((p->flags & LBD_WALLS) && !tile_ok(c, c->tile)) {
+        c->tile = Tile{118, 64};
+        if (!tile_ok(c, c->tile)) {
+            c->params = keep;
+            return fail(c, LBD_EINVAL, "walls need the stripe kernel, which this lattice exceeds");
+        }
+    }
     CK(c, cudaSetDevice(c->dev));
     return update_theta(c);
 }
@@ -687,11 +727,11 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     if (p.precision == LBD_FP64)
         init_kernel<double><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
-            (double *)c->g[c->cur], (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+            (p.flags & LBD_WALLS) ? 1 : 0, (double *)c->g[c->cur], (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
     else
         init_kernel<float><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
-            (float *)c->g[c->cur], (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+            (p.flags & LBD_WALLS) ? 1 : 0, (float *)c->g[c->cur], (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
     return LBD_OK;
@@ -745,10 +785,12 @@ int lbd_get_populations(lbd_ctx *c, double *f) {
     const int nb = grid_for(c->N);
     if (c->params.precision == LBD_FP64)
         populations_kernel<double><<<nb, 256, 0, c->stream>>>(
-            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const double *)c->g[c->cur], c->pop_staging);
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (c->params.flags & LBD_WALLS) ? 1 : 0,
+            (const double *)c->g[c->cur], c->pop_staging);
     else
         populations_kernel<float><<<nb, 256, 0, c->stream>>>(
-            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const float *)c->g[c->cur], c->pop_staging);
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, (c->params.flags & LBD_WALLS) ? 1 : 0,
+            (const float *)c->g[c->cur], c->pop_staging);
     CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(f, c->pop_staging, 9 * c->N * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
@@ -795,7 +837,7 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
 int lbd_set_tile(lbd_ctx *c, int32_t bx, int32_t by) {
     if (!c) return LBD_EINVAL;
     const Tile t{bx, by};
-    if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane))
+    if (!tile_ok(c, t))
         return fail(c, LBD_EINVAL, "launch shape %dx%d is not available for this precision and lattice",
                     bx, by);
     c->tile = t;
@@ -814,7 +856,7 @@ int lbd_autotune(lbd_ctx *c, int32_t reps, int32_t *bx, int32_t *by) {
     int rc = LBD_OK;
     for (int k = 0; k < lbd::n_tiles() && rc == LBD_OK; ++k) {
         const Tile t = lbd::tile_at(k);
-        if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane)) continue;
+        if (!tile_ok(c, t)) continue;
         // The trial launches read the current buffers and write the others; the
         // buffers are not swapped, so the state and t are unchanged.
         auto launch = [&]() -> cudaError_t {
@@ -911,6 +953,8 @@ int lbd_adjoint(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double ref_x, do
     if (!(ref_x >= 0 && ref_x < c->grid.nx)) return fail(c, LBD_EINVAL, "ref_x outside the lattice");
     if (c->params.flags & LBD_FROZEN_U)
         return fail(c, LBD_EINVAL, "the adjoint is defined for the coupled velocity only");
+    if (c->params.flags & LBD_WALLS)
+        return fail(c, LBD_EINVAL, "the adjoint is defined for periodic lattices only");
     CK(c, cudaSetDevice(c->dev));
     const int64_t K = ckpt_every < nsteps ? ckpt_every : nsteps;
     return c->params.precision == LBD_FP64
@@ -937,7 +981,8 @@ int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params,
     if (!out || !grids || !params || n < 1) return LBD_EINVAL;
     *out = nullptr;
     for (int k = 0; k < n; ++k)
-        if (params[k].precision != params[0].precision) return LBD_EINVAL;
+        if (params[k].precision != params[0].precision || (params[k].flags & LBD_WALLS))
+            return LBD_EINVAL;
     lbd_batch *b = new (std::nothrow) lbd_batch();
     if (!b) return LBD_ENOMEM;
     b->n = n;

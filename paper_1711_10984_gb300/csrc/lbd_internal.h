@@ -99,9 +99,10 @@ bool pair_supported(int nx);
 size_t pair_smem_bytes();
 
 // Fill the source indicator bit mask (words per row = (nx + 31) / 32) for the
-// disks (x, y, R) with the exact inclusive double-precision test.
-cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, uint32_t *mask,
-                              cudaStream_t s);
+// disks (x, y, R) with the exact inclusive double-precision test, periodic in
+// x and, if wrap_y, in y.
+cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, bool wrap_y,
+                              uint32_t *mask, cudaStream_t s);
 
 // Activity at step t (Section 4): off before t_on, then the sink rate gamma and
 // the source strength A(t) = min(A0 (t - t_on), A_max).

@@ -56,10 +56,11 @@ struct Stencil {
 };
 
 // Source indicator Theta(R - |r - r_P|), Section 2.1: inclusive, periodic minimum
-// image, union of the disks.  Evaluated once per parameter set (in double, with
+// image (in x only when plates bound the lattice in y), union of the disks.  Evaluated once per parameter set (in double, with
 // no contraction into FMAs so that the boundary test is the plain IEEE one);
 // the step kernel reads one bit per site.
-__global__ void theta_mask_kernel(int nx, int ny, int n_src, SourceList src, uint32_t *mask) {
+__global__ void theta_mask_kernel(int nx, int ny, int n_src, SourceList src, int wrap_y,
+                                  uint32_t *mask) {
     const int words = (nx + 31) / 32;
     const long long total = (long long)words * ny;
     for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
@@ -70,7 +71,9 @@ __global__ void theta_mask_kernel(int nx, int ny, int n_src, SourceList src, uin
             for (int k = 0; k < n_src; ++k) {
                 double dx = (double)(x0 + b) - src.s[k].x, dy = (double)y - src.s[k].y;
                 if (dx > 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
-                if (dy > 0.5 * ny) dy -= ny; else if (dy < -0.5 * ny) dy += ny;
+                if (wrap_y) {
+                    if (dy > 0.5 * ny) dy -= ny; else if (dy < -0.5 * ny) dy += ny;
+                }
                 if (__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <=
                     __dmul_rn(src.s[k].R, src.s[k].R)) {
                     bits |= 1u << b;
@@ -109,7 +112,14 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
     const long long pitch = p.pitch;
 
     for (int k = tid; k < W5; k += NT) s_gx[k] = pmod(x0 - HALO + k, nx);
-    for (int k = tid; k < H5; k += NT) s_gy[k] = pmod(y0 - HALO + k, ny);
+    // rows beyond a plate are read mirrored (walls: y = -1/2 and ny - 1/2)
+    const bool walls = (p.flags & LBD_WALLS) != 0;
+    for (int k = tid; k < H5; k += NT) {
+        const int y = y0 - HALO + k;
+        // (rows past the last tile's halo are never used; clamped to stay in bounds)
+        s_gy[k] = !walls ? pmod(y, ny)
+                         : min(max(y < 0 ? -1 - y : (y >= ny ? 2 * ny - 1 - y : y), 0), ny - 1);
+    }
     __syncthreads();
 
     // ---- stage 0: phi^n, psi^n on R5 -------------------------------------
@@ -166,6 +176,20 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
         g[6] = G[6 * P_ + rym + gxp];       // e = (-1, 1)
         g[7] = G[7 * P_ + ryp + gxp];       // e = (-1,-1)
         g[8] = G[8 * P_ + ryp + gxm];       // e = ( 1,-1)
+        if (walls) {  // halfway bounce-back: what would come through a plate is
+                      // the site's own reversed post-collision population
+            const int yr = y0 - HALO + yc;
+            if (yr == 0) {
+                g[2] = G[4 * P_ + ry0 + gx0];
+                g[5] = G[7 * P_ + ry0 + gx0];
+                g[6] = G[8 * P_ + ry0 + gx0];
+            }
+            if (yr == ny - 1) {
+                g[4] = G[2 * P_ + ry0 + gx0];
+                g[7] = G[5 * P_ + ry0 + gx0];
+                g[8] = G[6 * P_ + ry0 + gx0];
+            }
+        }
         // Eq. (11) on the deviations: n = 1 + sum g, sum f e = sum g e.
         dn = g[0] + ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
         const T jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
@@ -364,13 +388,13 @@ constexpr Tile kTiles[] = {{32, 8},   {32, 16},  {64, 8},    {32, 32},  {64, 16}
 
 }  // namespace
 
-cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, uint32_t *mask,
-                              cudaStream_t s) {
+cudaError_t launch_theta_mask(int nx, int ny, int n_src, const lbd_source *src, bool wrap_y,
+                              uint32_t *mask, cudaStream_t s) {
     SourceList l;
     for (int k = 0; k < n_src; ++k) l.s[k] = src[k];
     const long long words = (long long)((nx + 31) / 32) * ny;
     const int nb = (int)((words + 255) / 256 < 4096 ? (words + 255) / 256 : 4096);
-    theta_mask_kernel<<<nb, 256, 0, s>>>(nx, ny, n_src, l, mask);
+    theta_mask_kernel<<<nb, 256, 0, s>>>(nx, ny, n_src, l, wrap_y ? 1 : 0, mask);
     return cudaGetLastError();
 }
 

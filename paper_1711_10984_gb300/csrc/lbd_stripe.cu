@@ -26,6 +26,13 @@
 // Laplacian link weights).  The surfactant divergence of Eq. (19),
 // sum_j (2/3 or 1/6)[(psi_j - psi) + (psi + psi_j)(m_j - m)/2], is evaluated
 // through the identity  lap psi + (psi lap m + lap(psi m) - m lap psi) / 2.
+//
+// With plates at y = -1/2 and ny - 1/2 (WALLS): the loader reads rows beyond a
+// plate mirrored, so stage A produces mirrored mu, m there; the pulls at rows 0
+// and ny - 1 take the site's own reversed population (halfway bounce-back); the
+// advective flux through a plate face is zero; stages D and E, whose inputs come
+// from the LB velocity, never use rows beyond a plate: at row 0 the window's
+// row -1 is set to row 0, at row ny - 1 row ny is read as row ny - 1.
 #include <cstdint>
 #include <type_traits>
 
@@ -108,6 +115,8 @@ struct Win2 {
         mid = c0;
         cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
     }
+    // the row below the current one is the current row mirrored (a plate between)
+    __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; dm = d0; }
     __device__ __forceinline__ void push_grad(V c, V l, V r, V &gx, V &gy, V &mid) {
         using S = decltype(cm.x);
         const V t = vfma(c, vsplat(S(-2)), l + r);
@@ -131,6 +140,7 @@ struct WinLap2 {
         cm = c0; c0 = c; tm = t0; t0 = t;
         return lap;
     }
+    __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; }
 };
 
 template <typename T>
@@ -159,7 +169,7 @@ __device__ __forceinline__ void cp8(unsigned dst, const void *src) {
     asm volatile("cp.async.ca.shared.global [%0+%2], [%1], 8;\n" ::"r"(dst), "l"(src), "n"(OFF));
 }
 
-template <typename T, int NT>
+template <typename T, int NT, bool WALLS>
 __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, const int y0,
                                             const int seg, const T A_t, const T gamma_t,
                                             unsigned char *smem_raw) {
@@ -217,12 +227,15 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         const int rl = y0 - 5 + k;
         if (rl < yend + 5) {
             const unsigned so = (unsigned)((rl & (LD - 1)) * RS) * (2 * TB);
+            unsigned lo = lo_b;
+            if (WALLS)  // rows beyond a plate are the mirrored rows inside
+                lo = (unsigned)(rl < 0 ? -1 - rl : (rl >= ny ? 2 * ny - 1 - rl : rl)) * pitch_b + xg_b;
             if (TB == 8) {
-                cp8<0>(u_ps + so, phi_in + lo_b);
-                cp8<8>(u_ps + so, psi_in + lo_b);
+                cp8<0>(u_ps + so, phi_in + lo);
+                cp8<8>(u_ps + so, psi_in + lo);
             } else {
-                cp4<0>(u_ps + so, phi_in + lo_b);
-                cp4<4>(u_ps + so, psi_in + lo_b);
+                cp4<0>(u_ps + so, phi_in + lo);
+                cp4<4>(u_ps + so, psi_in + lo);
             }
         }
         const int rb = y0 - 9 + k;
@@ -230,17 +243,34 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
             const unsigned d = u_pop + (unsigned)((k % PS) * 9 * NT) * TB;
             constexpr int P = NT * (int)sizeof(T);
 #define LBD_PULL(I, ROW, COL)                                                              \
-    if (TB == 8) cp8<(I) * P>(d, g_in + ((I) * plane_b + ROW + COL));                     \
-    else cp4<(I) * P>(d, g_in + ((I) * plane_b + ROW + COL));
+    if (TB == 8) cp8<(I) * P>(d, g_in + ((I) * plane_b + (ROW) + (COL)));                 \
+    else cp4<(I) * P>(d, g_in + ((I) * plane_b + (ROW) + (COL)));
+#define LBD_PULL_FROM(I, J, ROW, COL)                                                      \
+    if (TB == 8) cp8<(I) * P>(d, g_in + ((J) * plane_b + (ROW) + (COL)));                 \
+    else cp4<(I) * P>(d, g_in + ((J) * plane_b + (ROW) + (COL)));
             LBD_PULL(0, r0_b, xg_b)  // e = ( 0, 0)
             LBD_PULL(1, r0_b, xm_b)  // e = ( 1, 0) from x - 1
-            LBD_PULL(2, rm_b, xg_b)  // e = ( 0, 1) from y - 1
             LBD_PULL(3, r0_b, xp_b)  // e = (-1, 0) from x + 1
-            LBD_PULL(4, rp_b, xg_b)  // e = ( 0,-1) from y + 1
-            LBD_PULL(5, rm_b, xm_b)  // e = ( 1, 1)
-            LBD_PULL(6, rm_b, xp_b)  // e = (-1, 1)
-            LBD_PULL(7, rp_b, xp_b)  // e = (-1,-1)
-            LBD_PULL(8, rp_b, xm_b)  // e = ( 1,-1)
+            if (WALLS) {
+                // halfway bounce-back: at row 0 the populations with e_y = 1, at
+                // row ny - 1 those with e_y = -1 are the site's own reversed ones
+                const bool bot = rb == 0, top = rb == ny - 1;
+                const unsigned rmw = bot ? r0_b : rm_b, rpw = top ? r0_b : rp_b;
+                LBD_PULL_FROM(2, bot ? 4u : 2u, rmw, xg_b)
+                LBD_PULL_FROM(5, bot ? 7u : 5u, rmw, bot ? xg_b : xm_b)
+                LBD_PULL_FROM(6, bot ? 8u : 6u, rmw, bot ? xg_b : xp_b)
+                LBD_PULL_FROM(4, top ? 2u : 4u, rpw, xg_b)
+                LBD_PULL_FROM(7, top ? 5u : 7u, rpw, top ? xg_b : xp_b)
+                LBD_PULL_FROM(8, top ? 6u : 8u, rpw, top ? xg_b : xm_b)
+            } else {
+                LBD_PULL(2, rm_b, xg_b)  // e = ( 0, 1) from y - 1
+                LBD_PULL(4, rp_b, xg_b)  // e = ( 0,-1) from y + 1
+                LBD_PULL(5, rm_b, xm_b)  // e = ( 1, 1)
+                LBD_PULL(6, rm_b, xp_b)  // e = (-1, 1)
+                LBD_PULL(7, rp_b, xp_b)  // e = (-1,-1)
+                LBD_PULL(8, rp_b, xm_b)  // e = ( 1,-1)
+            }
+#undef LBD_PULL_FROM
 #undef LBD_PULL
         }
         cp_commit();
@@ -276,8 +306,14 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         {
             const int r = y0 - 15 + i;   // output row; pushes row r + 1
             if ((!GUARD || i >= 13) && inE) {
-                const V *M1 = r_ms + ((r + 1) & (RD - 1)) * RS;
-                const V *P1 = r_pp + ((r + 1) & (RD - 1)) * RS;
+                // with plates, row ny mirrors row ny - 1 and row -1 mirrors row 0
+                const int rn = (WALLS && r == ny - 1) ? r : r + 1;
+                const V *M1 = r_ms + (rn & (RD - 1)) * RS;
+                const V *P1 = r_pp + (rn & (RD - 1)) * RS;
+                if (WALLS && r == 0) {
+                    wEm.mirror_below();
+                    wEp.mirror_below();
+                }
                 const V mc = wEm.c0, pc = wEp.c0;            // (mu*, m*), (psi*, p*) at r
                 const V lm = wEm.push(M1[0], M1[-1], M1[1]);  // (lap mu*, lap m*)
                 const V lp = wEp.push(P1[0], P1[-1], P1[1]);  // (lap psi*, lap p*)
@@ -305,8 +341,10 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         {
             const int r = y0 - 13 + i;
             if ((!GUARD || (i >= 10 && r < yend + 1)) && inD) {
-                const V *S1 = r_st + ((r + 1) & (CD - 1)) * RS;
+                const int rn = (WALLS && r == ny - 1) ? r : r + 1;
+                const V *S1 = r_st + (rn & (CD - 1)) * RS;
                 V gx, gy, lap, mid;
+                if (WALLS && r == 0) wD.mirror_below();
                 wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);  // lanes: phi*, psi*
                 if (!GUARD || i >= 12) {
                     const T pn = r_ps[(r & (LD - 1)) * RS].x;  // phi^n for the cubic
@@ -329,8 +367,10 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 const T uxc = ux2;
                 const T ue = T(0.5) * (uxc + U[1]);
                 const T uw = T(0.5) * (U[-1] + uxc);
-                const T un = T(0.5) * (uy2 + uy1);
-                const T us = T(0.5) * (uy3 + uy2);
+                T un = T(0.5) * (uy2 + uy1);
+                T us = T(0.5) * (uy3 + uy2);
+                if (WALLS && r == ny - 1) un = T(0);  // no flux through a plate
+                if (WALLS && r == 0) us = T(0);
                 const V Q0 = Q[0], QE = Q[1], QW = Q[-1];
                 // face flux = u_f * upwind value, both fields of the pair at once
                 const V fe = vsplat(ue) * (ue > T(0) ? Q0 : QE);
@@ -446,11 +486,11 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
-template <typename T, int NT>
+template <typename T, int NT, bool WALLS>
 __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
     stripe_kernel(const StepArgs<T> p, const int seg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stripe_body<T, NT>(p, blockIdx.x * (NT - 10), blockIdx.y * seg, seg, p.A, p.gamma, smem_raw);
+    stripe_body<T, NT, WALLS>(p, blockIdx.x * (NT - 10), blockIdx.y * seg, seg, p.A, p.gamma, smem_raw);
 }
 
 // Batched step: CTAs walk the work list; the arguments of the item's instance
@@ -478,7 +518,7 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
             s_gamma = (T)g;
         }
         __syncthreads();
-        stripe_body<T, NT>(sp, item.x0, item.y0, item.rows, s_A, s_gamma, smem_raw);
+        stripe_body<T, NT, false>(sp, item.x0, item.y0, item.rows, s_A, s_gamma, smem_raw);
         __syncthreads();
     }
 }
@@ -493,31 +533,33 @@ size_t stripe_smem_bytes(int nt) {
     return sizeof(T) * StripeSmem<T>::floats(nt);
 }
 
-template <typename T>
-cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s) {
-    const size_t smem = stripe_smem_bytes<T>(nt);
-    static unsigned long long configured[2] = {0, 0};
+template <typename T, int NT, bool WALLS>
+cudaError_t launch_stripe_as(const StepArgs<T> &a, int seg, cudaStream_t s) {
+    const size_t smem = stripe_smem_bytes<T>(NT);
+    static unsigned long long configured = 0;  // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int which = nt == 128 ? 0 : 1;
     const unsigned long long bit = 1ull << (dev & 63);
-    if (!(configured[which] & bit)) {
-        e = nt == 128 ? cudaFuncSetAttribute(stripe_kernel<T, 128>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                      : cudaFuncSetAttribute(stripe_kernel<T, 256>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(stripe_kernel<T, NT, WALLS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[which] |= bit;
+        configured |= bit;
     }
-    dim3 grid((a.nx + (nt - 10) - 1) / (nt - 10), (a.ny + seg - 1) / seg);
-    if (nt == 128)
-        stripe_kernel<T, 128><<<grid, 128, smem, s>>>(a, seg);
-    else if (nt == 256)
-        stripe_kernel<T, 256><<<grid, 256, smem, s>>>(a, seg);
-    else
-        return cudaErrorInvalidValue;
+    dim3 grid((a.nx + (NT - 10) - 1) / (NT - 10), (a.ny + seg - 1) / seg);
+    stripe_kernel<T, NT, WALLS><<<grid, NT, smem, s>>>(a, seg);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s) {
+    const bool walls = (a.flags & LBD_WALLS) != 0;
+    if (nt == 128) return walls ? launch_stripe_as<T, 128, true>(a, seg, s)
+                                : launch_stripe_as<T, 128, false>(a, seg, s);
+    if (nt == 256) return walls ? launch_stripe_as<T, 256, true>(a, seg, s)
+                                : launch_stripe_as<T, 256, false>(a, seg, s);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

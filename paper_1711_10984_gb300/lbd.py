@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "liblbd.so")
 LBD_OK, LBD_EINVAL, LBD_ENOMEM, LBD_ECUDA = 0, -1, -2, -3
 LBD_ENONFINITE, LBD_EUNSTABLE, LBD_ETIMEOUT = -4, -5, -6
 LBD_FP64, LBD_FP32 = 0, 1
-LBD_FROZEN_U, LBD_BODY_FORCE = 1, 2
+LBD_FROZEN_U, LBD_BODY_FORCE, LBD_WALLS = 1, 2, 16
 LBD_MAX_SOURCES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
