@@ -175,8 +175,7 @@ def ncu_traffic(precision):
 
 
 def time_precision(torch, lbd, autotune, w, prec, steps, warmup, stream, dev_name, barrier):
-    n = w["nx"]
-    sim = lbd.Sim(n, n, precision=prec, sources=w["sources"], stream=stream.cuda_stream,
+    sim = lbd.Sim(w["nx"], w["ny"], precision=prec, sources=w["sources"], stream=stream.cuda_stream,
                   **w["params"])
     sim.set_fields(w["phi"], w["psi"])
     tile = autotune.tune(sim, dev_name)
@@ -343,11 +342,22 @@ def run_ours(args):
     e2e = time_e2e(torch, lbd, w, args.steps, stream)
     batch = time_batch(torch, lbd, min(args.steps, 500), args.warmup)
     adj = time_adjoint(lbd, steps=min(4000, 4 * args.steps)) if rank == 0 else None
+    # walls (bounce-back plates): the same emulsion between plates, and the
+    # channel of Section 4 (512 x 256, one droplet R = 32, tau = 0.6)
+    from paper_1711_10984_gb300 import inputs
+    w_pl = dict(w, params=dict(w["params"], flags=lbd.LBD_WALLS))
+    nw = min(args.steps, 500)
+    rw = time_precision(torch, lbd, autotune, w_pl, lbd.LBD_FP32, nw, args.warmup, stream,
+                        dev_name, barrier)
+    wc = inputs.channel()
+    rc = time_precision(torch, lbd, autotune, wc, lbd.LBD_FP32, nw, args.warmup, stream,
+                        dev_name, barrier)
 
     maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
     t32, t64, te = maxr(r32["total_ms"]), maxr(r64["total_ms"]), maxr(e2e["ms"])
     k32, k64 = maxr(r32["kernel_ms"]), maxr(r64["kernel_ms"])
+    tw, kw, tc = maxr(rw["total_ms"]), maxr(rw["kernel_ms"]), maxr(rc["total_ms"])
     cpu = cpu_baseline(w) if (rank == 0 and world == 1) else None
     if dist:
         dist.destroy_process_group()
@@ -388,6 +398,18 @@ def run_ours(args):
         "fp32_over_fp64_speedup": round(t64 / t32, 2),
         "fp32_drift": r32["drift"],
         "adjoint_forward_cost": adj,
+        "walls": {"workload": "the same 2048x2048 emulsion between bounce-back plates "
+                              "(LBD_WALLS), FP32",
+                  "value": round(whole_job_mlups(N, world, nw, tw), 1),
+                  "unit": "MLUPS", "steps": nw, "tile": rw["tile"],
+                  "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                               "achieved": round(BYTES_PER_SITE[1] * N / (kw / nw * 1e-3) / 1e9, 1),
+                               "frac": round(BYTES_PER_SITE[1] * N / (kw / nw * 1e-3) / 1e9 / hbm,
+                                             4)},
+                  "channel": {"workload": "Section 4 channel: 512x256 between plates, one droplet "
+                                          "R=32, tau=0.6, B1=-0.05, source and sink on, FP32",
+                              "value": round(whole_job_mlups(wc["nx"] * wc["ny"], world, nw, tc), 1),
+                              "unit": "MLUPS", "tile": rc["tile"], "ms_per_step": tc / nw}},
         "batch": {"workload": "256 FP32 single-droplet instances, sides 128-384, radii 15-40, "
                               "B1 and psi amplitude log-uniform, source and sink on",
                   "value": round(world * batch["mlups"], 1), "unit": "MLUPS",

@@ -2,8 +2,8 @@
 
 The timing itself is native (``lbd_autotune`` times every compiled tile shape on
 the context's own state with CUDA events); this module only remembers the
-winner per (device name, nx, ny, precision) in a JSON file so that later runs
-skip the search.
+winner per (device name, nx, ny, precision, walls) in a JSON file so that later
+runs skip the search.
 """
 import json
 import os
@@ -12,8 +12,9 @@ CACHE = os.environ.get("LBD_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json"))
 
 
-def _key(device, nx, ny, precision):
-    return "%s|%dx%d|%s" % (device, nx, ny, "fp64" if precision == 0 else "fp32")
+def _key(device, nx, ny, precision, flags=0):
+    walls = "|walls" if flags & 16 else ""
+    return "%s|%dx%d|%s%s" % (device, nx, ny, "fp64" if precision == 0 else "fp32", walls)
 
 
 def load_cache(path=CACHE):
@@ -35,7 +36,7 @@ def store(key, tile, path=CACHE):
 
 def tune(sim, device, reps=20, path=CACHE, refresh=False):
     """Set sim's tile from the cache, or search, store and set it.  Returns the tile."""
-    key = _key(device, sim.nx, sim.ny, sim.params.precision)
+    key = _key(device, sim.nx, sim.ny, sim.params.precision, sim.params.flags)
     cache = load_cache(path)
     if key in cache and not refresh:
         tile = tuple(cache[key])

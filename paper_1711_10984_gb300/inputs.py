@@ -113,6 +113,19 @@ def single_droplet(n=128, R=20.0, seed=1):
                 sources=[default_source(d, n, n)], droplets=[d])
 
 
+def channel(nx=512, ny=256, R=32.0, B1=-0.05, seed=3):
+    """Section 4's channel: one droplet of radius R at the centre of an nx x ny
+    box between two plates (LBD_WALLS), psi = 0.1 with seeded noise, tau = 0.6,
+    B0 = 0.006, B1 = +-0.05; sink gamma = 1.5e-3 and the source schedule on from
+    the start, the source disk inside the droplet at its +x interface."""
+    d = dict(x=nx / 2, y=ny / 2, R=R, psi_mean=0.1, noise=0.01, gx=0.0)
+    phi, psi = droplet_fields(nx, ny, [d], seed=seed, B1=B1)
+    params = dict(PAPER, B1=B1, tau=0.6, M=1.0, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4,
+                  t_on=0, flags=16)
+    return dict(nx=nx, ny=ny, phi=phi, psi=psi, params=params,
+                sources=[default_source(d, nx, ny)], droplets=[d])
+
+
 def two_droplets(nx=512, ny=256, R=25.0, sep=80.0, offset=0.0, seed=2):
     """Two droplets R on nx x ny, centres (nx/2 -+ sep/2, ny/2 -+ offset/2), each
     with a psi ramp pointing at its partner of seeded amplitude."""
