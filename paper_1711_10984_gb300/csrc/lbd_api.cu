@@ -351,12 +351,13 @@ StepArgs<T> make_args(const lbd_ctx *c, int cur = -1) {
     a.omega = (T)(1.0 / p.tau);
     a.guo = (T)(1.0 - 0.5 / p.tau);
     a.c0 = (T)p.c0;
-    a.fx = (T)p.fx;
-    a.fy = (T)p.fy;
+    // zero unless LBD_BODY_FORCE: the stripe kernel adds (fx, fy) unconditionally
+    a.fx = (p.flags & LBD_BODY_FORCE) ? (T)p.fx : T(0);
+    a.fy = (p.flags & LBD_BODY_FORCE) ? (T)p.fy : T(0);
     a.ux0 = (T)p.ux0;
     a.uy0 = (T)p.uy0;
     a.flags = p.flags;
-    a.theta = p.n_src > 0 ? c->theta : nullptr;
+    a.theta = c->theta;  // always valid (all zero without sources)
     a.theta_words = (a.nx + 31) / 32;
     return a;
 }

@@ -31,8 +31,8 @@ struct StepArgs {
     T gamma, c0, A;                    // activity at this step
     T fx, fy, ux0, uy0;
     uint32_t flags;
-    // Source indicator Theta as a bit mask: bit (x & 31) of word y*theta_words + x/32;
-    // nullptr when there is no source.
+    // Source indicator Theta as a bit mask: bit (x & 31) of word y*theta_words + x/32
+    // (all zero when there is no source).
     const uint32_t *theta;
     int theta_words;
     // Activity schedule, used by the batched kernel, which reads the step count

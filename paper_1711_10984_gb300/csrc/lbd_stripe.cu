@@ -32,7 +32,7 @@
 // and ny - 1 take the site's own reversed population (halfway bounce-back); the
 // advective flux through a plate face is zero; stages D and E, whose inputs come
 // from the LB velocity, never use rows beyond a plate: at row 0 the window's
-// row -1 is set to row 0, at row ny - 1 row ny is read as row ny - 1.
+// row -1 is set to row 0, at row ny - 1 the window pushes its own row again.
 #include <cstdint>
 #include <type_traits>
 
@@ -42,8 +42,9 @@ namespace lbd {
 namespace {
 
 constexpr int LD = 16;  // rows in the (phi^n, psi^n) ring
-constexpr int RD = 4;   // rows in the (mu, m), u_x, (mu*, m*), (psi*, p*) rings
-constexpr int CD = 8;   // rows in the (phi*, psi*) ring
+constexpr int RD = 4;   // rows in the u_x ring
+constexpr int RM = 2;   // rows in the (mu, m), (mu*, m*), (psi*, p*) rings
+constexpr int CD = 2;   // rows in the (phi*, psi*) ring
 constexpr int PS = 3;   // population staging depth (rows in flight)
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -90,6 +91,10 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
     return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
 __device__ __forceinline__ double2 vsplat(double s) { return make_double2(s, s); }
+
+// correctly rounded reciprocal (the same value as 1 / x)
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return 1.0 / x; }
 __device__ __forceinline__ double2 vmake(double a, double b) { return make_double2(a, b); }
 
 // Stencil history of one column for a pair of fields: rows r-1 and r are kept in
@@ -117,6 +122,17 @@ struct Win2 {
     }
     // the row below the current one is the current row mirrored (a plate between)
     __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; dm = d0; }
+    // push(r+1) where row r+1 is row r mirrored (a plate above): the same values
+    // as pushing row r's data again, taken from the window instead of shared memory
+    __device__ __forceinline__ void push_mirror(V &gx, V &gy, V &lap, V &mid) {
+        using S = decltype(cm.x);
+        gx = vfma(d0, vsplat(S(4)), dm + d0) * vsplat(S(1.0 / 12.0));
+        gy = vfma(c0 - cm, vsplat(S(0.5)), (t0 - tm) * vsplat(S(1.0 / 12.0)));
+        lap = vfma(t0, vsplat(S(2.0 / 3.0)),
+                   vfma(tm + t0, vsplat(S(1.0 / 6.0)), (c0 - c0) - (c0 - cm)));
+        mid = c0;
+        cm = c0; tm = t0; dm = d0;
+    }
     __device__ __forceinline__ void push_grad(V c, V l, V r, V &gx, V &gy, V &mid) {
         using S = decltype(cm.x);
         const V t = vfma(c, vsplat(S(-2)), l + r);
@@ -141,6 +157,13 @@ struct WinLap2 {
         return lap;
     }
     __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; }
+    __device__ __forceinline__ V push_mirror() {
+        using S = decltype(cm.x);
+        const V lap = vfma(t0, vsplat(S(2.0 / 3.0)),
+                           vfma(tm + t0, vsplat(S(1.0 / 6.0)), (c0 - c0) - (c0 - cm)));
+        cm = c0; tm = t0;
+        return lap;
+    }
 };
 
 template <typename T>
@@ -149,7 +172,7 @@ struct StripeSmem {
     // padded by one column on each side so the x-neighbours of every thread are in
     // bounds; then the population staging.
     static constexpr size_t floats(int nt) {
-        return (size_t)(nt + 2) * (2 * (LD + RD + RD + RD + CD) + RD) + (size_t)nt * PS * 9;
+        return (size_t)(nt + 2) * (2 * (LD + RM + RM + RM + CD) + RD) + (size_t)nt * PS * 9;
     }
 };
 
@@ -179,11 +202,11 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     // this thread's element in slot 0 of each ring (x-neighbours at -1, +1)
     V *const r_ps = reinterpret_cast<V *>(smem_raw) + 1 + c;  // [LD] (phi^n, psi^n)
     V *const r_mm = r_ps + LD * RS;                             // [RD] (mu, m)       A -> B
-    V *const r_ms = r_mm + RD * RS;                             // [RD] (mu*, m*)     D -> E
-    V *const r_pp = r_ms + RD * RS;                             // [RD] (psi*, p*)    D -> E
-    V *const r_st = r_pp + RD * RS;                             // [CD] (phi*, psi*)  C -> D, E
+    V *const r_ms = r_mm + RM * RS;                             // [RD] (mu*, m*)     D -> E
+    V *const r_pp = r_ms + RM * RS;                             // [RD] (psi*, p*)    D -> E
+    V *const r_st = r_pp + RM * RS;                             // [CD] (phi*, psi*)  C -> D
     T *const r_ux = reinterpret_cast<T *>(r_st - 1 - c + CD * RS) + 1 + c;  // [RD] u_x  B -> C
-    T *const s_pop = reinterpret_cast<T *>(smem_raw) + 2 * (LD + 3 * RD + CD) * RS + RD * RS + c;
+    T *const s_pop = reinterpret_cast<T *>(smem_raw) + 2 * (LD + 3 * RM + CD) * RS + RD * RS + c;
     const unsigned u_ps = (unsigned)__cvta_generic_to_shared(r_ps);
     const unsigned u_pop = (unsigned)__cvta_generic_to_shared(s_pop);
 
@@ -196,10 +219,11 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     const unsigned xg_b = (unsigned)xg * TB;
     const unsigned xm_b = (unsigned)(xg == 0 ? nx - 1 : xg - 1) * TB;
     const unsigned xp_b = (unsigned)(xg == nx - 1 ? 0 : xg + 1) * TB;
-    const bool inA = c >= 1 && c < NT - 1;
+    // Every thread runs every stage: stage k's results are valid on columns
+    // [k, NT - k) and the columns outside are read only by threads whose own
+    // results are outside the next stage's valid range (the ring rows carry a
+    // padding column on each side, so every read stays inside shared memory).
     const bool inB = c >= 2 && c < NT - 2;
-    const bool inC = c >= 3 && c < NT - 3;
-    const bool inD = c >= 4 && c < NT - 4;
     const int xo = x0 + c - 5;  // output column of this thread
     const bool inE = c >= 5 && c < NT - 5 && xo < nx;
     const unsigned xo_b = (unsigned)xo * TB;
@@ -223,10 +247,10 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     // Asynchronous loads of iteration k: (phi^n, psi^n) of loader row y0 - 5 + k
     // into the two lanes of the pair ring, and the pulled populations f_i(x - e_i)
     // of stage-B row y0 - 9 + k.
-    auto issue = [&](int k) {
+    auto issue = [&](int k, int slot) {  // slot = k % PS
         const int rl = y0 - 5 + k;
         if (rl < yend + 5) {
-            const unsigned so = (unsigned)((rl & (LD - 1)) * RS) * (2 * TB);
+            const unsigned so = (unsigned)(((rl - y0) & (LD - 1)) * RS) * (2 * TB);
             unsigned lo = lo_b;
             if (WALLS)  // rows beyond a plate are the mirrored rows inside
                 lo = (unsigned)(rl < 0 ? -1 - rl : (rl >= ny ? 2 * ny - 1 - rl : rl)) * pitch_b + xg_b;
@@ -240,7 +264,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         }
         const int rb = y0 - 9 + k;
         if (inB && rb >= y0 - 3 && rb < yend + 3) {
-            const unsigned d = u_pop + (unsigned)((k % PS) * 9 * NT) * TB;
+            const unsigned d = u_pop + (unsigned)(slot * 9 * NT) * TB;
             constexpr int P = NT * (int)sizeof(T);
 #define LBD_PULL(I, ROW, COL)                                                              \
     if (TB == 8) cp8<(I) * P>(d, g_in + ((I) * plane_b + (ROW) + (COL)));                 \
@@ -281,6 +305,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     };
 
     uint32_t theta_w = 0;         // source-mask word of stage E's current row
+    T phs_e = T(0);               // phi* of stage E's next row, from stage D's window
     Win2<V> wA, wB, wD;           // (phi, psi), (mu, m), (phi*, psi*)
     WinLap2<V> wEm, wEp;          // (mu*, m*), (psi*, p*)
     wA.reset(); wB.reset(); wD.reset(); wEm.reset(); wEp.reset();
@@ -291,8 +316,9 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     char *const g_out = reinterpret_cast<char *>(p.g_out);
     char *const phi_out = reinterpret_cast<char *>(p.phi_out);
     char *const psi_out = reinterpret_cast<char *>(p.psi_out);
-    issue(0);
-    issue(1);
+    issue(0, 0);
+    issue(1, 1);
+    int ps = 0;  // population staging slot of the current iteration, i % PS
     const int iters = (yend - y0) + 15;
     // One pipeline iteration; with GUARD false (steady state: every stage active,
     // every row written is owned) the row conditions vanish at compile time.
@@ -300,31 +326,36 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         constexpr bool GUARD = decltype(guard_tag)::value;
         cp_wait1();
         __syncthreads();
-        issue(i + 2);
+        issue(i + 2, ps == 0 ? PS - 1 : ps - 1);
 
         // ---- E: phi^{n+1} (Eq. 18), psi^{n+1} (Eq. 19 + source, sink), row y0 - 15 + i
         {
             const int r = y0 - 15 + i;   // output row; pushes row r + 1
             if ((!GUARD || i >= 13) && inE) {
-                // with plates, row ny mirrors row ny - 1 and row -1 mirrors row 0
-                const int rn = (WALLS && r == ny - 1) ? r : r + 1;
-                const V *M1 = r_ms + (rn & (RD - 1)) * RS;
-                const V *P1 = r_pp + (rn & (RD - 1)) * RS;
+                // with plates, row -1 mirrors row 0 and row ny mirrors row ny - 1
+                const V *M1 = r_ms + ((r + 1 - y0) & (RM - 1)) * RS;
+                const V *P1 = r_pp + ((r + 1 - y0) & (RM - 1)) * RS;
                 if (WALLS && r == 0) {
                     wEm.mirror_below();
                     wEp.mirror_below();
                 }
                 const V mc = wEm.c0, pc = wEp.c0;            // (mu*, m*), (psi*, p*) at r
-                const V lm = wEm.push(M1[0], M1[-1], M1[1]);  // (lap mu*, lap m*)
-                const V lp = wEp.push(P1[0], P1[-1], P1[1]);  // (lap psi*, lap p*)
+                V lm, lp;                                     // (lap mu*, lap m*), (lap psi*, lap p*)
+                if (WALLS && r == ny - 1) {
+                    lm = wEm.push_mirror();
+                    lp = wEp.push_mirror();
+                } else {
+                    lm = wEm.push(M1[0], M1[-1], M1[1]);
+                    lp = wEp.push(P1[0], P1[-1], P1[1]);
+                }
                 if (!GUARD || r >= y0) {
-                    const T phs = r_st[(r & (CD - 1)) * RS].x;
+                    const T phs = phs_e;
                     const T phi_new = phs + p.M * lm.x;
                     // lap psi + (psi lap m + lap(psi m) - m lap psi) / 2
                     const T psc = pc.x;
                     const T div = lp.x + T(0.5) * ((psc * lm.y + lp.y) - mc.y * lp.x);
                     T src = T(0);
-                    if (p.theta && ((theta_w >> (xo & 31)) & 1u)) src = A_t;
+                    if ((theta_w >> (xo & 31)) & 1u) src = A_t;
                     const T psi_new = psc + (p.D * div - gamma_t * (psc - p.c0) + src);
                     const unsigned o = (unsigned)r * pitch_b + xo_b;
                     *reinterpret_cast<T *>(phi_out + o) = phi_new;
@@ -333,25 +364,28 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
             }
         }
         // source-mask word of the next output row, loaded one iteration ahead
-        if (p.theta && inE) {
+        if (inE) {
             const int rn = y0 - 14 + i;
             theta_w = (rn >= y0 && rn < yend) ? p.theta[rn * p.theta_words + (xo >> 5)] : 0u;
         }
         // ---- D: mu*, m*, p* at row y0 - 13 + i (Eq. 3 on phi*, psi*; Eq. 5) ----
         {
             const int r = y0 - 13 + i;
-            if ((!GUARD || (i >= 10 && r < yend + 1)) && inD) {
-                const int rn = (WALLS && r == ny - 1) ? r : r + 1;
-                const V *S1 = r_st + (rn & (CD - 1)) * RS;
+            if (!GUARD || (i >= 10 && r < yend + 1)) {
+                const V *S1 = r_st + ((r + 1 - y0) & (CD - 1)) * RS;
                 V gx, gy, lap, mid;
+                phs_e = wD.cm.x;  // phi* at row r - 1: stage E's row in the next iteration
                 if (WALLS && r == 0) wD.mirror_below();
-                wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);  // lanes: phi*, psi*
+                if (WALLS && r == ny - 1)
+                    wD.push_mirror(gx, gy, lap, mid);
+                else
+                    wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);  // lanes: phi*, psi*
                 if (!GUARD || i >= 12) {
-                    const T pn = r_ps[(r & (LD - 1)) * RS].x;  // phi^n for the cubic
+                    const T pn = r_ps[((r - y0) & (LD - 1)) * RS].x;  // phi^n for the cubic
                     const T mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
                                   B1 * (gx.x * gx.y + gy.x * gy.y);
                     const T ms = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
-                    const int so = (r & (RD - 1)) * RS;
+                    const int so = ((r - y0) & (RM - 1)) * RS;
                     r_ms[so] = vmake(mus, ms);
                     r_pp[so] = vmake(mid.y, mid.y * ms);
                 }
@@ -360,10 +394,10 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         // ---- C: phi*, psi* at row y0 - 11 + i (donor-cell fluxes, Eqs. 16-17) ----
         {
             const int r = y0 - 11 + i;
-            if ((!GUARD || (i >= 9 && r < yend + 2)) && inC) {
-                const V *Q = r_ps + (r & (LD - 1)) * RS;
-                const V QN = r_ps[((r + 1) & (LD - 1)) * RS], QS = r_ps[((r - 1) & (LD - 1)) * RS];
-                const T *U = r_ux + (r & (RD - 1)) * RS;
+            if (!GUARD || (i >= 9 && r < yend + 2)) {
+                const V *Q = r_ps + ((r - y0) & (LD - 1)) * RS;
+                const V QN = r_ps[((r + 1 - y0) & (LD - 1)) * RS], QS = r_ps[((r - 1 - y0) & (LD - 1)) * RS];
+                const T *U = r_ux + ((r - y0) & (RD - 1)) * RS;
                 const T uxc = ux2;
                 const T ue = T(0.5) * (uxc + U[1]);
                 const T uw = T(0.5) * (U[-1] + uxc);
@@ -377,24 +411,24 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 const V fw = vsplat(uw) * (uw > T(0) ? QW : Q0);
                 const V fn = vsplat(un) * (un > T(0) ? Q0 : QN);
                 const V fs = vsplat(us) * (us > T(0) ? QS : Q0);
-                r_st[(r & (CD - 1)) * RS] = Q0 - ((fe - fw) + (fn - fs));
+                r_st[((r - y0) & (CD - 1)) * RS] = Q0 - ((fe - fw) + (fn - fs));
             }
         }
         // ---- B: force (Eq. 14), moments (Eq. 11), collision (Eqs. 10, 12, 13) ----
         {
             const int r = y0 - 9 + i;
             T ux = T(0), uy = T(0);
-            if ((!GUARD || (i >= 4 && r < yend + 3)) && inB) {
-                const V *M1 = r_mm + ((r + 1) & (RD - 1)) * RS;
+            if (!GUARD || (i >= 4 && r < yend + 3)) {
+                const V *M1 = r_mm + ((r + 1 - y0) & (RM - 1)) * RS;
                 V gx, gy, mid;
                 wB.push_grad(M1[0], M1[-1], M1[1], gx, gy, mid);  // lanes: mu, m
                 if (!GUARD || i >= 6) {
-                    const V pp = r_ps[(r & (LD - 1)) * RS];  // (phi, psi) at r
+                    const V pp = r_ps[((r - y0) & (LD - 1)) * RS];  // (phi, psi) at r
                     // F = -phi grad mu - (grad psi + psi grad m); lanes x, y
-                    V F = vfma(vsplat(-pp.x), vmake(gx.x, gy.x),
-                               vfma(vsplat(-pp.y), vmake(gx.y, gy.y), vsplat(T(0)) - gps2));
-                    if (p.flags & LBD_BODY_FORCE) F = F + vmake(p.fx, p.fy);
-                    const T *G = s_pop + (i % PS) * 9 * NT;
+                    V F = vmake(fma(-pp.x, gx.x, fma(-pp.y, gx.y, -gps2.x)),
+                                fma(-pp.x, gy.x, fma(-pp.y, gy.y, -gps2.y)));
+                    F = F + vmake(p.fx, p.fy);  // zero unless LBD_BODY_FORCE
+                    const T *G = s_pop + ps * 9 * NT;
                     const T g0 = G[0];
                     const V g12 = vmake(G[NT], G[2 * NT]), g34 = vmake(G[3 * NT], G[4 * NT]);
                     const V g56 = vmake(G[5 * NT], G[6 * NT]), g78 = vmake(G[7 * NT], G[8 * NT]);
@@ -405,7 +439,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                     const T jx = a13.x + ((g56.x - g56.y) + (g78.y - g78.x));
                     const T jy = a13.y + ((g56.x + g56.y) - (g78.x + g78.y));
                     const T n = T(1) + dn;
-                    const T inv = T(1) / n;
+                    const T inv = rcp_rn(n);
                     const V u = vfma(vsplat(T(0.5)), F, vmake(jx, jy)) * vsplat(inv);
                     ux = u.x;
                     uy = u.y;
@@ -448,7 +482,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                         ux = p.ux0;
                         uy = p.uy0;
                     }
-                    r_ux[(r & (RD - 1)) * RS] = ux;
+                    r_ux[((r - y0) & (RD - 1)) * RS] = ux;
                 }
             }
             // own-column u history for stage C (rows r-1, r-2, r-3 next iteration)
@@ -459,8 +493,8 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
         {
             const int r = y0 - 7 + i;
             V gp = vsplat(T(0));
-            if ((!GUARD || (i >= 1 && r < yend + 4)) && inA) {
-                const V *F1 = r_ps + ((r + 1) & (LD - 1)) * RS;
+            if (!GUARD || (i >= 1 && r < yend + 4)) {
+                const V *F1 = r_ps + ((r + 1 - y0) & (LD - 1)) * RS;
                 V gx, gy, lap, mid;
                 wA.push(F1[0], F1[-1], F1[1], gx, gy, lap, mid);  // lanes: phi, psi
                 gp = vmake(gx.y, gy.y);
@@ -469,17 +503,18 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                     const T mu = a * ph + b * (ph * ph * ph) - (B0 + B1 * mid.y) * lap.x -
                                  B1 * (gx.x * gx.y + gy.x * gy.y);
                     const T m = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
-                    r_mm[(r & (RD - 1)) * RS] = vmake(mu, m);
+                    r_mm[((r - y0) & (RM - 1)) * RS] = vmake(mu, m);
                 }
             }
             gps2 = gps1; gps1 = gp;
         }
+        ps = ps == PS - 1 ? 0 : ps + 1;
     };
     const std::integral_constant<bool, true> guarded;
     const std::integral_constant<bool, false> steady;
     const int s1 = (yend - y0) + 9;
     int i = 0;
-    for (; i < 15 && i < iters; ++i) body(guarded, i);
+    for (; i < 16 && i < iters; ++i) body(guarded, i);
 #pragma unroll 2
     for (; i < s1; ++i) body(steady, i);
     for (; i < iters; ++i) body(guarded, i);
