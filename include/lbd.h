@@ -175,13 +175,14 @@ int lbd_autotune(lbd_ctx *ctx, int32_t reps, int32_t *bx, int32_t *by);
  *     L = X_cm(t0 + nsteps) - X_cm(t0),
  * X_cm the x centre of mass of the phi >= 0 region (Section 4), each site at
  * its minimum image about ref_x in [0, nx).  The reverse sweep restores each
- * checkpoint, recomputes its segment and applies the transposed step (in
- * double precision) to give dL/dpsi(t0) (host array of nx*ny doubles, may be
+ * checkpoint, recomputes its segment and applies the transposed step (in the
+ * context's precision; dL/dB1 summed in double) to give dL/dpsi(t0) (host
+ * array of nx*ny doubles, may be
  * NULL) and dL/dB1, B1 the surfactant coupling of B(psi) = B0 + B1 psi.
  * The upwind directions of the advection and the phi >= 0 mask are those of
  * the forward run.  On return the context holds the state at t0 + nsteps.
- * Device memory: (nsteps/ckpt_every + ckpt_every + 2) states plus 75 doubles
- * per site, allocated for the call.  LBD_FROZEN_U and LBD_WALLS are not
+ * Device memory: (nsteps/ckpt_every + ckpt_every + 2) states plus 74 values
+ * of the context's precision and one double per site, allocated for the call.  LBD_FROZEN_U and LBD_WALLS are not
  * supported.
  * Synchronises. */
 int lbd_adjoint(lbd_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double ref_x, double *loss,

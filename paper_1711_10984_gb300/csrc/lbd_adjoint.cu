@@ -9,7 +9,8 @@
 // states of the segment are recomputed and kept, and the step is reversed one
 // at a time.  Reversing a step recomputes its intermediates (gradients,
 // Laplacians, chemical potentials, force, pulled populations, moments,
-// advected fields) in double precision and applies the transposed operators:
+// advected fields) in the step's precision (float for the FP32 form, double for
+// FP64) and applies the transposed operators:
 //   psi update  (Eq. 19, link form)          -> lambda psi*, lambda m*
 //   phi update  (Eq. 18)                     -> lambda mu*, lambda phi*
 //   mu*, m*     (Eq. 3 on phi*, psi*)        -> lambda phi*, lambda psi*, lambda phi^n
@@ -18,7 +19,7 @@
 //   streaming   (pull)                       -> lambda buffer (push)
 //   force       (Eq. 14)                     -> lambda phi, lambda psi, lambda mu, lambda m
 //   mu, m       (Eqs. 3, 5)                  -> lambda phi, lambda psi
-// with dL/dB1 accumulated per site.  The transposes use that the isotropic
+// with dL/dB1 accumulated per site in double.  The transposes use that the isotropic
 // gradient stencil is antisymmetric (G^T = -G) and the Laplacian symmetric.
 // The upwind choices and the phi >= 0 mask of the centroid are taken from the
 // forward state (they are piecewise constant).
@@ -45,19 +46,23 @@ __device__ __forceinline__ Nbr nbr(long long s, int nx, int ny) {
 }
 
 // isotropic D2Q9 stencils on dense arrays
-__device__ __forceinline__ double Gx(const double *A, const Nbr &q) {
-    return (A[q.e] - A[q.w]) / 3.0 + ((A[q.ne] - A[q.nw]) + (A[q.se] - A[q.sw])) / 12.0;
+template <typename R>
+__device__ __forceinline__ R Gx(const R *A, const Nbr &q) {
+    return (A[q.e] - A[q.w]) / R(3.0) + ((A[q.ne] - A[q.nw]) + (A[q.se] - A[q.sw])) / R(12.0);
 }
-__device__ __forceinline__ double Gy(const double *A, const Nbr &q) {
-    return (A[q.n] - A[q.s]) / 3.0 + ((A[q.ne] - A[q.se]) + (A[q.nw] - A[q.sw])) / 12.0;
+template <typename R>
+__device__ __forceinline__ R Gy(const R *A, const Nbr &q) {
+    return (A[q.n] - A[q.s]) / R(3.0) + ((A[q.ne] - A[q.se]) + (A[q.nw] - A[q.sw])) / R(12.0);
 }
-__device__ __forceinline__ double Lap(const double *A, const Nbr &q) {
-    const double c = A[q.c];
-    return (2.0 / 3.0) * ((A[q.e] - c) + (A[q.w] - c) + (A[q.n] - c) + (A[q.s] - c)) +
-           (1.0 / 6.0) * ((A[q.ne] - c) + (A[q.nw] - c) + (A[q.se] - c) + (A[q.sw] - c));
+template <typename R>
+__device__ __forceinline__ R Lap(const R *A, const Nbr &q) {
+    const R c = A[q.c];
+    return (R(2.0) / R(3.0)) * ((A[q.e] - c) + (A[q.w] - c) + (A[q.n] - c) + (A[q.s] - c)) +
+           (R(1.0) / R(6.0)) * ((A[q.ne] - c) + (A[q.nw] - c) + (A[q.se] - c) + (A[q.sw] - c));
 }
 // sum_alpha G_alpha(V_alpha)
-__device__ __forceinline__ double Div(const double *Vx, const double *Vy, const Nbr &q) {
+template <typename R>
+__device__ __forceinline__ R Div(const R *Vx, const R *Vy, const Nbr &q) {
     return Gx(Vx, q) + Gy(Vy, q);
 }
 
@@ -73,126 +78,134 @@ __device__ __forceinline__ int EX(int i) {
 __device__ __forceinline__ int EY(int i) {
     return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
 }
-__device__ __forceinline__ double wgt(int i) {
-    return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+template <typename R>
+__device__ __forceinline__ R wgt(int i) {
+    return i == 0 ? R(4.0) / R(9.0) : (i < 5 ? R(1.0) / R(9.0) : R(1.0) / R(36.0));
 }
 
 // Scalars of one step.
+template <typename R>
 struct AdjPar {
     int nx, ny;
     long long N, pitch, plane;
-    double a, b, B0, B1, M, D, omega, guo, gamma, c0, fx, fy;
+    R a, b, B0, B1, M, D, omega, guo, gamma, c0, fx, fy;
     int body;
 };
 
-// Dense double work arrays of one reversed step.
+// Dense work arrays of one reversed step (R: the step's precision).
+template <typename R>
 struct Work {
     // forward intermediates
-    double *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy, *MU, *MM;
-    double *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *FP, *RHO, *UX, *UY;
-    double *PHS, *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
+    R *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy, *MU, *MM;
+    R *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *FP, *RHO, *UX, *UY;
+    R *PHS, *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
     // adjoints
-    double *Lphi, *Lpsi, *Lbuf;       // of the step output (9 planes for Lbuf)
-    double *Lphi0, *Lpsi0, *Lbuf0;    // of the step input
-    double *LMUS, *LMS, *LPHS, *LPSS, *LUX, *LUY, *LFX, *LFY, *LMU, *LMM;
-    double *T1, *T2, *T3, *T4, *T5, *T6, *T7;  // products for the transposed stencils
-    double *dB1;                                // per-site accumulator of dL/dB1
+    R *Lphi, *Lpsi, *Lbuf;       // of the step output (9 planes for Lbuf)
+    R *Lphi0, *Lpsi0, *Lbuf0;    // of the step input
+    R *LMUS, *LMS, *LPHS, *LPSS, *LUX, *LUY, *LFX, *LFY, *LMU, *LMM;
+    R *T1, *T2, *T3, *T4, *T5, *T6, *T7;  // products for the transposed stencils
+    double *dB1;                           // per-site accumulator of dL/dB1 (double)
 };
 
 // ---- forward intermediates ----------------------------------------------------
-template <typename T>
-__global__ void fwd1(AdjPar p, const T *phi, const T *psi, Work w) {
+template <typename T, typename R>
+__global__ void fwd1(AdjPar<R> p, const T *phi, const T *psi, Work<R> w) {
     LBD_SITES(p.N) {
         const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
         const long long o = (long long)y * p.pitch + x;
-        w.PH[s] = (double)phi[o];
-        w.PS[s] = (double)psi[o];
+        w.PH[s] = (R)phi[o];
+        w.PS[s] = (R)psi[o];
     }
 }
 
-__global__ void fwd2(AdjPar p, Work w) {
+template <typename R>
+__global__ void fwd2(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
-        const double px = Gx(w.PH, q), py = Gy(w.PH, q), lp = Lap(w.PH, q);
-        const double cx = Gx(w.PS, q), cy = Gy(w.PS, q);
-        const double ph = w.PH[s];
+        const R px = Gx(w.PH, q), py = Gy(w.PH, q), lp = Lap(w.PH, q);
+        const R cx = Gx(w.PS, q), cy = Gy(w.PS, q);
+        const R ph = w.PH[s];
         w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
         w.MU[s] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * w.PS[s]) * lp -
                   p.B1 * (px * cx + py * cy);
-        w.MM[s] = 0.5 * p.B1 * (px * px + py * py);
+        w.MM[s] = R(0.5) * p.B1 * (px * px + py * py);
     }
 }
 
-template <typename T>
-__global__ void fwd3(AdjPar p, const T *g, Work w) {
+template <typename T, typename R>
+__global__ void fwd3(AdjPar<R> p, const T *g, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
-        const double gmx = Gx(w.MU, q), gmy = Gy(w.MU, q), gnx = Gx(w.MM, q), gny = Gy(w.MM, q);
+        const R gmx = Gx(w.MU, q), gmy = Gy(w.MU, q), gnx = Gx(w.MM, q), gny = Gy(w.MM, q);
         w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
-        const double ph = w.PH[s], c = w.PS[s];
-        double Fx = -ph * gmx - (w.GSx[s] + c * gnx);
-        double Fy = -ph * gmy - (w.GSy[s] + c * gny);
+        const R ph = w.PH[s], c = w.PS[s];
+        R Fx = -ph * gmx - (w.GSx[s] + c * gnx);
+        R Fy = -ph * gmy - (w.GSy[s] + c * gny);
         if (p.body) { Fx += p.fx; Fy += p.fy; }
         w.Fx[s] = Fx; w.Fy[s] = Fy;
-        double n = 0, jx = 0, jy = 0;
+        R n = 0, jx = 0, jy = 0;
         for (int i = 0; i < 9; ++i) {
             int xs = x - EX(i), ys = y - EY(i);
             xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
             ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-            const double f = wgt(i) + (double)g[i * p.plane + (long long)ys * p.pitch + xs];
+            const R f = wgt<R>(i) + (R)g[i * p.plane + (long long)ys * p.pitch + xs];
             w.FP[i * p.N + s] = f;
             n += f; jx += f * EX(i); jy += f * EY(i);
         }
         w.RHO[s] = n;
-        w.UX[s] = (jx + 0.5 * Fx) / n;
-        w.UY[s] = (jy + 0.5 * Fy) / n;
+        w.UX[s] = (jx + R(0.5) * Fx) / n;
+        w.UY[s] = (jy + R(0.5) * Fy) / n;
     }
 }
 
-__device__ __forceinline__ double up(double u, double a, double b) { return u > 0.0 ? a : b; }
+template <typename R>
+__device__ __forceinline__ R up(R u, R a, R b) { return u > R(0.0) ? a : b; }
 
-__global__ void fwd4(AdjPar p, Work w) {
+template <typename R>
+__global__ void fwd4(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
-        const double *UX = w.UX, *UY = w.UY;
-        const double ue = 0.5 * (UX[s] + UX[q.e]), uw = 0.5 * (UX[q.w] + UX[s]);
-        const double un = 0.5 * (UY[s] + UY[q.n]), us = 0.5 * (UY[q.s] + UY[s]);
-        const double *P = w.PH, *C = w.PS;
-        const double fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
-        const double fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
-        const double ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
-        const double gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
+        const R *UX = w.UX, *UY = w.UY;
+        const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
+        const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
+        const R *P = w.PH, *C = w.PS;
+        const R fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
+        const R fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
+        const R ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
+        const R gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
         w.PHS[s] = P[s] - ((fe - fw) + (fn - fs));
         w.PSS[s] = C[s] - ((ge - gw) + (gn - gs));
     }
 }
 
-__global__ void fwd5(AdjPar p, Work w) {
+template <typename R>
+__global__ void fwd5(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
-        const double px = Gx(w.PHS, q), py = Gy(w.PHS, q);
+        const R px = Gx(w.PHS, q), py = Gy(w.PHS, q);
         w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(w.PHS, q);
         w.GRx[s] = Gx(w.PSS, q); w.GRy[s] = Gy(w.PSS, q);
-        w.MS[s] = 0.5 * p.B1 * (px * px + py * py);
+        w.MS[s] = R(0.5) * p.B1 * (px * px + py * py);
     }
 }
 
 // ---- reverse of the phi and psi updates (Eqs. 18, 19) ---------------------------
-__global__ void adj_e(AdjPar p, double gamma, Work w) {
+template <typename R>
+__global__ void adj_e(AdjPar<R> p, R gamma, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         w.LMUS[s] = p.M * Lap(w.Lphi, q);
         const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
-        const double *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
-        double lpss = Lp[s] * (1.0 - gamma), lms = 0.0;
+        const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
+        R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
         for (int k = 0; k < 8; ++k) {
-            const double lam = k < 4 ? 2.0 / 3.0 : 1.0 / 6.0;
+            const R lam = k < 4 ? R(2.0) / R(3.0) : R(1.0) / R(6.0);
             const long long j = nb[k];
             // psi'_s's own link to j, and psi'_j's link back to s
-            lpss += p.D * lam * (Lp[s] * (-1.0 + 0.5 * (m[j] - m[s])) +
-                                 Lp[j] * (1.0 + 0.5 * (m[s] - m[j])));
-            lms += p.D * lam * 0.5 * (c[s] + c[j]) * (Lp[j] - Lp[s]);
+            lpss += p.D * lam * (Lp[s] * (-R(1.0) + R(0.5) * (m[j] - m[s])) +
+                                 Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
+            lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
         }
         w.LPSS[s] = lpss;
         w.LMS[s] = lms;
@@ -200,23 +213,25 @@ __global__ void adj_e(AdjPar p, double gamma, Work w) {
 }
 
 // products for the transposed stencils of mu*, m*; local terms; dB1
-__global__ void adj_d1(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_d1(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
-        const double lmu = w.LMUS[s], lm = w.LMS[s];
-        const double qx = w.GQx[s], qy = w.GQy[s], rx = w.GRx[s], ry = w.GRy[s];
+        const R lmu = w.LMUS[s], lm = w.LMS[s];
+        const R qx = w.GQx[s], qy = w.GQy[s], rx = w.GRx[s], ry = w.GRy[s];
         w.T1[s] = (p.B0 + p.B1 * w.PSS[s]) * lmu;  // for -L(.)
         w.T2[s] = lmu * rx; w.T3[s] = lmu * ry;    // B1 div(lambda mu* grad psi*)  -> phi*
         w.T4[s] = lmu * qx; w.T5[s] = lmu * qy;    // B1 div(lambda mu* grad phi*)  -> psi*
         w.T6[s] = lm * qx;  w.T7[s] = lm * qy;     // -B1 div(lambda m* grad phi*)  -> phi*
-        const double ph = w.PH[s];
-        w.Lphi0[s] = 3.0 * p.b * ph * ph * lmu;     // cubic term uses phi^n
+        const R ph = w.PH[s];
+        w.Lphi0[s] = R(3.0) * p.b * ph * ph * lmu;     // cubic term uses phi^n
         w.LPSS[s] += -p.B1 * w.LQ[s] * lmu;
-        w.dB1[s] += lmu * (-w.PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
-                    lm * 0.5 * (qx * qx + qy * qy);
+        w.dB1[s] += (double)(lmu * (-w.PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
+                             lm * R(0.5) * (qx * qx + qy * qy));
     }
 }
 
-__global__ void adj_d2(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_d2(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         w.LPHS[s] = w.Lphi[s] + p.a * w.LMUS[s] - Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) -
@@ -226,19 +241,20 @@ __global__ void adj_d2(AdjPar p, Work w) {
 }
 
 // ---- reverse of the donor-cell advection (Eqs. 16-17) ---------------------------
-__global__ void adj_c(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_c(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
-        const double *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
-        const double *LP = w.LPHS, *LC = w.LPSS;
-        const double ue = 0.5 * (UX[s] + UX[q.e]), uw = 0.5 * (UX[q.w] + UX[s]);
-        const double un = 0.5 * (UY[s] + UY[q.n]), us = 0.5 * (UY[q.s] + UY[s]);
+        const R *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
+        const R *LP = w.LPHS, *LC = w.LPSS;
+        const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
+        const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
         // adjoint of each face flux: (lambda at the right/upper site) - (left/lower)
-        const double lpe = LP[q.e] - LP[s], lpw = LP[s] - LP[q.w];
-        const double lpn = LP[q.n] - LP[s], lps = LP[s] - LP[q.s];
-        const double lce = LC[q.e] - LC[s], lcw = LC[s] - LC[q.w];
-        const double lcn = LC[q.n] - LC[s], lcs = LC[s] - LC[q.s];
-        double lphi = LP[s], lpsi = LC[s];
+        const R lpe = LP[q.e] - LP[s], lpw = LP[s] - LP[q.w];
+        const R lpn = LP[q.n] - LP[s], lps = LP[s] - LP[q.s];
+        const R lce = LC[q.e] - LC[s], lcw = LC[s] - LC[q.w];
+        const R lcn = LC[q.n] - LC[s], lcs = LC[s] - LC[q.s];
+        R lphi = LP[s], lpsi = LC[s];
         // this site is upwind of the east / north face when u_f > 0, of west / south when u_f <= 0
         if (ue > 0) { lphi += lpe * ue; lpsi += lce * ue; }
         if (!(uw > 0)) { lphi += lpw * uw; lpsi += lcw * uw; }
@@ -246,44 +262,45 @@ __global__ void adj_c(AdjPar p, Work w) {
         if (!(us > 0)) { lphi += lps * us; lpsi += lcs * us; }
         w.Lphi0[s] += lphi;
         w.Lpsi0[s] = lpsi;
-        w.LUX[s] = 0.5 * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
+        w.LUX[s] = R(0.5) * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
                           lpw * up(uw, P[q.w], P[s]) + lcw * up(uw, C[q.w], C[s]));
-        w.LUY[s] = 0.5 * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
+        w.LUY[s] = R(0.5) * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
                           lps * up(us, P[q.s], P[s]) + lcs * up(us, C[q.s], C[s]));
     }
 }
 
 // ---- reverse of the collision (Eqs. 10-13), moments (Eq. 11) and streaming -------
-__global__ void adj_b(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_b(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
-        const double n = w.RHO[s], ux = w.UX[s], uy = w.UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
-        const double om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
-        double ln = 0, lux = w.LUX[s], luy = w.LUY[s], lFx = 0, lFy = 0;
-        double lpost[9];
+        const R n = w.RHO[s], ux = w.UX[s], uy = w.UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
+        const R om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
+        R ln = 0, lux = w.LUX[s], luy = w.LUY[s], lFx = 0, lFy = 0;
+        R lpost[9];
         for (int i = 0; i < 9; ++i) {
-            const double lp = w.Lbuf[i * p.N + s];
+            const R lp = w.Lbuf[i * p.N + s];
             lpost[i] = lp;
-            const double ex = EX(i), ey = EY(i), wi = wgt(i);
-            const double eu = ex * ux + ey * uy, eF = ex * Fx + ey * Fy;
-            ln += lp * om * wi * (1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * usq);
+            const R ex = EX(i), ey = EY(i), wi = wgt<R>(i);
+            const R eu = ex * ux + ey * uy, eF = ex * Fx + ey * Fy;
+            ln += lp * om * wi * (R(1.0) + R(3.0) * eu + R(4.5) * eu * eu - R(1.5) * usq);
             // d feq/du and d F_i/du
-            lux += lp * (om * wi * n * (3.0 * ex + 9.0 * eu * ex - 3.0 * ux) +
-                         gk * wi * (-3.0 * Fx + 9.0 * eF * ex));
-            luy += lp * (om * wi * n * (3.0 * ey + 9.0 * eu * ey - 3.0 * uy) +
-                         gk * wi * (-3.0 * Fy + 9.0 * eF * ey));
-            lFx += lp * gk * wi * (3.0 * (ex - ux) + 9.0 * eu * ex);
-            lFy += lp * gk * wi * (3.0 * (ey - uy) + 9.0 * eu * ey);
+            lux += lp * (om * wi * n * (R(3.0) * ex + R(9.0) * eu * ex - R(3.0) * ux) +
+                         gk * wi * (-R(3.0) * Fx + R(9.0) * eF * ex));
+            luy += lp * (om * wi * n * (R(3.0) * ey + R(9.0) * eu * ey - R(3.0) * uy) +
+                         gk * wi * (-R(3.0) * Fy + R(9.0) * eF * ey));
+            lFx += lp * gk * wi * (R(3.0) * (ex - ux) + R(9.0) * eu * ex);
+            lFy += lp * gk * wi * (R(3.0) * (ey - uy) + R(9.0) * eu * ey);
         }
         // u = (j + F/2) / n
-        const double ljx = lux / n, ljy = luy / n;
-        lFx += 0.5 * lux / n;
-        lFy += 0.5 * luy / n;
+        const R ljx = lux / n, ljy = luy / n;
+        lFx += R(0.5) * lux / n;
+        lFy += R(0.5) * luy / n;
         ln += -(lux * ux + luy * uy) / n;
         w.LFX[s] = lFx;
         w.LFY[s] = lFy;
         for (int i = 0; i < 9; ++i) {
-            const double lf = (1.0 - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
+            const R lf = (R(1.0) - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
             // f_i(x) was pulled from buffer_i(x - e_i)
             int xs = x - EX(i), ys = y - EY(i);
             xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
@@ -294,9 +311,10 @@ __global__ void adj_b(AdjPar p, Work w) {
 }
 
 // ---- reverse of the force (Eq. 14) and of mu, m (Eqs. 3, 5) ----------------------
-__global__ void adj_a1(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_a1(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
-        const double lfx = w.LFX[s], lfy = w.LFY[s];
+        const R lfx = w.LFX[s], lfy = w.LFY[s];
         w.T1[s] = w.PH[s] * lfx; w.T2[s] = w.PH[s] * lfy;   // -> lambda mu
         w.T3[s] = w.PS[s] * lfx; w.T4[s] = w.PS[s] * lfy;   // -> lambda m
         w.Lphi0[s] += -(lfx * w.GMx[s] + lfy * w.GMy[s]);
@@ -304,7 +322,8 @@ __global__ void adj_a1(AdjPar p, Work w) {
     }
 }
 
-__global__ void adj_a2(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_a2(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         w.LMU[s] = Div(w.T1, w.T2, q);
@@ -313,22 +332,25 @@ __global__ void adj_a2(AdjPar p, Work w) {
     }
 }
 
-__global__ void adj_a3(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_a3(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
-        const double lmu = w.LMU[s], lm = w.LMM[s];
-        const double px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
-        const double ph = w.PH[s];
+        const R lmu = w.LMU[s], lm = w.LMM[s];
+        const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
+        const R ph = w.PH[s];
         w.T1[s] = (p.B0 + p.B1 * w.PS[s]) * lmu;
         w.T2[s] = lmu * cx; w.T3[s] = lmu * cy;
         w.T4[s] = lmu * px; w.T5[s] = lmu * py;
         w.T6[s] = lm * px;  w.T7[s] = lm * py;
-        w.Lphi0[s] += (p.a + 3.0 * p.b * ph * ph) * lmu;
+        w.Lphi0[s] += (p.a + R(3.0) * p.b * ph * ph) * lmu;
         w.Lpsi0[s] += -p.B1 * w.LP[s] * lmu;
-        w.dB1[s] += lmu * (-w.PS[s] * w.LP[s] - (px * cx + py * cy)) + lm * 0.5 * (px * px + py * py);
+        w.dB1[s] += (double)(lmu * (-w.PS[s] * w.LP[s] - (px * cx + py * cy)) +
+                             lm * R(0.5) * (px * px + py * py));
     }
 }
 
-__global__ void adj_a4(AdjPar p, Work w) {
+template <typename R>
+__global__ void adj_a4(AdjPar<R> p, Work<R> w) {
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         w.Lphi0[s] += -Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) - p.B1 * Div(w.T6, w.T7, q);
@@ -370,14 +392,14 @@ __global__ void centroid_partial(int nx, int ny, long long pitch, const T *phi, 
 
 template <typename T>
 __global__ void centroid_seed(int nx, int ny, long long pitch, const T *phi, double refx,
-                              double X, double W, double *Lphi) {
+                              double X, double W, T *Lphi) {
     const long long N = (long long)nx * ny;
     LBD_SITES(N) {
         const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
         const double ph = (double)phi[(long long)y * pitch + x];
         double dx = x - refx;
         if (dx >= 0.5 * nx) dx -= nx; else if (dx < -0.5 * nx) dx += nx;
-        Lphi[s] = ph >= 0.0 ? (dx - (X - refx)) / W : 0.0;
+        Lphi[s] = (T)(ph >= 0.0 ? (dx - (X - refx)) / W : 0.0);
     }
 }
 
@@ -430,17 +452,18 @@ int adjoint_run(const AdjointJob<T> &job) {
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
-    const int n_dense = 75;  // dense arrays carved out below
-    double *dense = (double *)dalloc(sizeof(double) * (size_t)N * n_dense);
+    const int n_dense = 74;  // dense arrays of the step's precision carved out below
+    // ... followed by the per-site dL/dB1 accumulator in double
+    T *dense = (T *)dalloc(sizeof(T) * (size_t)N * n_dense + sizeof(double) * (size_t)N);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
     if (!ckpt || !seg || !dense || !part) {
         release();
         return LBD_ENOMEM;
     }
-    Work w;
+    Work<T> w;
     {
-        double *d = dense;
-        auto take = [&](int k) { double *r = d; d += (size_t)k * N; return r; };
+        T *d = dense;
+        auto take = [&](int k) { T *r = d; d += (size_t)k * N; return r; };
         w.PH = take(1); w.PS = take(1); w.GPx = take(1); w.GPy = take(1); w.LP = take(1);
         w.GSx = take(1); w.GSy = take(1); w.MU = take(1); w.MM = take(1);
         w.GMx = take(1); w.GMy = take(1); w.GNx = take(1); w.GNy = take(1);
@@ -453,7 +476,8 @@ int adjoint_run(const AdjointJob<T> &job) {
         w.LUX = take(1); w.LUY = take(1); w.LFX = take(1); w.LFY = take(1);
         w.LMU = take(1); w.LMM = take(1);
         w.T1 = take(1); w.T2 = take(1); w.T3 = take(1); w.T4 = take(1); w.T5 = take(1);
-        w.T6 = take(1); w.T7 = take(1); w.dB1 = take(1);
+        w.T6 = take(1); w.T7 = take(1);
+        w.dB1 = reinterpret_cast<double *>(d);  // 8-byte aligned: N * 74 * sizeof(T) is
         if (d - dense != (ptrdiff_t)n_dense * N) {  // carve-out must match the allocation
             release();
             return LBD_EINVAL;
@@ -527,15 +551,15 @@ int adjoint_run(const AdjointJob<T> &job) {
     // ---- seed: lambda phi = dX/dphi at T, lambda psi = lambda populations = 0 ----
     centroid_seed<T><<<nb, 256, 0, st>>>(nx, ny, pitch, fin + 9 * plane, job.refx, XT, WT, w.Lphi);
     ACK(cudaGetLastError());
-    ACK(cudaMemsetAsync(w.Lpsi, 0, sizeof(double) * N, st));
-    ACK(cudaMemsetAsync(w.Lbuf, 0, sizeof(double) * 9 * N, st));
+    ACK(cudaMemsetAsync(w.Lpsi, 0, sizeof(T) * N, st));
+    ACK(cudaMemsetAsync(w.Lbuf, 0, sizeof(T) * 9 * N, st));
     ACK(cudaMemsetAsync(w.dB1, 0, sizeof(double) * N, st));
 
-    AdjPar ap;
+    AdjPar<T> ap;
     ap.nx = nx; ap.ny = ny; ap.N = N; ap.pitch = pitch; ap.plane = plane;
-    ap.a = job.a; ap.b = job.b; ap.B0 = job.B0; ap.B1 = job.B1; ap.M = job.M; ap.D = job.D;
-    ap.omega = 1.0 / job.tau; ap.guo = 1.0 - 0.5 / job.tau; ap.gamma = 0; ap.c0 = job.c0;
-    ap.fx = job.fx; ap.fy = job.fy; ap.body = job.body;
+    ap.a = (T)job.a; ap.b = (T)job.b; ap.B0 = (T)job.B0; ap.B1 = (T)job.B1; ap.M = (T)job.M;
+    ap.D = (T)job.D; ap.omega = (T)(1.0 / job.tau); ap.guo = (T)(1.0 - 0.5 / job.tau);
+    ap.gamma = 0; ap.c0 = (T)job.c0; ap.fx = (T)job.fx; ap.fy = (T)job.fy; ap.body = job.body;
 
     // ---- reverse, segment by segment ----
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
@@ -548,31 +572,34 @@ int adjoint_run(const AdjointJob<T> &job) {
             const T *in = slot(seg, k - k0);
             double A, gm;
             activity_at(*job.params, job.t0 + k, &A, &gm);
-            fwd1<T><<<nb, 256, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
-            fwd2<<<nb, 256, 0, st>>>(ap, w);
-            fwd3<T><<<nb, 256, 0, st>>>(ap, in, w);
-            fwd4<<<nb, 256, 0, st>>>(ap, w);
-            fwd5<<<nb, 256, 0, st>>>(ap, w);
-            adj_e<<<nb, 256, 0, st>>>(ap, gm, w);
-            adj_d1<<<nb, 256, 0, st>>>(ap, w);
-            adj_d2<<<nb, 256, 0, st>>>(ap, w);
-            adj_c<<<nb, 256, 0, st>>>(ap, w);
-            adj_b<<<nb, 256, 0, st>>>(ap, w);
-            adj_a1<<<nb, 256, 0, st>>>(ap, w);
-            adj_a2<<<nb, 256, 0, st>>>(ap, w);
-            adj_a3<<<nb, 256, 0, st>>>(ap, w);
-            adj_a4<<<nb, 256, 0, st>>>(ap, w);
+            fwd1<T, T><<<nb, 256, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
+            fwd2<T><<<nb, 256, 0, st>>>(ap, w);
+            fwd3<T, T><<<nb, 256, 0, st>>>(ap, in, w);
+            fwd4<T><<<nb, 256, 0, st>>>(ap, w);
+            fwd5<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_e<T><<<nb, 256, 0, st>>>(ap, (T)gm, w);
+            adj_d1<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_d2<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_c<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_b<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_a1<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_a2<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_a3<T><<<nb, 256, 0, st>>>(ap, w);
+            adj_a4<T><<<nb, 256, 0, st>>>(ap, w);
             ACK(cudaGetLastError());
             // the input adjoints become the output adjoints of the previous step
-            double *tp;
+            T *tp;
             tp = w.Lphi; w.Lphi = w.Lphi0; w.Lphi0 = tp;
             tp = w.Lpsi; w.Lpsi = w.Lpsi0; w.Lpsi0 = tp;
             tp = w.Lbuf; w.Lbuf = w.Lbuf0; w.Lbuf0 = tp;
         }
     }
     // dL/dpsi(t0) = lambda psi; dL/dB1 = sum of the per-site accumulator
-    if (job.dpsi_host)
-        ACK(cudaMemcpyAsync(job.dpsi_host, w.Lpsi, sizeof(double) * N, cudaMemcpyDeviceToHost, st));
+    std::vector<T> dpsi_t;
+    if (job.dpsi_host) {
+        dpsi_t.resize((size_t)N);
+        ACK(cudaMemcpyAsync(dpsi_t.data(), w.Lpsi, sizeof(T) * N, cudaMemcpyDeviceToHost, st));
+    }
     sum_kernel<<<RB, 256, 0, st>>>(N, w.dB1, part);
     ACK(cudaGetLastError());
     std::vector<double> h(RB);
@@ -581,6 +608,7 @@ int adjoint_run(const AdjointJob<T> &job) {
     double sb = 0;
     for (int k = 0; k < RB; ++k) sb += h[k];
     *job.dB1 = sb;
+    for (size_t k = 0; k < dpsi_t.size(); ++k) job.dpsi_host[k] = (double)dpsi_t[k];
 #undef ACK
     release();
     return LBD_OK;

@@ -658,6 +658,11 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
         }
         const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
         if (params->flags & LBD_WALLS) {
+            // stripe shapes only: shorter segments where 64 rows leave SMs idle
+            for (int by : {32, 16})
+                if ((long long)((grid->nx + 117) / 118) * ((grid->ny + c->tile.by - 1) / c->tile.by) <
+                    2LL * sms)
+                    c->tile = Tile{118, by};
             if (!tile_ok(c, c->tile)) {
                 lbd_destroy(c);
                 return LBD_EINVAL;  // too large for the stripe kernel's 32-bit offsets

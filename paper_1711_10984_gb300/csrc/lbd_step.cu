@@ -383,8 +383,8 @@ cudaError_t launch_tile(const StepArgs<T> &a, int mode, cudaStream_t s) {
 }
 
 constexpr Tile kTiles[] = {{32, 8},   {32, 16},  {64, 8},    {32, 32},  {64, 16},
-                           {118, 32}, {118, 64}, {118, 128}, {246, 32}, {246, 64},
-                           {240, 32}, {240, 64}, {240, 128}};
+                           {118, 16}, {118, 32}, {118, 64}, {118, 128}, {246, 32},
+                           {246, 64}, {240, 32}, {240, 64}, {240, 128}};
 
 }  // namespace
 

@@ -275,7 +275,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
             LBD_PULL(0, r0_b, xg_b)  // e = ( 0, 0)
             LBD_PULL(1, r0_b, xm_b)  // e = ( 1, 0) from x - 1
             LBD_PULL(3, r0_b, xp_b)  // e = (-1, 0) from x + 1
-            if (WALLS) {
+            if (WALLS && (rb == 0 || rb == ny - 1)) {
                 // halfway bounce-back: at row 0 the populations with e_y = 1, at
                 // row ny - 1 those with e_y = -1 are the site's own reversed ones
                 const bool bot = rb == 0, top = rb == ny - 1;

@@ -137,7 +137,7 @@ def test_adjoint_leaves_the_forward_state():
 
 
 def test_fp32_forward_adjoint_against_fp64_differences():
-    """FP32 forward (shifted populations) with the FP64 adjoint sweep: within 2e-2
+    """FP32 forward (shifted populations) with the FP32 reverse sweep: within 2e-2
     of FP64 central differences."""
     n, steps = 64, 300
     d, phi, psi, src = case(n)

@@ -73,7 +73,7 @@ def test_fp32_walls_match_oracle():
 
 def test_stripe_shapes_identical_with_walls():
     outs = []
-    for tile in ((118, 32), (118, 64), (118, 128), (246, 32), (246, 64)):
+    for tile in ((118, 16), (118, 32), (118, 64), (118, 128), (246, 32), (246, 64)):
         phi, psi, src = wall_droplet(300, 90, 11)
         sim = lbd.Sim(300, 90, precision=lbd.LBD_FP32, sources=src, flags=lbd.LBD_WALLS, **ACTIVE)
         sim.set_tile(*tile)
