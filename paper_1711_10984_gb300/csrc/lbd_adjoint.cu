@@ -192,7 +192,8 @@ __global__ void fwd5(AdjPar<R> p, Work<R> w) {
 
 // ---- reverse of the phi and psi updates (Eqs. 18, 19) ---------------------------
 template <typename R>
-__global__ void adj_e(AdjPar<R> p, R gamma, Work<R> w) {
+__global__ void adj_e(AdjPar<R> p, const R *gam, int j, Work<R> w) {
+    const R gamma = gam[j];  // sink rate of the reversed step (j-th of its segment)
     LBD_SITES(p.N) {
         const Nbr q = nbr(s, p.nx, p.ny);
         w.LMUS[s] = p.M * Lap(w.Lphi, q);
@@ -430,7 +431,18 @@ int adjoint_run(const AdjointJob<T> &job) {
     const long long N = (long long)nx * ny;
     const long long plane = job.plane, pitch = job.pitch;
     const size_t state_elems = (size_t)11 * plane;  // 9 populations + phi + psi
-    cudaStream_t st = job.stream;
+    // the reverse sweep is captured as CUDA graphs, which the legacy default
+    // stream does not allow: a context on it lends the call a private stream,
+    // ordered after the work already queued (the call synchronises at the end)
+    cudaStream_t st = job.stream, own = nullptr;
+    if (!st) {
+        if (cudaStreamSynchronize(nullptr) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return LBD_ECUDA;
+        }
+        st = own;
+    }
     const int nb = (int)((N + 255) / 256 < 2048 ? (N + 255) / 256 : 2048);
     const int64_t nsteps = job.nsteps, K = job.ckpt_every;
     const int64_t nseg = (nsteps + K - 1) / K;
@@ -446,9 +458,20 @@ int adjoint_run(const AdjointJob<T> &job) {
         allocs.push_back(ptr);
         return ptr;
     };
+    cudaGraphExec_t graphs[2] = {nullptr, nullptr};  // reverse sweep of a segment, per parity
     auto release = [&]() {
+        for (auto &g : graphs)
+            if (g) {
+                cudaGraphExecDestroy(g);
+                g = nullptr;
+            }
         for (void *ptr : allocs) cudaFree(ptr);
         allocs.clear();
+        if (own) {
+            cudaStreamSynchronize(own);
+            cudaStreamDestroy(own);
+            own = nullptr;
+        }
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
@@ -456,7 +479,8 @@ int adjoint_run(const AdjointJob<T> &job) {
     // ... followed by the per-site dL/dB1 accumulator in double
     T *dense = (T *)dalloc(sizeof(T) * (size_t)N * n_dense + sizeof(double) * (size_t)N);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
-    if (!ckpt || !seg || !dense || !part) {
+    T *gam = (T *)dalloc(sizeof(T) * (size_t)K);  // sink rate of each step of a segment
+    if (!ckpt || !seg || !dense || !part || !gam) {
         release();
         return LBD_ENOMEM;
     }
@@ -562,22 +586,26 @@ int adjoint_run(const AdjointJob<T> &job) {
     ap.gamma = 0; ap.c0 = (T)job.c0; ap.fx = (T)job.fx; ap.fy = (T)job.fy; ap.body = job.body;
 
     // ---- reverse, segment by segment ----
-    for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
-        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
-                       slot(ckpt, sgi) + 10 * plane));
-        for (int64_t k = k0; k < k1 - 1; ++k)
-            ACK(step_between(slot(seg, k - k0), slot(seg, k - k0 + 1), job.t0 + k));
+    // The reversed steps of a full segment (K of them) are captured once as a
+    // CUDA graph and replayed for the other full segments: their launches and
+    // arguments are the same (the recomputed states sit in the same slots; the
+    // sink rate is read from gam[j]), except for the alternation of the adjoint
+    // buffers, so a graph is kept per buffer parity at the segment start.
+    std::vector<T> gam_h((size_t)nsteps);
+    for (int64_t k = 0; k < nsteps; ++k) {
+        double A, gm;
+        activity_at(*job.params, job.t0 + k, &A, &gm);
+        gam_h[(size_t)k] = (T)gm;
+    }
+    auto reverse_steps = [&](int64_t k0, int64_t k1) -> cudaError_t {
         for (int64_t k = k1 - 1; k >= k0; --k) {
             const T *in = slot(seg, k - k0);
-            double A, gm;
-            activity_at(*job.params, job.t0 + k, &A, &gm);
             fwd1<T, T><<<nb, 256, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
             fwd2<T><<<nb, 256, 0, st>>>(ap, w);
             fwd3<T, T><<<nb, 256, 0, st>>>(ap, in, w);
             fwd4<T><<<nb, 256, 0, st>>>(ap, w);
             fwd5<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_e<T><<<nb, 256, 0, st>>>(ap, (T)gm, w);
+            adj_e<T><<<nb, 256, 0, st>>>(ap, gam, (int)(k - k0), w);
             adj_d1<T><<<nb, 256, 0, st>>>(ap, w);
             adj_d2<T><<<nb, 256, 0, st>>>(ap, w);
             adj_c<T><<<nb, 256, 0, st>>>(ap, w);
@@ -586,13 +614,68 @@ int adjoint_run(const AdjointJob<T> &job) {
             adj_a2<T><<<nb, 256, 0, st>>>(ap, w);
             adj_a3<T><<<nb, 256, 0, st>>>(ap, w);
             adj_a4<T><<<nb, 256, 0, st>>>(ap, w);
-            ACK(cudaGetLastError());
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
             // the input adjoints become the output adjoints of the previous step
             T *tp;
             tp = w.Lphi; w.Lphi = w.Lphi0; w.Lphi0 = tp;
             tp = w.Lpsi; w.Lpsi = w.Lpsi0; w.Lpsi0 = tp;
             tp = w.Lbuf; w.Lbuf = w.Lbuf0; w.Lbuf0 = tp;
         }
+        return cudaSuccess;
+    };
+    int parity = 0;  // adjoint buffer alternation at the current segment start
+    for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
+        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
+                       slot(ckpt, sgi) + 10 * plane));
+        for (int64_t k = k0; k < k1 - 1; ++k)
+            ACK(step_between(slot(seg, k - k0), slot(seg, k - k0 + 1), job.t0 + k));
+        // stream-ordered after the previous segment's reads of gam
+        ACK(cudaMemcpyAsync(gam, gam_h.data() + k0, sizeof(T) * (size_t)(k1 - k0),
+                            cudaMemcpyHostToDevice, st));
+        if (k1 - k0 == K && K > 1) {
+            cudaGraphExec_t &ge = graphs[parity];
+            if (!ge) {
+                cudaGraph_t g = nullptr;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                    release();
+                    return LBD_ECUDA;
+                }
+                const cudaError_t e1 = reverse_steps(k0, k1);
+                const cudaError_t e2 = cudaStreamEndCapture(st, &g);
+                cudaError_t e3 = cudaErrorUnknown;
+                if (e1 == cudaSuccess && e2 == cudaSuccess)
+                    e3 = cudaGraphInstantiate(&ge, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (e3 != cudaSuccess) {
+                    cudaGetLastError();
+                    ge = nullptr;
+                    release();
+                    return LBD_ECUDA;
+                }
+            } else {
+                // replay: the host-side buffer alternation advances as in the capture
+                for (int64_t k = 0; k < K; ++k) {
+                    T *tp;
+                    tp = w.Lphi; w.Lphi = w.Lphi0; w.Lphi0 = tp;
+                    tp = w.Lpsi; w.Lpsi = w.Lpsi0; w.Lpsi0 = tp;
+                    tp = w.Lbuf; w.Lbuf = w.Lbuf0; w.Lbuf0 = tp;
+                }
+            }
+            if (cudaGraphLaunch(ge, st) != cudaSuccess) {
+                cudaGetLastError();
+                release();
+                return LBD_ECUDA;
+            }
+        } else {
+            const cudaError_t e = reverse_steps(k0, k1);
+            if (e != cudaSuccess) {
+                release();
+                return LBD_ECUDA;
+            }
+        }
+        parity ^= (int)((k1 - k0) & 1);
     }
     // dL/dpsi(t0) = lambda psi; dL/dB1 = sum of the per-site accumulator
     std::vector<T> dpsi_t;
