@@ -296,6 +296,30 @@ def time_adjoint(lbd, steps=4000, ckpt=100):
                 loss=L, dL_dB1=dB1, max_abs_dL_dpsi0=float(np.abs(dpsi).max()))
 
 
+def time_tracking(lbd, w, reps=20):
+    """Per-droplet tracking and the squirmer fit (lbd_droplets + lbd_squirmer) of
+    all droplets of the FP32 emulsion: wall clock per call, fields evaluation
+    and the synchronising read-back included."""
+    n = w["nx"]
+    sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=w["sources"], **w["params"])
+    sim.set_fields(w["phi"], w["psi"])
+    sim.step(10)
+    refs = [(d["x"] % n, d["y"] % n) for d in w["droplets"]]
+    drops = sim.droplets(refs)
+    sim.squirmer(drops)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        drops = sim.droplets(refs)
+    t1 = time.perf_counter()
+    for _ in range(reps):
+        fit = sim.squirmer(drops)
+    t2 = time.perf_counter()
+    sim.close()
+    return dict(droplets=len(refs), ms_droplets=(t1 - t0) / reps * 1e3,
+                ms_squirmer=(t2 - t1) / reps * 1e3,
+                points=int(sum(f["points"] for f in fit)))
+
+
 def cpu_baseline(w, budget_s=12.0):
     """The FP64 oracle as it stands on the host cores, on the same 2048^2
     workload, for as many whole steps as fit in about budget_s seconds."""
@@ -352,6 +376,7 @@ def run_ours(args):
     wc = inputs.channel()
     rc = time_precision(torch, lbd, autotune, wc, lbd.LBD_FP32, nw, args.warmup, stream,
                         dev_name, barrier)
+    trk = time_tracking(lbd, w) if rank == 0 else None
 
     maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
@@ -398,6 +423,7 @@ def run_ours(args):
         "fp32_over_fp64_speedup": round(t64 / t32, 2),
         "fp32_drift": r32["drift"],
         "adjoint_forward_cost": adj,
+        "tracking": trk,
         "walls": {"workload": "the same 2048x2048 emulsion between bounce-back plates "
                               "(LBD_WALLS), FP32",
                   "value": round(whole_job_mlups(N, world, nw, tw), 1),

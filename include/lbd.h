@@ -148,6 +148,44 @@ int lbd_get_populations(lbd_ctx *ctx, double *f);
  * previous centre to follow a moving droplet).  Synchronises. */
 int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
 
+/* One droplet of the current state (Section 4). */
+typedef struct {
+    double x, y;    /* centre of mass sum phi r / sum phi over its sites with phi >= 0,
+                       wrapped into [0,nx) x [0,ny) (y not wrapped with LBD_WALLS) */
+    double mass;    /* sum of phi over those sites                                  */
+    double ux, uy;  /* phi-weighted mean fluid velocity (Eq. 11) over those sites   */
+    int64_t sites;  /* number of those sites                                        */
+} lbd_droplet;
+
+#define LBD_MAX_DROPLETS 64
+
+/* Track n droplets (1 <= n <= LBD_MAX_DROPLETS) at the current time: every site
+ * with phi >= 0 belongs to the nearest of the n reference points ref_xy
+ * (host array x0, y0, x1, y1, ..., each inside the lattice; minimum image in x,
+ * and in y unless LBD_WALLS; ties to the lower index), and out[k] (host array
+ * of n) receives the centre of mass of Section 4 of droplet k, taken as its
+ * reference plus the phi-weighted mean minimum-image displacement, with its
+ * mass, mean velocity and site count.  A droplet with no site gets NaN centre
+ * and velocity.  Pass the previous centres to follow moving droplets.
+ * LBD_EINVAL for a bad n or reference.  Synchronises. */
+int lbd_droplets(lbd_ctx *ctx, int32_t n, const double *ref_xy, lbd_droplet *out);
+
+/* Squirmer fit of Section 4 (Eq. 21) for the n droplets drops[] (as returned by
+ * lbd_droplets for the current state): the phi = 0 contour is sampled where
+ * phi changes sign along a lattice link (x to x+1, y to y+1, none through a
+ * plate), point and velocity interpolated linearly along the link, each point
+ * belonging to the nearest droplet centre.  In the droplet frame (velocity
+ * minus (ux, uy)), with theta measured from the swimming direction e = u/|u|
+ * (e = x if the droplet is at rest) towards z x e, the polar velocity
+ * u_theta(theta) at the points is fitted by least squares to
+ * b1 sin(theta) + (b2 / 2) sin(2 theta), all points weighted equally.  b1[k],
+ * b2[k] (host arrays of n) receive the coefficients, NaN with fewer than two
+ * points or a singular fit, points[k] (may be NULL) the number of points;
+ * beta = b2 / b1 classifies the swimmer (beta < 0 pusher, > 0 puller).
+ * LBD_EINVAL for a bad n or a non-finite centre.  Synchronises. */
+int lbd_squirmer(lbd_ctx *ctx, int32_t n, const lbd_droplet *drops, double *b1, double *b2,
+                 int64_t *points);
+
 /* Select the launch shape of the step: bx output columns x by output rows per
  * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
  * column per thread, segments of by rows); bx 240: FP32 column-pair kernel

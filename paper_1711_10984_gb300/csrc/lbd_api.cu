@@ -38,6 +38,8 @@ struct lbd_ctx {
     double *pop_staging = nullptr;  // dense doubles, 9*N (on demand)
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
     uint32_t *theta = nullptr;      // source indicator, one bit per site
+    double *drop_dev = nullptr;     // droplet sums: block partials, results, references
+    double *h_drop = nullptr;       // pinned: results and references
     int64_t t = 0;
     Tile tile{118, 64};
     int sticky = 0;
@@ -587,6 +589,8 @@ void lbd_destroy(lbd_ctx *c) {
     }
     cudaFree(c->staging);
     cudaFree(c->pop_staging);
+    cudaFree(c->drop_dev);
+    cudaFreeHost(c->h_drop);
     cudaFree(c->red_partial);
     cudaFree(c->red_out);
     cudaFree(c->theta);
@@ -751,9 +755,12 @@ int lbd_step(lbd_ctx *c, int64_t n) {
     return c->params.precision == LBD_FP64 ? run_steps<double>(c, n) : run_steps<float>(c, n);
 }
 
-int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi, double *psi) {
-    if (!c) return LBD_EINVAL;
-    if (c->sticky) return c->sticky;
+}  // extern "C"
+
+namespace {
+// Fields of the current state (rho, ux, uy, phi, psi: dense doubles, Eq. 11 for
+// u) into the device staging area, queued on the context's stream.
+int eval_fields(lbd_ctx *c) {
     int rc = ensure_staging(c);
     if (rc != LBD_OK) return rc;
     CK(c, cudaSetDevice(c->dev));
@@ -768,6 +775,50 @@ int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi,
         a.rho_f = d; a.ux_f = d + N; a.uy_f = d + 2 * N; a.phi_f = d + 3 * N; a.psi_f = d + 4 * N;
         CK(c, lbd::launch_step<float>(a, lbd::MODE_FIELDS, c->tile, c->stream));
     }
+    return LBD_OK;
+}
+
+// Per-droplet sums (tracking, or the squirmer fit) of the current state for n
+// references of `stride` doubles each (host); the n * DROP_SUMS results land in
+// c->h_drop.  Synchronises.
+int droplet_sums(lbd_ctx *c, int n, const double *ref, int stride, bool squirm) {
+    int rc = eval_fields(c);
+    if (rc != LBD_OK) return rc;
+    const size_t m = (size_t)LBD_MAX_DROPLETS * lbd::DROP_SUMS;
+    if (!c->drop_dev) {
+        if (cudaMalloc(&c->drop_dev, sizeof(double) * (m * (RED_BLOCKS + 1) + 4 * LBD_MAX_DROPLETS)) !=
+                cudaSuccess ||
+            cudaMallocHost(&c->h_drop, sizeof(double) * (m + 4 * LBD_MAX_DROPLETS)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->drop_dev);
+            c->drop_dev = nullptr;
+            return fail(c, LBD_ENOMEM, "droplet scratch allocation failed");
+        }
+    }
+    double *partial = c->drop_dev, *out = partial + m * RED_BLOCKS, *dref = out + m;
+    double *href = c->h_drop + m;
+    for (int k = 0; k < n * stride; ++k) href[k] = ref[k];
+    CK(c, cudaMemcpyAsync(dref, href, sizeof(double) * n * stride, cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, lbd::launch_droplet_sums(c->grid.nx, c->grid.ny, !(c->params.flags & LBD_WALLS),
+                                   c->staging, n, dref, squirm, partial, RED_BLOCKS, out,
+                                   c->stream));
+    CK(c, cudaMemcpyAsync(c->h_drop, out, sizeof(double) * n * lbd::DROP_SUMS,
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi, double *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    int rc = eval_fields(c);
+    if (rc != LBD_OK) return rc;
+    const size_t N = c->N;
+    double *d = c->staging;
     double *outs[5] = {rho, ux, uy, phi, psi};
     for (int k = 0; k < 5; ++k)
         if (outs[k])
@@ -837,6 +888,77 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
     out->min_B = r[6];
     out->min_psi = r[7];
     out->nonfinite = (int64_t)r[8];
+    return LBD_OK;
+}
+
+int lbd_droplets(lbd_ctx *c, int32_t n, const double *ref_xy, lbd_droplet *out) {
+    if (!c || !ref_xy || !out) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (n < 1 || n > LBD_MAX_DROPLETS)
+        return fail(c, LBD_EINVAL, "n must be in [1, %d]", LBD_MAX_DROPLETS);
+    const int nx = c->grid.nx, ny = c->grid.ny;
+    for (int k = 0; k < n; ++k)
+        if (!(ref_xy[2 * k] >= 0 && ref_xy[2 * k] < nx && ref_xy[2 * k + 1] >= 0 &&
+              ref_xy[2 * k + 1] < ny))
+            return fail(c, LBD_EINVAL, "reference point %d outside the lattice", k);
+    int rc = droplet_sums(c, n, ref_xy, 2, false);
+    if (rc != LBD_OK) return rc;
+    const bool walls = (c->params.flags & LBD_WALLS) != 0;
+    for (int k = 0; k < n; ++k) {
+        const double *a = c->h_drop + k * lbd::DROP_SUMS;
+        lbd_droplet &d = out[k];
+        d.mass = a[0];
+        d.sites = (int64_t)a[5];
+        if (a[0] > 0) {
+            double x = std::fmod(ref_xy[2 * k] + a[1] / a[0], (double)nx);
+            double y = ref_xy[2 * k + 1] + a[2] / a[0];
+            if (x < 0) x += nx;
+            if (!walls) {
+                y = std::fmod(y, (double)ny);
+                if (y < 0) y += ny;
+            }
+            d.x = x;
+            d.y = y;
+            d.ux = a[3] / a[0];
+            d.uy = a[4] / a[0];
+        } else {
+            d.x = d.y = d.ux = d.uy = NAN;
+        }
+    }
+    return LBD_OK;
+}
+
+int lbd_squirmer(lbd_ctx *c, int32_t n, const lbd_droplet *drops, double *b1, double *b2,
+                 int64_t *points) {
+    if (!c || !drops || !b1 || !b2) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (n < 1 || n > LBD_MAX_DROPLETS)
+        return fail(c, LBD_EINVAL, "n must be in [1, %d]", LBD_MAX_DROPLETS);
+    double cen[4 * LBD_MAX_DROPLETS];
+    for (int k = 0; k < n; ++k) {
+        const lbd_droplet &d = drops[k];
+        if (!std::isfinite(d.x) || !std::isfinite(d.y) || !std::isfinite(d.ux) ||
+            !std::isfinite(d.uy))
+            return fail(c, LBD_EINVAL, "droplet %d has a non-finite centre or velocity", k);
+        cen[4 * k] = d.x;
+        cen[4 * k + 1] = d.y;
+        cen[4 * k + 2] = d.ux;
+        cen[4 * k + 3] = d.uy;
+    }
+    int rc = droplet_sums(c, n, cen, 4, true);
+    if (rc != LBD_OK) return rc;
+    for (int k = 0; k < n; ++k) {
+        // normal equations [S11 S12; S12 S22] (b1, b2) = (U1, U2)
+        const double *a = c->h_drop + k * lbd::DROP_SUMS;
+        const double det = a[0] * a[2] - a[1] * a[1];
+        if (a[5] >= 2 && det != 0.0) {
+            b1[k] = (a[3] * a[2] - a[4] * a[1]) / det;
+            b2[k] = (a[0] * a[4] - a[1] * a[3]) / det;
+        } else {
+            b1[k] = b2[k] = NAN;
+        }
+        if (points) points[k] = (int64_t)a[5];
+    }
     return LBD_OK;
 }
 

@@ -98,6 +98,18 @@ cudaError_t launch_pair(const StepArgs<float> &a, int seg, cudaStream_t s);
 bool pair_supported(int nx);
 size_t pair_smem_bytes();
 
+// Per-droplet sums (lbd_droplets.cu) on the dense fields of the fields
+// evaluation (5 arrays of nx*ny doubles: rho, ux, uy, phi, psi).  Tracking
+// (squirm false): ref holds n (x, y) reference points; per droplet sum phi,
+// sum phi dx, sum phi dy, sum phi ux, sum phi uy, sites.  Squirmer fit (squirm
+// true): ref holds n (x, y, ux, uy) centres; per droplet sum s^2, sum s^2 c,
+// sum s^2 c^2, sum u_theta s, sum u_theta s c, points.  partial holds
+// nblocks * n * DROP_SUMS doubles; out receives n * DROP_SUMS.
+constexpr int DROP_SUMS = 6;
+cudaError_t launch_droplet_sums(int nx, int ny, bool wrap_y, const double *fields, int n,
+                                const double *ref, bool squirm, double *partial, int nblocks,
+                                double *out, cudaStream_t s);
+
 // Fill the source indicator bit mask (words per row = (nx + 31) / 32) for the
 // disks (x, y, R) with the exact inclusive double-precision test, periodic in
 // x and, if wrap_y, in y.

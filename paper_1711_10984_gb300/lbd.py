@@ -49,6 +49,13 @@ class lbd_diag(ctypes.Structure):
                 ("nonfinite", ctypes.c_int64)]
 
 
+class lbd_droplet(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_double), ("y", ctypes.c_double), ("mass", ctypes.c_double),
+                ("ux", ctypes.c_double), ("uy", ctypes.c_double), ("sites", ctypes.c_int64)]
+
+
+LBD_MAX_DROPLETS = 64
+
 _P = ctypes.c_void_p
 # name -> (restype, argtypes); the list mirrors include/lbd.h
 SIGNATURES = {
@@ -63,6 +70,11 @@ SIGNATURES = {
     "lbd_get_populations": (ctypes.c_int, [_P, _dp]),
     "lbd_diagnostics": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(lbd_diag)]),
+    "lbd_droplets": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(lbd_droplet)]),
+    "lbd_squirmer": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lbd_droplet),
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "lbd_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int32]),
@@ -203,6 +215,26 @@ class Sim:
         d = lbd_diag()
         self._check(load().lbd_diagnostics(self._h, float(refx), float(refy), ctypes.byref(d)))
         return {k: getattr(d, k) for k, _ in lbd_diag._fields_}
+
+    def droplets(self, refs):
+        """Per-droplet centre, mass, mean velocity and site count (lbd_droplets)
+        for the reference points refs = [(x, y), ...]."""
+        n = len(refs)
+        ref = (ctypes.c_double * (2 * n))(*[float(v) for r in refs for v in r])
+        out = (lbd_droplet * n)()
+        self._check(load().lbd_droplets(self._h, n, ref, out))
+        return [{k: getattr(d, k) for k, _ in lbd_droplet._fields_} for d in out]
+
+    def squirmer(self, drops):
+        """Squirmer fit of Eq. (21) (lbd_squirmer) for droplets as returned by
+        droplets(): list of dict(b1, b2, points)."""
+        n = len(drops)
+        arr = (lbd_droplet * n)(*[lbd_droplet(d["x"], d["y"], d.get("mass", 0.0), d["ux"],
+                                              d["uy"], int(d.get("sites", 0))) for d in drops])
+        b1, b2 = (ctypes.c_double * n)(), (ctypes.c_double * n)()
+        pts = (ctypes.c_int64 * n)()
+        self._check(load().lbd_squirmer(self._h, n, arr, b1, b2, pts))
+        return [dict(b1=b1[k], b2=b2[k], points=pts[k]) for k in range(n)]
 
     @property
     def t(self):
