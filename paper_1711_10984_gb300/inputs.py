@@ -126,6 +126,18 @@ def channel(nx=512, ny=256, R=32.0, B1=-0.05, seed=3):
                 sources=[default_source(d, nx, ny)], droplets=[d])
 
 
+def ellipse_fields(n, R, eps, B1=0.0, a=-0.001, b=0.001, B0=0.006, psi_bg=0.1):
+    """An area-preserving elliptical droplet (semi-axes R (1 + eps) along x and
+    R / (1 + eps) along y) centred on an n x n lattice: phi = phi_eq
+    tanh((1 - r_e) R / xi) with r_e the elliptical radius, psi = psi_bg."""
+    xi = interface_width(a, B0, B1, psi_bg)
+    yy, xx = np.mgrid[0:n, 0:n].astype(np.float64)
+    c = n / 2 - 0.5
+    re = np.sqrt(((xx - c) / (R * (1 + eps))) ** 2 + ((yy - c) / (R / (1 + eps))) ** 2)
+    phi = math.sqrt(-a / b) * np.tanh((1.0 - re) * R / xi)
+    return phi, np.full((n, n), float(psi_bg))
+
+
 def two_droplets(nx=512, ny=256, R=25.0, sep=80.0, offset=0.0, seed=2):
     """Two droplets R on nx x ny, centres (nx/2 -+ sep/2, ny/2 -+ offset/2), each
     with a psi ramp pointing at its partner of seeded amplitude."""
