@@ -1,0 +1,818 @@
+// lbd3.cu -- the coupled step of arXiv 1711.10984 (Section 2) on the D3Q19
+// lattice, and the C ABI of include/lbd3.h.
+//
+// One step is five kernels, one thread per site, each reading its inputs with
+// their stencil neighbourhood from global memory (neighbour rows and planes
+// are reused from L1/L2):
+//   k_chem    mu_phi (Eq. 3), m (Eq. 5) at t^n                       -> mu, m
+//   k_lb      F (Eq. 14), pull f_i, u (Eq. 11), BGK + Guo collision
+//             (Eqs. 10, 12, 13), u for the advection                 -> f, u
+//   k_advect  phi*, psi* by donor-cell fluxes on 6 faces (Eqs. 16-17)
+//   k_chem2   mu*, m* from phi*, psi* (cubic from phi^n)
+//   k_update  phi^{n+1} (Eq. 18), psi^{n+1} (Eq. 19 in link form, sink, source)
+// Populations are stored as deviations g_i = f_i - w_i (pull layout: buffer_i(x)
+// is read by site x + e_i); x rows are padded to 128 bytes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "lbd3.h"
+
+namespace {
+
+constexpr int Q = 19;
+__constant__ int c_ex[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ int c_ey[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__constant__ int c_ez[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+__host__ __device__ inline double wq(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Lattice geometry and the scalars of one step.
+template <typename T>
+struct Arg3 {
+    int nx, ny, nz;
+    long long pitch, plane, vol;  // row pitch, pitch * ny, plane * nz (elements)
+    const T *g_in;
+    T *g_out;
+    const T *phi, *psi;  // phi^n, psi^n
+    T *phi_o, *psi_o;    // phi^{n+1}, psi^{n+1}
+    T *mu, *mm, *ux, *uy, *uz, *phs, *pss, *mus, *mms;  // intermediates
+    const uint32_t *theta;  // source balls, one bit per site (words per row (nx+31)/32)
+    T a, b, B0, B1, M, D, omega, guo, gamma, c0, A;
+    T fx, fy, fz, ux0, uy0, uz0;
+    int frozen;
+};
+
+// Offsets of the 27 sites around (x, y, z) (periodic), ox/oy/oz index -1, 0, 1.
+struct Nb {
+    long long ox[3], oy[3], oz[3];
+    __device__ long long at(int ex, int ey, int ez) const {
+        return ox[ex + 1] + oy[ey + 1] + oz[ez + 1];
+    }
+};
+
+template <typename T>
+__device__ inline Nb neighbours(const Arg3<T> &p, int x, int y, int z) {
+    Nb n;
+    n.ox[0] = x ? x - 1 : p.nx - 1;
+    n.ox[1] = x;
+    n.ox[2] = x + 1 < p.nx ? x + 1 : 0;
+    n.oy[0] = (long long)(y ? y - 1 : p.ny - 1) * p.pitch;
+    n.oy[1] = (long long)y * p.pitch;
+    n.oy[2] = (long long)(y + 1 < p.ny ? y + 1 : 0) * p.pitch;
+    n.oz[0] = (long long)(z ? z - 1 : p.nz - 1) * p.plane;
+    n.oz[1] = (long long)z * p.plane;
+    n.oz[2] = (long long)(z + 1 < p.nz ? z + 1 : 0) * p.plane;
+    return n;
+}
+
+// The 19 values of field A around the site, in the D3Q19 order.
+template <typename T>
+__device__ inline void gather(const T *A, const Nb &n, T v[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = A[n.at(c_ex[i], c_ey[i], c_ez[i])];
+}
+
+// Isotropic D3Q19 gradient and Laplacian of the gathered values.
+template <typename T>
+__device__ inline void grad_lap(const T v[Q], T &gx, T &gy, T &gz, T &lap) {
+    T sx = 0, sy = 0, sz = 0, sl = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+        const T w = (T)wq(i);
+        sx += w * (T)c_ex[i] * v[i];
+        sy += w * (T)c_ey[i] * v[i];
+        sz += w * (T)c_ez[i] * v[i];
+        sl += w * (v[i] - v[0]);
+    }
+    gx = T(3) * sx;
+    gy = T(3) * sy;
+    gz = T(3) * sz;
+    lap = T(6) * sl;
+}
+
+template <typename T>
+__device__ inline void grad3(const T v[Q], T &gx, T &gy, T &gz) {
+    T lap;
+    grad_lap(v, gx, gy, gz, lap);
+}
+
+#define LBD3_SITE(p)                                                        \
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;                    \
+    const int y = blockIdx.y, z = blockIdx.z;                               \
+    if (x >= (p).nx) return;                                                \
+    const long long s = (long long)z * (p).plane + (long long)y * (p).pitch + x;
+
+// mu_phi and m at t^n (Eqs. 3, 5)
+template <typename T>
+__global__ void k_chem(const Arg3<T> p) {
+    LBD3_SITE(p)
+    const Nb n = neighbours(p, x, y, z);
+    T P[Q], C[Q];
+    gather(p.phi, n, P);
+    gather(p.psi, n, C);
+    T px, py, pz, lp, cx, cy, cz;
+    grad_lap(P, px, py, pz, lp);
+    grad3(C, cx, cy, cz);
+    const T ph = P[0];
+    p.mu[s] = p.a * ph + p.b * (ph * ph * ph) - (p.B0 + p.B1 * C[0]) * lp -
+              p.B1 * (px * cx + py * cy + pz * cz);
+    p.mm[s] = T(0.5) * p.B1 * (px * px + py * py + pz * pz);
+}
+
+// F (Eq. 14), pulled populations, u (Eq. 11) and the BGK + Guo collision
+// (Eqs. 10, 12, 13) on the deviations g = f - w; with FIELDS, rho and u of the
+// current state to dense doubles (rho, ux, uy, uz at d, N + d, 2N + d, 3N + d).
+template <typename T, int FIELDS>
+__global__ void k_lb(const Arg3<T> p, double *out) {
+    LBD3_SITE(p)
+    const Nb n = neighbours(p, x, y, z);
+    T v[Q];
+    T gmx, gmy, gmz, gnx, gny, gnz, gcx, gcy, gcz;
+    gather(p.mu, n, v);
+    grad3(v, gmx, gmy, gmz);
+    gather(p.mm, n, v);
+    grad3(v, gnx, gny, gnz);
+    gather(p.psi, n, v);
+    grad3(v, gcx, gcy, gcz);
+    const T ph = p.phi[s], c = v[0];
+    // psi grad mu_psi = grad psi + psi grad m; (fx, fy, fz) is zero without a body force
+    const T Fx = -ph * gmx - (gcx + c * gnx) + p.fx;
+    const T Fy = -ph * gmy - (gcy + c * gny) + p.fy;
+    const T Fz = -ph * gmz - (gcz + c * gnz) + p.fz;
+    T g[Q];
+    T dn = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        g[i] = p.g_in[i * p.vol + n.at(-c_ex[i], -c_ey[i], -c_ez[i])];  // from x - e_i
+        dn += g[i];
+        jx += (T)c_ex[i] * g[i];
+        jy += (T)c_ey[i] * g[i];
+        jz += (T)c_ez[i] * g[i];
+    }
+    const T rho = T(1) + dn;
+    const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
+            uz = (jz + T(0.5) * Fz) / rho;
+    if (FIELDS) {
+        const long long N = (long long)p.nx * p.ny * p.nz;
+        const long long d = ((long long)z * p.ny + y) * p.nx + x;
+        out[d] = (double)rho;
+        out[N + d] = (double)ux;
+        out[2 * N + d] = (double)uy;
+        out[3 * N + d] = (double)uz;
+        return;
+    }
+    const T usq = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        const T w = (T)wq(i);
+        const T ex = (T)c_ex[i], ey = (T)c_ey[i], ez = (T)c_ez[i];
+        const T eu = ex * ux + ey * uy + ez * uz, eF = ex * Fx + ey * Fy + ez * Fz;
+        const T geq = w * (dn + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
+        const T Fi = p.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
+        p.g_out[i * p.vol + s] = g[i] - p.omega * (g[i] - geq) + Fi;
+    }
+    p.ux[s] = p.frozen ? p.ux0 : ux;
+    p.uy[s] = p.frozen ? p.uy0 : uy;
+    p.uz[s] = p.frozen ? p.uz0 : uz;
+}
+
+// phi*, psi* (Eqs. 16-17): g* = g - sum over the 6 faces of the outgoing flux
+// u_f g_upwind, u_f the mean of the two sites' normal velocities.
+template <typename T>
+__global__ void k_advect(const Arg3<T> p) {
+    LBD3_SITE(p)
+    const Nb n = neighbours(p, x, y, z);
+    T netp = 0, netc = 0;
+    const T P0 = p.phi[s], C0 = p.psi[s];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const long long up = n.at(a == 0, a == 1, a == 2), dn = n.at(-(a == 0), -(a == 1), -(a == 2));
+        const T *U = a == 0 ? p.ux : (a == 1 ? p.uy : p.uz);
+        const T fp = T(0.5) * (U[s] + U[up]), fm = T(0.5) * (U[dn] + U[s]);
+        netp += fp * (fp > T(0) ? P0 : p.phi[up]) - fm * (fm > T(0) ? p.phi[dn] : P0);
+        netc += fp * (fp > T(0) ? C0 : p.psi[up]) - fm * (fm > T(0) ? p.psi[dn] : C0);
+    }
+    p.phs[s] = P0 - netp;
+    p.pss[s] = C0 - netc;
+}
+
+// mu*, m* from phi*, psi* (Eqs. 3, 5), the cubic from phi^n (Eq. 18)
+template <typename T>
+__global__ void k_chem2(const Arg3<T> p) {
+    LBD3_SITE(p)
+    const Nb n = neighbours(p, x, y, z);
+    T P[Q], C[Q];
+    gather(p.phs, n, P);
+    gather(p.pss, n, C);
+    T px, py, pz, lp, cx, cy, cz;
+    grad_lap(P, px, py, pz, lp);
+    grad3(C, cx, cy, cz);
+    const T pn = p.phi[s];
+    p.mus[s] = p.a * P[0] + p.b * (pn * pn * pn) - (p.B0 + p.B1 * C[0]) * lp -
+               p.B1 * (px * cx + py * cy + pz * cz);
+    p.mms[s] = T(0.5) * p.B1 * (px * px + py * py + pz * pz);
+}
+
+// phi^{n+1} = phi* + M lap mu* (Eq. 18); psi^{n+1} = psi* + D sum_j 6 w_j
+// [(psi*_j - psi*) + (psi* + psi*_j)(m*_j - m*)/2] - gamma (psi* - c0) + A Theta (Eq. 19)
+template <typename T>
+__global__ void k_update(const Arg3<T> p) {
+    LBD3_SITE(p)
+    const Nb n = neighbours(p, x, y, z);
+    T v[Q], C[Q], Mv[Q];
+    gather(p.mus, n, v);
+    T sl = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) sl += (T)wq(i) * (v[i] - v[0]);
+    p.phi_o[s] = p.phs[s] + p.M * (T(6) * sl);
+    gather(p.pss, n, C);
+    gather(p.mms, n, Mv);
+    T div = 0;
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+        div += (T)wq(i) * ((C[i] - C[0]) + T(0.5) * (C[0] + C[i]) * (Mv[i] - Mv[0]));
+    const int words = (p.nx + 31) / 32;
+    const uint32_t bit = (p.theta[((long long)z * p.ny + y) * words + (x >> 5)] >> (x & 31)) & 1u;
+    p.psi_o[s] = C[0] + (p.D * (T(6) * div) - p.gamma * (C[0] - p.c0) + (bit ? p.A : T(0)));
+}
+
+// ------------------------------------------------------------ utility kernels
+
+struct Geo3 {
+    int nx, ny, nz;
+    long long pitch, plane, vol;
+};
+
+__device__ inline void coords(const Geo3 &G, long long d, int &x, int &y, int &z) {
+    const long long r = d / G.nx;
+    x = (int)(d - r * G.nx);
+    y = (int)(r % G.ny);
+    z = (int)(r / G.ny);
+}
+
+__device__ inline int pw(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// f_i = f_i^eq(rho, u) (Eq. 12) in the pull layout: buffer_i(x) holds the value
+// site x + e_i reads, f_i^eq at x + e_i; phi, psi copied.  Inputs: dense doubles
+// rho, ux, uy, uz, phi, psi at d, N + d, ..., 5N + d.
+template <typename T>
+__global__ void k_init(const Geo3 G, const double *in, T *g, T *phi, T *psi) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
+         d += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(G, d, x, y, z);
+        const long long s = (long long)z * G.plane + (long long)y * G.pitch + x;
+        phi[s] = (T)in[4 * N + d];
+        psi[s] = (T)in[5 * N + d];
+        for (int i = 0; i < Q; ++i) {
+            const int xs = pw(x + c_ex[i], G.nx), ys = pw(y + c_ey[i], G.ny), zs = pw(z + c_ez[i], G.nz);
+            const long long q = ((long long)zs * G.ny + ys) * G.nx + xs;
+            const double n = in[q], u = in[N + q], v = in[2 * N + q], w = in[3 * N + q];
+            const double eu = c_ex[i] * u + c_ey[i] * v + c_ez[i] * w, usq = u * u + v * v + w * w;
+            g[i * G.vol + s] = (T)(wq(i) * ((n - 1.0) + n * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
+        }
+    }
+}
+
+// pre-collision f_i(x) = w_i + buffer_i(x - e_i), and phi, psi, as dense doubles
+template <typename T>
+__global__ void k_pops(const Geo3 G, const T *g, double *f) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
+         d += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(G, d, x, y, z);
+        for (int i = 0; i < Q; ++i) {
+            const long long s = (long long)pw(z - c_ez[i], G.nz) * G.plane +
+                                (long long)pw(y - c_ey[i], G.ny) * G.pitch + pw(x - c_ex[i], G.nx);
+            f[i * N + d] = wq(i) + (double)g[i * G.vol + s];
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_dense(const Geo3 G, const T *phi, const T *psi, double *out_phi, double *out_psi) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
+         d += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(G, d, x, y, z);
+        const long long s = (long long)z * G.plane + (long long)y * G.pitch + x;
+        out_phi[d] = (double)phi[s];
+        out_psi[d] = (double)psi[s];
+    }
+}
+
+struct Balls {
+    lbd3_source s[LBD_MAX_SOURCES];
+};
+
+// Theta of the source balls, one bit per site: inclusive, periodic minimum
+// image, union; the test in double without contraction into FMAs.
+__global__ void k_theta(const Geo3 G, int n_src, Balls b, uint32_t *mask) {
+    const int words = (G.nx + 31) / 32;
+    const long long total = (long long)words * G.ny * G.nz;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long r = w / words;
+        const int y = (int)(r % G.ny), z = (int)(r / G.ny), x0 = (int)(w - r * words) * 32;
+        uint32_t bits = 0;
+        for (int k = 0; k < 32 && x0 + k < G.nx; ++k)
+            for (int j = 0; j < n_src; ++j) {
+                double d[3] = {(double)(x0 + k) - b.s[j].x, (double)y - b.s[j].y,
+                               (double)z - b.s[j].z};
+                const int L[3] = {G.nx, G.ny, G.nz};
+                for (int a = 0; a < 3; ++a) {
+                    if (d[a] > 0.5 * L[a]) d[a] -= L[a];
+                    else if (d[a] < -0.5 * L[a]) d[a] += L[a];
+                }
+                const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(d[0], d[0]), __dmul_rn(d[1], d[1])),
+                                            __dmul_rn(d[2], d[2]));
+                if (r2 <= __dmul_rn(b.s[j].R, b.s[j].R)) {
+                    bits |= 1u << k;
+                    break;
+                }
+            }
+        mask[w] = bits;
+    }
+}
+
+constexpr int NRED3 = 8;  // sum g, sum phi, sum psi, phi dx, phi dy, phi dz, phi, nonfinite
+constexpr int RED3_BLOCKS = 608, RED3_THREADS = 256;
+
+// Per-block sums over a fixed set of sites (block b: sites b, b + B, ...), tree
+// reduced in shared memory: the result does not depend on scheduling.
+template <typename T>
+__global__ void k_red(const Geo3 G, const T *g, const T *phi, const T *psi, double rx, double ry,
+                      double rz, double *partial) {
+    __shared__ double sh[NRED3][RED3_THREADS];
+    double v[NRED3] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
+         d += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        coords(G, d, x, y, z);
+        const long long s = (long long)z * G.plane + (long long)y * G.pitch + x;
+        double dn = 0;
+        for (int i = 0; i < Q; ++i) dn += (double)g[i * G.vol + s];
+        const double ph = (double)phi[s], c = (double)psi[s];
+        v[0] += dn;
+        v[1] += ph;
+        v[2] += c;
+        if (!isfinite(dn) || !isfinite(ph) || !isfinite(c)) v[7] += 1;
+        if (ph >= 0) {
+            double e[3] = {x - rx, y - ry, z - rz};
+            const int L[3] = {G.nx, G.ny, G.nz};
+            for (int a = 0; a < 3; ++a) {
+                if (e[a] >= 0.5 * L[a]) e[a] -= L[a];
+                else if (e[a] < -0.5 * L[a]) e[a] += L[a];
+            }
+            v[3] += ph * e[0];
+            v[4] += ph * e[1];
+            v[5] += ph * e[2];
+            v[6] += ph;
+        }
+    }
+    for (int k = 0; k < NRED3; ++k) sh[k][threadIdx.x] = v[k];
+    __syncthreads();
+    for (int h = RED3_THREADS / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h)
+            for (int k = 0; k < NRED3; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < NRED3; ++k) partial[k * gridDim.x + blockIdx.x] = sh[k][0];
+}
+
+__global__ void k_red_final(int nb, const double *partial, double *out) {
+    const int k = threadIdx.x;
+    if (k >= NRED3) return;
+    double a = 0;
+    for (int b = 0; b < nb; ++b) a += partial[k * nb + b];
+    out[k] = a;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- host side
+
+struct lbd3_ctx {
+    int dev = 0;
+    lbd3_grid grid{};
+    lbd3_params params{};
+    cudaStream_t stream = nullptr;
+    long long pitch = 0, plane = 0, vol = 0, N = 0;
+    size_t esz = 0;
+    void *g[2] = {nullptr, nullptr}, *phi[2] = {nullptr, nullptr}, *psi[2] = {nullptr, nullptr};
+    void *work = nullptr;            // mu, m, ux, uy, uz, phi*, psi*, mu*, m* (9 fields)
+    uint32_t *theta = nullptr;
+    double *staging = nullptr;       // 6N dense doubles
+    double *pop_staging = nullptr;   // 19N, on demand
+    double *red = nullptr;           // NRED3 * RED3_BLOCKS partials + NRED3 results
+    int cur = 0;
+    int64_t t = 0;
+    int sticky = 0;
+    std::string msg;
+};
+
+namespace {
+
+int fail3(lbd3_ctx *c, int code, const char *fmt, ...) {
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        c->msg = buf;
+        if (code == LBD_ECUDA) c->sticky = LBD_ECUDA;
+    }
+    return code;
+}
+
+#define CK3(ctx, call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail3(ctx, LBD_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),   \
+                         __FILE__, __LINE__);                                               \
+    } while (0)
+
+int check3(lbd3_ctx *c, const lbd3_params *q) {
+    if (!q) return fail3(c, LBD_EINVAL, "params is NULL");
+    const lbd_params &p = q->base;
+    if (!(p.tau > 0.5)) return fail3(c, LBD_EINVAL, "tau must be > 1/2");
+    if (!(p.b >= 0.0)) return fail3(c, LBD_EINVAL, "b must be >= 0");
+    const double vals[] = {p.a, p.b, p.B0, p.B1, p.M, p.D, p.tau, p.gamma, p.c0, p.A0, p.A_max,
+                           p.fx, p.fy, p.ux0, p.uy0, q->fz, q->uz0};
+    for (double v : vals)
+        if (!std::isfinite(v)) return fail3(c, LBD_EINVAL, "non-finite parameter");
+    if (p.precision != LBD_FP64 && p.precision != LBD_FP32)
+        return fail3(c, LBD_EINVAL, "precision must be LBD_FP64 or LBD_FP32");
+    if (p.flags & ~(LBD_FROZEN_U | LBD_BODY_FORCE))
+        return fail3(c, LBD_EINVAL, "unknown or unsupported flags (3D has no walls)");
+    if (q->n_src < 0 || q->n_src > LBD_MAX_SOURCES)
+        return fail3(c, LBD_EINVAL, "n_src must be in [0, %d]", LBD_MAX_SOURCES);
+    for (int k = 0; k < q->n_src; ++k) {
+        const lbd3_source &b = q->src[k];
+        if (!std::isfinite(b.x) || !std::isfinite(b.y) || !std::isfinite(b.z) || !(b.R >= 0.0))
+            return fail3(c, LBD_EINVAL, "bad source %d", k);
+    }
+    return LBD_OK;
+}
+
+int theta3(lbd3_ctx *c) {
+    Balls b;
+    const lbd3_params &q = c->params;
+    const double L[3] = {(double)c->grid.nx, (double)c->grid.ny, (double)c->grid.nz};
+    for (int k = 0; k < q.n_src; ++k) {
+        double v[3] = {q.src[k].x, q.src[k].y, q.src[k].z};
+        for (int a = 0; a < 3; ++a) {
+            v[a] = std::fmod(v[a], L[a]);
+            if (v[a] < 0) v[a] += L[a];
+        }
+        b.s[k] = lbd3_source{v[0], v[1], v[2], q.src[k].R};
+    }
+    const Geo3 G{c->grid.nx, c->grid.ny, c->grid.nz, c->pitch, c->plane, c->vol};
+    k_theta<<<1024, 256, 0, c->stream>>>(G, q.n_src, b, c->theta);
+    CK3(c, cudaGetLastError());
+    return LBD_OK;
+}
+
+Geo3 geo(const lbd3_ctx *c) {
+    return Geo3{c->grid.nx, c->grid.ny, c->grid.nz, c->pitch, c->plane, c->vol};
+}
+
+template <typename T>
+Arg3<T> args3(const lbd3_ctx *c) {
+    Arg3<T> a;
+    memset(&a, 0, sizeof a);
+    a.nx = c->grid.nx;
+    a.ny = c->grid.ny;
+    a.nz = c->grid.nz;
+    a.pitch = c->pitch;
+    a.plane = c->plane;
+    a.vol = c->vol;
+    a.g_in = (const T *)c->g[c->cur];
+    a.g_out = (T *)c->g[1 - c->cur];
+    a.phi = (const T *)c->phi[c->cur];
+    a.psi = (const T *)c->psi[c->cur];
+    a.phi_o = (T *)c->phi[1 - c->cur];
+    a.psi_o = (T *)c->psi[1 - c->cur];
+    T *w = (T *)c->work;
+    T **f[9] = {&a.mu, &a.mm, &a.ux, &a.uy, &a.uz, &a.phs, &a.pss, &a.mus, &a.mms};
+    for (int k = 0; k < 9; ++k) *f[k] = w + k * c->vol;
+    a.theta = c->theta;
+    const lbd_params &p = c->params.base;
+    a.a = (T)p.a;
+    a.b = (T)p.b;
+    a.B0 = (T)p.B0;
+    a.B1 = (T)p.B1;
+    a.M = (T)p.M;
+    a.D = (T)p.D;
+    a.omega = (T)(1.0 / p.tau);
+    a.guo = (T)(1.0 - 0.5 / p.tau);
+    a.c0 = (T)p.c0;
+    double A = 0, gm = 0;
+    if (c->t >= p.t_on) {
+        A = p.A0 * (double)(c->t - p.t_on);
+        A = A < p.A_max ? A : p.A_max;
+        gm = p.gamma;
+    }
+    a.A = (T)A;
+    a.gamma = (T)gm;
+    const bool body = (p.flags & LBD_BODY_FORCE) != 0;
+    a.fx = body ? (T)p.fx : T(0);
+    a.fy = body ? (T)p.fy : T(0);
+    a.fz = body ? (T)c->params.fz : T(0);
+    a.frozen = (p.flags & LBD_FROZEN_U) ? 1 : 0;
+    a.ux0 = (T)p.ux0;
+    a.uy0 = (T)p.uy0;
+    a.uz0 = (T)c->params.uz0;
+    return a;
+}
+
+template <typename T>
+cudaError_t launch_step3(const Arg3<T> &a, cudaStream_t s) {
+    const dim3 blk(128), grd((a.nx + 127) / 128, a.ny, a.nz);
+    k_chem<T><<<grd, blk, 0, s>>>(a);
+    k_lb<T, 0><<<grd, blk, 0, s>>>(a, nullptr);
+    k_advect<T><<<grd, blk, 0, s>>>(a);
+    k_chem2<T><<<grd, blk, 0, s>>>(a);
+    k_update<T><<<grd, blk, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fields3(const Arg3<T> &a, const Geo3 &G, double *out, cudaStream_t s) {
+    const dim3 blk(128), grd((a.nx + 127) / 128, a.ny, a.nz);
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    k_chem<T><<<grd, blk, 0, s>>>(a);
+    k_lb<T, 1><<<grd, blk, 0, s>>>(a, out);
+    k_dense<T><<<1024, 256, 0, s>>>(G, a.phi, a.psi, out + 4 * N, out + 5 * N);
+    return cudaGetLastError();
+}
+
+int ensure_staging3(lbd3_ctx *c) {
+    if (c->staging) return LBD_OK;
+    if (cudaMalloc(&c->staging, sizeof(double) * 6 * c->N) != cudaSuccess) {
+        cudaGetLastError();
+        c->staging = nullptr;
+        return fail3(c, LBD_ENOMEM, "staging allocation failed");
+    }
+    return LBD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbd3_last_error(const lbd3_ctx *c) { return c ? c->msg.c_str() : "null context"; }
+
+void lbd3_destroy(lbd3_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->g[k]);
+        cudaFree(c->phi[k]);
+        cudaFree(c->psi[k]);
+    }
+    cudaFree(c->work);
+    cudaFree(c->theta);
+    cudaFree(c->staging);
+    cudaFree(c->pop_staging);
+    cudaFree(c->red);
+    cudaGetLastError();
+    delete c;
+}
+
+int lbd3_create(const lbd3_grid *grid, const lbd3_params *params, void *stream, lbd3_ctx **out) {
+    if (!grid || !params || !out) return LBD_EINVAL;
+    *out = nullptr;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 4096 || grid->ny > 4096 ||
+        grid->nz > 4096 || (long long)grid->nx * grid->ny * grid->nz > (1LL << 31))
+        return LBD_EINVAL;
+    if (check3(nullptr, params) != LBD_OK) return LBD_EINVAL;
+    lbd3_ctx *c = new (std::nothrow) lbd3_ctx();
+    if (!c) return LBD_ENOMEM;
+    c->grid = *grid;
+    c->params = *params;
+    c->stream = (cudaStream_t)stream;
+    c->esz = params->base.precision == LBD_FP64 ? sizeof(double) : sizeof(float);
+    const long long align = 128 / (long long)c->esz;
+    c->pitch = (grid->nx + align - 1) / align * align;
+    c->plane = c->pitch * grid->ny;
+    c->vol = c->plane * grid->nz;
+    c->N = (long long)grid->nx * grid->ny * grid->nz;
+    if (cudaGetDevice(&c->dev) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return LBD_ECUDA;
+    }
+    const size_t fb = (size_t)c->vol * c->esz;
+    const size_t words = (size_t)((grid->nx + 31) / 32) * grid->ny * grid->nz;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&c->g[k], (size_t)Q * fb) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->phi[k], fb) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->psi[k], fb) == cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&c->work, 9 * fb) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->theta, 4 * words) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->red, sizeof(double) * NRED3 * (RED3_BLOCKS + 1)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        lbd3_destroy(c);
+        return LBD_ENOMEM;
+    }
+    // rest state; the work fields are zeroed so that padding columns stay finite
+    for (int k = 0; k < 2; ++k)
+        ok &= cudaMemsetAsync(c->g[k], 0, Q * fb, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(c->phi[k], 0, fb, c->stream) == cudaSuccess &&
+              cudaMemsetAsync(c->psi[k], 0, fb, c->stream) == cudaSuccess;
+    ok &= cudaMemsetAsync(c->work, 0, 9 * fb, c->stream) == cudaSuccess;
+    if (!ok || theta3(c) != LBD_OK || cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        lbd3_destroy(c);
+        return LBD_ECUDA;
+    }
+    *out = c;
+    return LBD_OK;
+}
+
+int lbd3_set_params(lbd3_ctx *c, const lbd3_params *p) {
+    if (!c) return LBD_EINVAL;
+    int rc = check3(c, p);
+    if (rc != LBD_OK) return rc;
+    if (p->base.precision != c->params.base.precision)
+        return fail3(c, LBD_EINVAL, "precision cannot change after creation");
+    c->params = *p;
+    CK3(c, cudaSetDevice(c->dev));
+    return theta3(c);
+}
+
+int lbd3_set_fields(lbd3_ctx *c, const double *rho, const double *ux, const double *uy,
+                    const double *uz, const double *phi, const double *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (!phi || !psi) return fail3(c, LBD_EINVAL, "phi and psi are required");
+    const long long N = c->N;
+    const lbd_params &p = c->params.base;
+    for (long long d = 0; d < N; ++d) {
+        if (!std::isfinite(phi[d]) || !std::isfinite(psi[d]) || (rho && !std::isfinite(rho[d])) ||
+            (ux && !std::isfinite(ux[d])) || (uy && !std::isfinite(uy[d])) ||
+            (uz && !std::isfinite(uz[d])))
+            return fail3(c, LBD_ENONFINITE, "non-finite value at site %lld", d);
+        if (!(psi[d] > 0.0) || !(p.B0 + p.B1 * psi[d] > 0.0))
+            return fail3(c, LBD_EUNSTABLE, "B(psi) <= 0 or psi <= 0 at site %lld", d);
+    }
+    int rc = ensure_staging3(c);
+    if (rc != LBD_OK) return rc;
+    CK3(c, cudaSetDevice(c->dev));
+    double *d = c->staging;
+    const size_t B = sizeof(double) * N;
+    if (rho) CK3(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
+    const double *u[3] = {ux, uy, uz};
+    for (int k = 0; k < 3; ++k)
+        if (u[k]) CK3(c, cudaMemcpyAsync(d + (k + 1) * N, u[k], B, cudaMemcpyHostToDevice, c->stream));
+        else CK3(c, cudaMemsetAsync(d + (k + 1) * N, 0, B, c->stream));
+    CK3(c, cudaMemcpyAsync(d + 4 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
+    CK3(c, cudaMemcpyAsync(d + 5 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
+    if (!rho) {
+        // rho = 1: fill on the host side of the copy to keep this path simple
+        double *h = nullptr;
+        if (cudaMallocHost(&h, B) != cudaSuccess) {
+            cudaGetLastError();
+            return fail3(c, LBD_ENOMEM, "host staging allocation failed");
+        }
+        for (long long k = 0; k < N; ++k) h[k] = 1.0;
+        cudaError_t e = cudaMemcpyAsync(d, h, B, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFreeHost(h);
+        CK3(c, e);
+    }
+    const Geo3 G = geo(c);
+    if (p.precision == LBD_FP64)
+        k_init<double><<<1024, 256, 0, c->stream>>>(G, d, (double *)c->g[c->cur],
+                                                    (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+    else
+        k_init<float><<<1024, 256, 0, c->stream>>>(G, d, (float *)c->g[c->cur],
+                                                   (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+    CK3(c, cudaGetLastError());
+    CK3(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd3_step(lbd3_ctx *c, int64_t n) {
+    if (!c || n < 0) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK3(c, cudaSetDevice(c->dev));
+    for (int64_t k = 0; k < n; ++k) {
+        if (c->params.base.precision == LBD_FP64)
+            CK3(c, launch_step3<double>(args3<double>(c), c->stream));
+        else
+            CK3(c, launch_step3<float>(args3<float>(c), c->stream));
+        c->cur = 1 - c->cur;
+        c->t += 1;
+    }
+    return LBD_OK;
+}
+
+int lbd3_get_fields(lbd3_ctx *c, double *rho, double *ux, double *uy, double *uz, double *phi,
+                    double *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    int rc = ensure_staging3(c);
+    if (rc != LBD_OK) return rc;
+    CK3(c, cudaSetDevice(c->dev));
+    const Geo3 G = geo(c);
+    if (c->params.base.precision == LBD_FP64)
+        CK3(c, launch_fields3<double>(args3<double>(c), G, c->staging, c->stream));
+    else
+        CK3(c, launch_fields3<float>(args3<float>(c), G, c->staging, c->stream));
+    double *outs[6] = {rho, ux, uy, uz, phi, psi};
+    for (int k = 0; k < 6; ++k)
+        if (outs[k])
+            CK3(c, cudaMemcpyAsync(outs[k], c->staging + k * c->N, sizeof(double) * c->N,
+                                   cudaMemcpyDeviceToHost, c->stream));
+    CK3(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd3_get_populations(lbd3_ctx *c, double *f) {
+    if (!c || !f) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK3(c, cudaSetDevice(c->dev));
+    if (!c->pop_staging && cudaMalloc(&c->pop_staging, sizeof(double) * Q * c->N) != cudaSuccess) {
+        cudaGetLastError();
+        c->pop_staging = nullptr;
+        return fail3(c, LBD_ENOMEM, "population staging allocation failed");
+    }
+    const Geo3 G = geo(c);
+    if (c->params.base.precision == LBD_FP64)
+        k_pops<double><<<1024, 256, 0, c->stream>>>(G, (const double *)c->g[c->cur], c->pop_staging);
+    else
+        k_pops<float><<<1024, 256, 0, c->stream>>>(G, (const float *)c->g[c->cur], c->pop_staging);
+    CK3(c, cudaGetLastError());
+    CK3(c, cudaMemcpyAsync(f, c->pop_staging, sizeof(double) * Q * c->N, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK3(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd3_diagnostics(lbd3_ctx *c, double rx, double ry, double rz, lbd3_diag *out) {
+    if (!c || !out) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (!(rx >= 0 && rx < c->grid.nx && ry >= 0 && ry < c->grid.ny && rz >= 0 && rz < c->grid.nz))
+        return fail3(c, LBD_EINVAL, "reference point outside the lattice");
+    CK3(c, cudaSetDevice(c->dev));
+    const Geo3 G = geo(c);
+    if (c->params.base.precision == LBD_FP64)
+        k_red<double><<<RED3_BLOCKS, RED3_THREADS, 0, c->stream>>>(
+            G, (const double *)c->g[c->cur], (const double *)c->phi[c->cur],
+            (const double *)c->psi[c->cur], rx, ry, rz, c->red);
+    else
+        k_red<float><<<RED3_BLOCKS, RED3_THREADS, 0, c->stream>>>(
+            G, (const float *)c->g[c->cur], (const float *)c->phi[c->cur],
+            (const float *)c->psi[c->cur], rx, ry, rz, c->red);
+    CK3(c, cudaGetLastError());
+    k_red_final<<<1, 32, 0, c->stream>>>(RED3_BLOCKS, c->red, c->red + NRED3 * RED3_BLOCKS);
+    CK3(c, cudaGetLastError());
+    double h[NRED3];
+    CK3(c, cudaMemcpyAsync(h, c->red + NRED3 * RED3_BLOCKS, sizeof h, cudaMemcpyDeviceToHost,
+                           c->stream));
+    CK3(c, cudaStreamSynchronize(c->stream));
+    out->sum_rho = (double)c->N + h[0];
+    out->sum_phi = h[1];
+    out->sum_psi = h[2];
+    out->mass_pos = h[6];
+    out->cm_x = h[6] > 0 ? rx + h[3] / h[6] : NAN;
+    out->cm_y = h[6] > 0 ? ry + h[4] / h[6] : NAN;
+    out->cm_z = h[6] > 0 ? rz + h[5] / h[6] : NAN;
+    out->nonfinite = (int64_t)h[7];
+    return LBD_OK;
+}
+
+int lbd3_synchronize(lbd3_ctx *c) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    CK3(c, cudaSetDevice(c->dev));
+    CK3(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd3_get_time(const lbd3_ctx *c, int64_t *t) {
+    if (!c || !t) return LBD_EINVAL;
+    *t = c->t;
+    return LBD_OK;
+}
+
+}  // extern "C"

@@ -138,6 +138,50 @@ def ellipse_fields(n, R, eps, B1=0.0, a=-0.001, b=0.001, B0=0.006, psi_bg=0.1):
     return phi, np.full((n, n), float(psi_bg))
 
 
+def sphere_fields(nx, ny, nz, spheres, *, a=-0.001, b=0.001, B0=0.006, B1=-0.05, psi_bg=0.1,
+                  noise=0.0, seed=0):
+    """phi, psi of shape (nz, ny, nx) for droplets (x, y, z, R) on a periodic 3D
+    lattice: phi = phi_eq tanh(max_k (R_k - r_k) / xi0), r_k the minimum-image
+    distance; psi = psi_bg plus seeded uniform noise of half-width `noise`."""
+    xi = interface_width(a, B0, B1, psi_bg)
+    zz, yy, xx = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    best = np.full((nz, ny, nx), -np.inf)
+    for (cx, cy, cz, R) in spheres:
+        d = [_min_image(xx - cx, nx), _min_image(yy - cy, ny), _min_image(zz - cz, nz)]
+        best = np.maximum(best, R - np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2))
+    phi = math.sqrt(-a / b) * np.tanh(best / xi)
+    u = 2.0 * uniform01(seed, nx * ny * nz).reshape(nz, ny, nx) - 1.0
+    return phi, psi_bg + noise * u
+
+
+def emulsion3(n=256, count=64, R=16.0, seed=9):
+    """count spherical droplets of radius R at seeded non-overlapping positions
+    (minimum centre distance 2R + 4 xi0, periodic) in an n^3 box; psi = 0.1
+    with noise +-0.005; one source ball of radius R/4 inside each droplet,
+    tangent to its +x surface."""
+    xi0 = interface_width(PAPER["a"], PAPER["B0"], PAPER["B1"], 0.1)
+    dmin = 2 * R + 4 * xi0
+    centres = []
+    k = 0
+    while len(centres) < count and k < 100000:
+        u = uniform01(seed + 7919 * k, 3) * n
+        k += 1
+        ok = True
+        for c in centres:
+            d = [_min_image(u[i] - c[i], n) for i in range(3)]
+            if d[0] ** 2 + d[1] ** 2 + d[2] ** 2 < dmin ** 2:
+                ok = False
+                break
+        if ok:
+            centres.append((float(u[0]), float(u[1]), float(u[2])))
+    spheres = [(x, y, z, R) for (x, y, z) in centres]
+    phi, psi = sphere_fields(n, n, n, spheres, noise=0.005, seed=seed)
+    srcs = [((x + R - R / 4) % n, y, z, R / 4) for (x, y, z) in centres]
+    params = dict(PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+    return dict(nx=n, ny=n, nz=n, phi=phi, psi=psi, params=params, sources=srcs,
+                droplets=[dict(x=x, y=y, z=z, R=R) for (x, y, z) in centres])
+
+
 def two_droplets(nx=512, ny=256, R=25.0, sep=80.0, offset=0.0, seed=2):
     """Two droplets R on nx x ny, centres (nx/2 -+ sep/2, ny/2 -+ offset/2), each
     with a psi ramp pointing at its partner of seeded amplitude."""

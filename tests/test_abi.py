@@ -68,3 +68,40 @@ def test_strerror_names_codes(lib):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert lib.lbd_strerror(code).startswith(b"LBD_")
     assert (32, 8) in lbd.tiles() and (240, 64) in lbd.tiles()
+
+
+HEADER3 = os.path.join(ROOT, "include", "lbd3.h")
+
+
+def declared3():
+    src = open(HEADER3).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbd3_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_3d_symbols_exported_and_bound(lib):
+    from paper_1711_10984_gb300 import lbd3
+    names = declared3()
+    assert "lbd3_create" in names and "lbd3_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(lbd3.SIGNATURES) == names
+
+
+def test_3d_struct_layout():
+    from paper_1711_10984_gb300 import lbd3
+    assert ctypes.sizeof(lbd3.lbd3_params) == ctypes.sizeof(lbd.lbd_params) + 2 * 8 + 2 * 4 + 64 * 32
+    assert ctypes.sizeof(lbd3.lbd3_diag) == 7 * 8 + 8
+    assert ctypes.sizeof(lbd3.lbd3_grid) == 12
+
+
+@pytest.mark.parametrize("grid,bad", [((8, 8, 8), dict(tau=0.5)), ((8, 8, 8), dict(flags=16)),
+                                      ((8, 8, 8), dict(b=-1.0)), ((0, 8, 8), {}),
+                                      ((8, 8, 5000), {})])
+def test_3d_create_rejects_bad_input(lib, grid, bad):
+    from paper_1711_10984_gb300 import lbd3
+    lbd3.load()
+    p = lbd3.make_params(**bad)
+    g = lbd3.lbd3_grid(*grid)
+    h = ctypes.c_void_p()
+    assert lib.lbd3_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h)) == lbd.LBD_EINVAL
