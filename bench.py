@@ -320,6 +320,30 @@ def time_tracking(lbd, w, reps=20):
                 points=int(sum(f["points"] for f in fit)))
 
 
+def time_3d(torch, stream, steps=100, n=256):
+    """The 3D (D3Q19) step on a periodic n^3 box with 64 seeded spherical
+    droplets (R = 16, a source ball in each, sink on), FP32, CUDA events on the
+    launching stream; 5 kernel launches per step."""
+    from paper_1711_10984_gb300 import inputs, lbd, lbd3
+    lbd3.load()
+    w = inputs.emulsion3(n=n)
+    sim = lbd3.Sim3(n, n, n, precision=lbd.LBD_FP32, sources=w["sources"],
+                    stream=stream.cuda_stream, **w["params"])
+    sim.set_fields(w["phi"], w["psi"])
+    sim.step(5)
+    sim.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    d = sim.diagnostics(*(w["droplets"][0][k] % n for k in ("x", "y", "z")))
+    sim.close()
+    return dict(n=n, steps=steps, ms_per_step=ms, mlups=n ** 3 / ms / 1e3,
+                nonfinite=d["nonfinite"])
+
+
 def cpu_baseline(w, budget_s=12.0):
     """The FP64 oracle as it stands on the host cores, on the same 2048^2
     workload, for as many whole steps as fit in about budget_s seconds."""
@@ -377,6 +401,7 @@ def run_ours(args):
     rc = time_precision(torch, lbd, autotune, wc, lbd.LBD_FP32, nw, args.warmup, stream,
                         dev_name, barrier)
     trk = time_tracking(lbd, w) if rank == 0 else None
+    r3 = time_3d(torch, stream, steps=min(args.steps, 100))
 
     maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
@@ -424,6 +449,15 @@ def run_ours(args):
         "fp32_drift": r32["drift"],
         "adjoint_forward_cost": adj,
         "tracking": trk,
+        "three_d": {"workload": "D3Q19 coupled step, periodic 256^3 box, 64 seeded spherical "
+                                "droplets R=16 with a source ball each, sink on, FP32",
+                    "value": round(world * r3["mlups"], 1), "unit": "MLUPS",
+                    "ms_per_step": r3["ms_per_step"], "steps": r3["steps"],
+                    "roofline": {"bound": "hbm", "unit": "GB/s", "peak": hbm,
+                                 "bytes_per_site": 168,
+                                 "achieved": round(r3["mlups"] * 1e6 * 168 / 1e9, 1),
+                                 "frac": round(r3["mlups"] * 1e6 * 168 / 1e9 / hbm, 4)},
+                    "nonfinite": r3["nonfinite"]},
         "walls": {"workload": "the same 2048x2048 emulsion between bounce-back plates "
                               "(LBD_WALLS), FP32",
                   "value": round(whole_job_mlups(N, world, nw, tw), 1),

@@ -32,7 +32,8 @@ extern "C" {
 typedef struct lbd3_ctx lbd3_ctx;
 
 typedef struct {
-    int32_t nx, ny, nz; /* each in [1, 4096], nx*ny*nz <= 2^31 */
+    int32_t nx, ny, nz; /* each in [1, 4096]; 19 * nz * ny * (nx rounded up to 128
+                           bytes) < 2^32 elements (512^3 in FP32 and FP64) */
 } lbd3_grid;
 
 typedef struct {

@@ -24,9 +24,20 @@
 namespace {
 
 constexpr int Q = 19;
-__constant__ int c_ex[Q] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
-__constant__ int c_ey[Q] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
-__constant__ int c_ez[Q] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+// D3Q19 velocity components of direction i (the order of include/lbd3.h), as
+// compile-time functions so that unrolled loops fold every neighbour index
+__host__ __device__ constexpr int c_ex(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int c_ey(int i) {
+    return (i == 3 || i == 7 || i == 10 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 8 || i == 9 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int c_ez(int i) {
+    return (i == 5 || i == 11 || i == 14 || i == 15 || i == 18) ? 1
+           : (i == 6 || i == 12 || i == 13 || i == 16 || i == 17) ? -1 : 0;
+}
 
 __host__ __device__ inline double wq(int i) {
     return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -48,10 +59,11 @@ struct Arg3 {
     int frozen;
 };
 
-// Offsets of the 27 sites around (x, y, z) (periodic), ox/oy/oz index -1, 0, 1.
+// Offsets of the 27 sites around (x, y, z) (periodic), ox/oy/oz index -1, 0, 1;
+// 32-bit (the host keeps 19 * vol below 2^32).
 struct Nb {
-    long long ox[3], oy[3], oz[3];
-    __device__ long long at(int ex, int ey, int ez) const {
+    unsigned ox[3], oy[3], oz[3];
+    __device__ unsigned at(int ex, int ey, int ez) const {
         return ox[ex + 1] + oy[ey + 1] + oz[ez + 1];
     }
 };
@@ -62,12 +74,13 @@ __device__ inline Nb neighbours(const Arg3<T> &p, int x, int y, int z) {
     n.ox[0] = x ? x - 1 : p.nx - 1;
     n.ox[1] = x;
     n.ox[2] = x + 1 < p.nx ? x + 1 : 0;
-    n.oy[0] = (long long)(y ? y - 1 : p.ny - 1) * p.pitch;
-    n.oy[1] = (long long)y * p.pitch;
-    n.oy[2] = (long long)(y + 1 < p.ny ? y + 1 : 0) * p.pitch;
-    n.oz[0] = (long long)(z ? z - 1 : p.nz - 1) * p.plane;
-    n.oz[1] = (long long)z * p.plane;
-    n.oz[2] = (long long)(z + 1 < p.nz ? z + 1 : 0) * p.plane;
+    const unsigned pitch = (unsigned)p.pitch, plane = (unsigned)p.plane;
+    n.oy[0] = (unsigned)(y ? y - 1 : p.ny - 1) * pitch;
+    n.oy[1] = (unsigned)y * pitch;
+    n.oy[2] = (unsigned)(y + 1 < p.ny ? y + 1 : 0) * pitch;
+    n.oz[0] = (unsigned)(z ? z - 1 : p.nz - 1) * plane;
+    n.oz[1] = (unsigned)z * plane;
+    n.oz[2] = (unsigned)(z + 1 < p.nz ? z + 1 : 0) * plane;
     return n;
 }
 
@@ -75,7 +88,7 @@ __device__ inline Nb neighbours(const Arg3<T> &p, int x, int y, int z) {
 template <typename T>
 __device__ inline void gather(const T *A, const Nb &n, T v[Q]) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = A[n.at(c_ex[i], c_ey[i], c_ez[i])];
+    for (int i = 0; i < Q; ++i) v[i] = A[n.at(c_ex(i), c_ey(i), c_ez(i))];
 }
 
 // Isotropic D3Q19 gradient and Laplacian of the gathered values.
@@ -85,9 +98,9 @@ __device__ inline void grad_lap(const T v[Q], T &gx, T &gy, T &gz, T &lap) {
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
         const T w = (T)wq(i);
-        sx += w * (T)c_ex[i] * v[i];
-        sy += w * (T)c_ey[i] * v[i];
-        sz += w * (T)c_ez[i] * v[i];
+        sx += w * (T)c_ex(i) * v[i];
+        sy += w * (T)c_ey(i) * v[i];
+        sz += w * (T)c_ez(i) * v[i];
         sl += w * (v[i] - v[0]);
     }
     gx = T(3) * sx;
@@ -106,7 +119,7 @@ __device__ inline void grad3(const T v[Q], T &gx, T &gy, T &gz) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;                    \
     const int y = blockIdx.y, z = blockIdx.z;                               \
     if (x >= (p).nx) return;                                                \
-    const long long s = (long long)z * (p).plane + (long long)y * (p).pitch + x;
+    const unsigned s = (unsigned)z * (unsigned)(p).plane + (unsigned)y * (unsigned)(p).pitch + x;
 
 // mu_phi and m at t^n (Eqs. 3, 5)
 template <typename T>
@@ -149,11 +162,11 @@ __global__ void k_lb(const Arg3<T> p, double *out) {
     T dn = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-        g[i] = p.g_in[i * p.vol + n.at(-c_ex[i], -c_ey[i], -c_ez[i])];  // from x - e_i
+        g[i] = p.g_in[i * (unsigned)p.vol + n.at(-c_ex(i), -c_ey(i), -c_ez(i))];  // from x - e_i
         dn += g[i];
-        jx += (T)c_ex[i] * g[i];
-        jy += (T)c_ey[i] * g[i];
-        jz += (T)c_ez[i] * g[i];
+        jx += (T)c_ex(i) * g[i];
+        jy += (T)c_ey(i) * g[i];
+        jz += (T)c_ez(i) * g[i];
     }
     const T rho = T(1) + dn;
     const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
@@ -171,11 +184,11 @@ __global__ void k_lb(const Arg3<T> p, double *out) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
         const T w = (T)wq(i);
-        const T ex = (T)c_ex[i], ey = (T)c_ey[i], ez = (T)c_ez[i];
+        const T ex = (T)c_ex(i), ey = (T)c_ey(i), ez = (T)c_ez(i);
         const T eu = ex * ux + ey * uy + ez * uz, eF = ex * Fx + ey * Fy + ez * Fz;
         const T geq = w * (dn + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
         const T Fi = p.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
-        p.g_out[i * p.vol + s] = g[i] - p.omega * (g[i] - geq) + Fi;
+        p.g_out[i * (unsigned)p.vol + s] = g[i] - p.omega * (g[i] - geq) + Fi;
     }
     p.ux[s] = p.frozen ? p.ux0 : ux;
     p.uy[s] = p.frozen ? p.uy0 : uy;
@@ -192,7 +205,7 @@ __global__ void k_advect(const Arg3<T> p) {
     const T P0 = p.phi[s], C0 = p.psi[s];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        const long long up = n.at(a == 0, a == 1, a == 2), dn = n.at(-(a == 0), -(a == 1), -(a == 2));
+        const unsigned up = n.at(a == 0, a == 1, a == 2), dn = n.at(-(a == 0), -(a == 1), -(a == 2));
         const T *U = a == 0 ? p.ux : (a == 1 ? p.uy : p.uz);
         const T fp = T(0.5) * (U[s] + U[up]), fm = T(0.5) * (U[dn] + U[s]);
         netp += fp * (fp > T(0) ? P0 : p.phi[up]) - fm * (fm > T(0) ? p.phi[dn] : P0);
@@ -272,10 +285,10 @@ __global__ void k_init(const Geo3 G, const double *in, T *g, T *phi, T *psi) {
         phi[s] = (T)in[4 * N + d];
         psi[s] = (T)in[5 * N + d];
         for (int i = 0; i < Q; ++i) {
-            const int xs = pw(x + c_ex[i], G.nx), ys = pw(y + c_ey[i], G.ny), zs = pw(z + c_ez[i], G.nz);
+            const int xs = pw(x + c_ex(i), G.nx), ys = pw(y + c_ey(i), G.ny), zs = pw(z + c_ez(i), G.nz);
             const long long q = ((long long)zs * G.ny + ys) * G.nx + xs;
             const double n = in[q], u = in[N + q], v = in[2 * N + q], w = in[3 * N + q];
-            const double eu = c_ex[i] * u + c_ey[i] * v + c_ez[i] * w, usq = u * u + v * v + w * w;
+            const double eu = c_ex(i) * u + c_ey(i) * v + c_ez(i) * w, usq = u * u + v * v + w * w;
             g[i * G.vol + s] = (T)(wq(i) * ((n - 1.0) + n * (3.0 * eu + 4.5 * eu * eu - 1.5 * usq)));
         }
     }
@@ -290,8 +303,8 @@ __global__ void k_pops(const Geo3 G, const T *g, double *f) {
         int x, y, z;
         coords(G, d, x, y, z);
         for (int i = 0; i < Q; ++i) {
-            const long long s = (long long)pw(z - c_ez[i], G.nz) * G.plane +
-                                (long long)pw(y - c_ey[i], G.ny) * G.pitch + pw(x - c_ex[i], G.nx);
+            const long long s = (long long)pw(z - c_ez(i), G.nz) * G.plane +
+                                (long long)pw(y - c_ey(i), G.ny) * G.pitch + pw(x - c_ex(i), G.nx);
             f[i * N + d] = wq(i) + (double)g[i * G.vol + s];
         }
     }
@@ -600,6 +613,11 @@ int lbd3_create(const lbd3_grid *grid, const lbd3_params *params, void *stream, 
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || grid->nx > 4096 || grid->ny > 4096 ||
         grid->nz > 4096 || (long long)grid->nx * grid->ny * grid->nz > (1LL << 31))
         return LBD_EINVAL;
+    {   // the kernels index the 19 population planes with 32-bit offsets
+        const long long al = 128 / (params->base.precision == LBD_FP64 ? 8 : 4);
+        const long long vol = (grid->nx + al - 1) / al * al * grid->ny * grid->nz;
+        if (19 * vol >= (1LL << 32)) return LBD_EINVAL;
+    }
     if (check3(nullptr, params) != LBD_OK) return LBD_EINVAL;
     lbd3_ctx *c = new (std::nothrow) lbd3_ctx();
     if (!c) return LBD_ENOMEM;
