@@ -2,6 +2,8 @@
 
     python -m paper_1711_10984_gb300.run_case --workload emulsion --n 2048 \
         --precision fp32 --steps 10 [--tile 32x16]
+    python -m paper_1711_10984_gb300.run_case --workload emulsion3 --n 128 \
+        --droplets 8 --radius 12 --steps 7          (the 3D step on an n^3 box)
 
 Prints the final diagnostics.  Used as the profiling target of the ncu
 summaries under profiles/.
@@ -24,14 +26,28 @@ def make(workload, n):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="emulsion", choices=["emulsion", "single", "two"])
+    ap.add_argument("--workload", default="emulsion",
+                    choices=["emulsion", "single", "two", "emulsion3"])
+    ap.add_argument("--droplets", type=int, default=64, help="emulsion3: droplet count")
+    ap.add_argument("--radius", type=float, default=16.0, help="emulsion3: droplet radius")
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--tile", default=None)
     a = ap.parse_args(argv)
-    w = make(a.workload, a.n)
     prec = lbd.LBD_FP32 if a.precision == "fp32" else lbd.LBD_FP64
+    if a.workload == "emulsion3":
+        from . import lbd3
+        lbd3.load()
+        w = inputs.emulsion3(n=a.n, count=a.droplets, R=a.radius)
+        sim = lbd3.Sim3(a.n, a.n, a.n, precision=prec, sources=w["sources"], **w["params"])
+        sim.set_fields(w["phi"], w["psi"])
+        sim.step(a.steps)
+        d0 = w["droplets"][0]
+        print(json.dumps(sim.diagnostics(d0["x"] % a.n, d0["y"] % a.n, d0["z"] % a.n)))
+        sim.close()
+        return
+    w = make(a.workload, a.n)
     sim = lbd.Sim(w["nx"], w["ny"], precision=prec, sources=w["sources"], **w["params"])
     if a.tile:
         sim.set_tile(*[int(v) for v in a.tile.split("x")])
