@@ -138,6 +138,35 @@ int lbd_step(lbd_ctx *ctx, int64_t nsteps);
  * current phi, psi.  Synchronises the stream. */
 int lbd_get_fields(lbd_ctx *ctx, double *rho, double *ux, double *uy, double *phi, double *psi);
 
+/* One droplet of a seeded initial state (lbd_init_droplets). */
+typedef struct {
+    double x, y, R;       /* centre and radius                                      */
+    double psi_mean;      /* psi inside the droplet                                 */
+    double psi_noise;     /* half-width of the uniform noise added inside           */
+    double gx, gy;        /* linear psi ramp inside: + gx (x - x0)/R + gy (y - y0)/R */
+} lbd_droplet_init;
+
+/* Seeded initial state built on the device (the initial conditions of
+ * Sections 3-4: tanh droplets in a surfactant bath), at rest (rho = 1, u = 0,
+ * f = f^eq):  phi = phi_eq tanh(max_k (R_k - r_k) / xi), phi_eq = sqrt(-a/b),
+ * r_k the minimum-image distance to droplet k (round half to even); xi <= 0
+ * takes xi0 = sqrt(2 (B0 + B1 psi_bg) / -a).  psi = psi_bg, except at sites with
+ * max_k (R_k - r_k) > 0, which take psi_mean + psi_noise (2 u - 1) + ramp of the
+ * droplet k attaining the maximum, u = uniform in [0, 1) of SplitMix64 draw
+ * y*nx + x of the stream `seed` ((draw >> 11) * 2^-53; draw k is the published
+ * finaliser of seed + (k+1) * 0x9E3779B97F4A7C15).  1 <= n <= LBD_MAX_DROPLETS.
+ * LBD_EUNSTABLE when the psi range this can produce reaches psi <= 0 or
+ * B(psi) <= 0; t is unchanged.  Synchronises. */
+int lbd_init_droplets(lbd_ctx *ctx, int32_t n, const lbd_droplet_init *d, double psi_bg,
+                      double xi, uint64_t seed);
+
+/* As lbd_get_fields, into caller-owned DEVICE arrays of nx*ny elements of the
+ * context's precision (double for LBD_FP64, float for LBD_FP32), site (x,y) at
+ * y*nx + x; any pointer may be NULL.  Asynchronous on the context's stream: the
+ * arrays hold the fields once the stream reaches this point.  The pointers are
+ * not checked (they must be device memory of the context's device). */
+int lbd_get_fields_device(lbd_ctx *ctx, void *rho, void *ux, void *uy, void *phi, void *psi);
+
 /* Copy the pre-collision populations f_i(r, t) to a host array of 9*nx*ny
  * doubles, plane i (velocity e_i) at offset i*nx*ny; velocities in the order
  * (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).  Synchronises. */

@@ -149,6 +149,58 @@ __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, co
     }
 }
 
+struct DropInits {
+    lbd_droplet_init d[LBD_MAX_DROPLETS];
+};
+
+__device__ inline uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+    uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ inline double min_image_even(double d, double L) { return d - L * rint(d / L); }
+
+// phi and psi of the seeded droplets (lbd_init_droplets) into the pitched buffers
+template <typename T>
+__global__ void init_droplets_kernel(int nx, int ny, long long pitch, int n, DropInits D,
+                                     double phieq, double xi, double psi_bg, uint64_t seed,
+                                     T *phi, T *psi) {
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        double best = -INFINITY, bdx = 0, bdy = 0;
+        int owner = -1;
+        for (int k = 0; k < n; ++k) {
+            const double dx = min_image_even(x - D.d[k].x, nx), dy = min_image_even(y - D.d[k].y, ny);
+            const double v = D.d[k].R - sqrt(dx * dx + dy * dy);
+            if (v > best) {
+                best = v;
+                owner = k;
+                bdx = dx;
+                bdy = dy;
+            }
+        }
+        const long long o = (long long)y * pitch + x;
+        phi[o] = (T)(phieq * tanh(best / xi));
+        double c = psi_bg;
+        if (owner >= 0 && best > 0) {
+            const lbd_droplet_init &d = D.d[owner];
+            const double u = (double)(splitmix64_at(seed, (uint64_t)s) >> 11) * 0x1.0p-53;
+            c = d.psi_mean + d.psi_noise * (2.0 * u - 1.0) + d.gx * bdx / d.R + d.gy * bdy / d.R;
+        }
+        psi[o] = (T)c;
+    }
+}
+
+__global__ void to_float_kernel(long long n, const double *a, float *b) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x)
+        b[s] = (float)a[s];
+}
+
 __global__ void fill_kernel(double *a, long long n, double v) {
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x)
@@ -825,6 +877,73 @@ int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi,
             CK(c, cudaMemcpyAsync(outs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
                                   c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_init_droplets(lbd_ctx *c, int32_t n, const lbd_droplet_init *d, double psi_bg, double xi,
+                      uint64_t seed) {
+    if (!c || !d) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    if (n < 1 || n > LBD_MAX_DROPLETS)
+        return fail(c, LBD_EINVAL, "n must be in [1, %d]", LBD_MAX_DROPLETS);
+    const lbd_params &p = c->params;
+    if (!(p.a < 0) || !(p.b > 0)) return fail(c, LBD_EINVAL, "droplets need a < 0 < b");
+    if (!std::isfinite(psi_bg) || !std::isfinite(xi)) return fail(c, LBD_EINVAL, "non-finite psi_bg or xi");
+    // bounds of psi: inside |x - x0|, |y - y0| < R, so each ramp term is below |g|
+    double lo = psi_bg, hi = psi_bg;
+    DropInits D;
+    for (int k = 0; k < n; ++k) {
+        const lbd_droplet_init &q = d[k];
+        const double v[7] = {q.x, q.y, q.R, q.psi_mean, q.psi_noise, q.gx, q.gy};
+        for (double e : v)
+            if (!std::isfinite(e)) return fail(c, LBD_EINVAL, "droplet %d: non-finite value", k);
+        if (!(q.R > 0)) return fail(c, LBD_EINVAL, "droplet %d: R must be > 0", k);
+        const double w = std::fabs(q.psi_noise) + std::fabs(q.gx) + std::fabs(q.gy);
+        lo = std::min(lo, q.psi_mean - w);
+        hi = std::max(hi, q.psi_mean + w);
+        D.d[k] = q;
+    }
+    if (!(lo > 0) || !(p.B0 + p.B1 * lo > 0) || !(p.B0 + p.B1 * hi > 0))
+        return fail(c, LBD_EUNSTABLE, "the droplets' psi range reaches psi <= 0 or B(psi) <= 0");
+    const double kappa = p.B0 + p.B1 * psi_bg;
+    const double w0 = xi > 0 ? xi : std::sqrt(2.0 * kappa / -p.a);
+    if (!(w0 > 0)) return fail(c, LBD_EINVAL, "interface width must be > 0");
+    CK(c, cudaSetDevice(c->dev));
+    const size_t fbytes = (size_t)c->plane * c->esz;
+    CK(c, cudaMemsetAsync(c->g[c->cur], 0, 9 * fbytes, c->stream));  // f = w_i: rho = 1, u = 0
+    const int nb = grid_for(c->N);
+    const double phieq = std::sqrt(-p.a / p.b);
+    if (p.precision == LBD_FP64)
+        init_droplets_kernel<double><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, n, D, phieq, w0, psi_bg, seed,
+            (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+    else
+        init_droplets_kernel<float><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, n, D, phieq, w0, psi_bg, seed,
+            (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_get_fields_device(lbd_ctx *c, void *rho, void *ux, void *uy, void *phi, void *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    int rc = eval_fields(c);
+    if (rc != LBD_OK) return rc;
+    void *outs[5] = {rho, ux, uy, phi, psi};
+    const long long N = (long long)c->N;
+    for (int k = 0; k < 5; ++k) {
+        if (!outs[k]) continue;
+        const double *src = c->staging + k * N;
+        if (c->params.precision == LBD_FP64) {
+            CK(c, cudaMemcpyAsync(outs[k], src, sizeof(double) * N, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+        } else {
+            to_float_kernel<<<grid_for(c->N), 256, 0, c->stream>>>(N, src, (float *)outs[k]);
+            CK(c, cudaGetLastError());
+        }
+    }
     return LBD_OK;
 }
 

@@ -56,6 +56,10 @@ class lbd_droplet(ctypes.Structure):
 
 LBD_MAX_DROPLETS = 64
 
+
+class lbd_droplet_init(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("x", "y", "R", "psi_mean", "psi_noise", "gx", "gy")]
+
 _P = ctypes.c_void_p
 # name -> (restype, argtypes); the list mirrors include/lbd.h
 SIGNATURES = {
@@ -75,6 +79,9 @@ SIGNATURES = {
     "lbd_squirmer": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lbd_droplet),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int64)]),
+    "lbd_get_fields_device": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lbd_init_droplets": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lbd_droplet_init),
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_uint64]),
     "lbd_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
     "lbd_tiles": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                  ctypes.c_int32]),
@@ -205,6 +212,23 @@ class Sim:
         out = [np.empty(self.N) for _ in range(5)]
         self._check(load().lbd_get_fields(self._h, *[o.ctypes.data_as(_dp) for o in out]))
         return tuple(o.reshape(self.ny, self.nx) for o in out)
+
+    def init_droplets(self, droplets, psi_bg=0.1, xi=0.0, seed=0):
+        """lbd_init_droplets: droplets as dicts with keys x, y, R and optional
+        psi_mean (default psi_bg), noise, gx, gy (the recipe of
+        inputs.droplet_fields)."""
+        n = len(droplets)
+        arr = (lbd_droplet_init * n)(*[lbd_droplet_init(
+            d["x"], d["y"], d["R"], d.get("psi_mean", psi_bg), d.get("noise", 0.0),
+            d.get("gx", 0.0), d.get("gy", 0.0)) for d in droplets])
+        self._check(load().lbd_init_droplets(self._h, n, arr, float(psi_bg), float(xi),
+                                             int(seed) & 0xFFFFFFFFFFFFFFFF))
+
+    def fields_device(self, rho=0, ux=0, uy=0, phi=0, psi=0):
+        """lbd_get_fields_device into caller-owned device buffers given as raw
+        addresses (0 = skip), e.g. torch tensors' data_ptr()."""
+        ptrs = [ctypes.c_void_p(int(a)) if a else None for a in (rho, ux, uy, phi, psi)]
+        self._check(load().lbd_get_fields_device(self._h, *ptrs))
 
     def populations(self):
         f = np.empty(9 * self.N)
