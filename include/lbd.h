@@ -172,6 +172,14 @@ int lbd_get_fields_device(lbd_ctx *ctx, void *rho, void *ux, void *uy, void *phi
  * (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1).  Synchronises. */
 int lbd_get_populations(lbd_ctx *ctx, double *f);
 
+/* Restore pre-collision populations f_i(r, t) from a host array laid out as
+ * lbd_get_populations writes it (9 planes of nx*ny doubles), e.g. to resume
+ * from a checkpoint: lbd_set_fields (phi, psi), then lbd_set_populations,
+ * then lbd_set_time.  The values are stored in the context's precision (for
+ * FP64 they round-trip to within the rounding of f - w).  LBD_ENONFINITE for
+ * a NaN or Inf.  Synchronises. */
+int lbd_set_populations(lbd_ctx *ctx, const double *f);
+
 /* Global diagnostics at the current time.  (ref_x, ref_y) in [0,nx) x [0,ny)
  * is the reference point for the minimum-image centre of mass (pass the
  * previous centre to follow a moving droplet).  Synchronises. */

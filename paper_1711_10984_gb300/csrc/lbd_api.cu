@@ -235,6 +235,35 @@ __global__ void populations_kernel(int nx, int ny, long long pitch, long long pl
     }
 }
 
+// Inverse of populations_kernel: pre-collision f_i(x) (dense doubles) into the
+// pull layout, buffer_i(x - e_i) = f_i(x) - w_i (with walls, buffer_{-i}(x) where
+// x - e_i lies beyond a plate).
+template <typename T>
+__global__ void set_populations_kernel(int nx, int ny, long long pitch, long long plane, int walls,
+                                       const double *f, T *g) {
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                         1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        for (int i = 0; i < 9; ++i) {
+            int xs = x - ex[i], ys = y - ey[i];
+            int k = i;
+            if (walls && (ys < 0 || ys >= ny)) {
+                xs = x;
+                ys = y;
+                k = i < 5 ? (i + 1) % 4 + 1 : (i - 3) % 4 + 5;
+            }
+            xs = xs < 0 ? xs + nx : (xs >= nx ? xs - nx : xs);
+            ys = ys < 0 ? ys + ny : (ys >= ny ? ys - ny : ys);
+            g[k * plane + (long long)ys * pitch + xs] = (T)(f[i * N + s] - w[i]);
+        }
+    }
+}
+
 // Block-wide reduction of the NRED slots (sums, then two minima).
 __device__ void block_reduce(double v[NRED], double *smem /* [NRED][32] */) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -944,6 +973,35 @@ int lbd_get_fields_device(lbd_ctx *c, void *rho, void *ux, void *uy, void *phi, 
             CK(c, cudaGetLastError());
         }
     }
+    return LBD_OK;
+}
+
+int lbd_set_populations(lbd_ctx *c, const double *f) {
+    if (!c || !f) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    const size_t n9 = 9 * c->N;
+    for (size_t k = 0; k < n9; ++k)
+        if (!std::isfinite(f[k])) return fail(c, LBD_ENONFINITE, "non-finite population %zu", k);
+    CK(c, cudaSetDevice(c->dev));
+    if (!c->pop_staging) {
+        if (cudaMalloc(&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->pop_staging = nullptr;
+            return fail(c, LBD_ENOMEM, "population staging allocation failed");
+        }
+    }
+    CK(c, cudaMemcpyAsync(c->pop_staging, f, n9 * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+    const int nb = grid_for(c->N);
+    const int walls = (c->params.flags & LBD_WALLS) ? 1 : 0;
+    if (c->params.precision == LBD_FP64)
+        set_populations_kernel<double><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, walls, c->pop_staging, (double *)c->g[c->cur]);
+    else
+        set_populations_kernel<float><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, walls, c->pop_staging, (float *)c->g[c->cur]);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
     return LBD_OK;
 }
 

@@ -80,6 +80,7 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_int64)]),
     "lbd_get_fields_device": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "lbd_set_populations": (ctypes.c_int, [_P, _dp]),
     "lbd_init_droplets": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(lbd_droplet_init),
                                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64]),
     "lbd_set_tile": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int32]),
@@ -229,6 +230,13 @@ class Sim:
         addresses (0 = skip), e.g. torch tensors' data_ptr()."""
         ptrs = [ctypes.c_void_p(int(a)) if a else None for a in (rho, ux, uy, phi, psi)]
         self._check(load().lbd_get_fields_device(self._h, *ptrs))
+
+    def set_populations(self, f):
+        """lbd_set_populations from an array shaped like populations()."""
+        a = np.ascontiguousarray(f, dtype=np.float64).ravel()
+        if a.size != 9 * self.N:
+            raise ValueError("expected %d values" % (9 * self.N))
+        self._check(load().lbd_set_populations(self._h, a.ctypes.data_as(_dp)))
 
     def populations(self):
         f = np.empty(9 * self.N)

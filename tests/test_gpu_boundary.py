@@ -81,3 +81,33 @@ def test_fields_device_equals_host_read_back(prec):
     s.synchronize()
     assert np.array_equal(skip.cpu().numpy(), host[3].astype(skip.cpu().numpy().dtype))
     s.close()
+
+
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32], ids=["fp64", "fp32"])
+@pytest.mark.parametrize("flags", [0, lbd.LBD_WALLS], ids=["periodic", "plates"])
+def test_checkpoint_restart(prec, flags):
+    """Resume from (phi, psi, f, t) read back mid-run: the resumed run follows the
+    uninterrupted one (FP32 bitwise; FP64 to the rounding of f - w)."""
+    nx, ny = 128, 64
+    kw = dict(M=0.5, tau=0.8, gamma=1.5e-3, c0=0.09, A0=1e-6, A_max=1e-4, t_on=30)
+    src = [(60.0, 30.0, 3.0)]
+    a = lbd.Sim(nx, ny, precision=prec, sources=src, flags=flags, **kw)
+    a.init_droplets([dict(x=60.0, y=30.0, R=14.0, noise=0.01, gx=0.005)], seed=9)
+    a.step(70)
+    _, _, _, phi, psi = a.fields()
+    f, t = a.populations(), a.t
+    b = lbd.Sim(nx, ny, precision=prec, sources=src, flags=flags, **kw)
+    b.set_fields(phi, psi)
+    b.set_populations(f)
+    b.t = t
+    assert np.array_equal(b.populations(), f) if prec == lbd.LBD_FP32 else \
+        np.abs(b.populations() - f).max() <= 1e-16
+    a.step(100)
+    b.step(100)
+    for x, y in zip(a.fields(), b.fields()):
+        if prec == lbd.LBD_FP32:
+            assert np.array_equal(x, y)
+        else:
+            assert np.abs(x - y).max() <= 1e-13 * max(np.abs(x).max(), 1e-3)
+    a.close()
+    b.close()
