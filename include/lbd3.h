@@ -83,6 +83,12 @@ int lbd3_get_populations(lbd3_ctx *ctx, double *f);
 int lbd3_diagnostics(lbd3_ctx *ctx, double ref_x, double ref_y, double ref_z, lbd3_diag *out);
 int lbd3_synchronize(lbd3_ctx *ctx);
 int lbd3_get_time(const lbd3_ctx *ctx, int64_t *t);
+/* Launch shape of the step: each CTA walks a run of `planes` z planes of a
+ * 32 x 8 tile of the xy plane; 0 restores the automatic choice (about sixteen
+ * CTAs per SM over the lattice, runs of at least four planes).  Results do not
+ * depend on it.  LBD_EINVAL unless 0 <= planes <= nz. */
+int lbd3_set_zrun(lbd3_ctx *ctx, int32_t planes);
+int lbd3_get_zrun(const lbd3_ctx *ctx, int32_t *planes);
 void lbd3_destroy(lbd3_ctx *ctx);
 
 #ifdef __cplusplus

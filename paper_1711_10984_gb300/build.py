@@ -28,7 +28,8 @@ def _stale(out, deps):
 def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".h", ".cuh"))]
-    headers.append(os.path.join(ROOT, "include", "lbd.h"))
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, h) for h in os.listdir(inc) if h.endswith(".h")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -1,9 +1,9 @@
 // lbd3.cu -- the coupled step of arXiv 1711.10984 (Section 2) on the D3Q19
 // lattice, and the C ABI of include/lbd3.h.
 //
-// One step is five kernels, one thread per site, each reading its inputs with
-// their stencil neighbourhood from global memory (neighbour rows and planes
-// are reused from L1/L2):
+// One step is five kernels, one thread per site; each CTA walks a run of z
+// planes of a 32 x 8 tile, the differentiated fields staged in a ring of
+// shared-memory halo planes:
 //   k_chem    mu_phi (Eq. 3), m (Eq. 5) at t^n                       -> mu, m
 //   k_lb      F (Eq. 14), pull f_i, u (Eq. 11), BGK + Guo collision
 //             (Eqs. 10, 12, 13), u for the advection                 -> f, u
@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 
 #include "lbd3.h"
 
@@ -47,6 +48,7 @@ __host__ __device__ inline double wq(int i) {
 template <typename T>
 struct Arg3 {
     int nx, ny, nz;
+    int zl;                       // planes per CTA of the marching kernels
     long long pitch, plane, vol;  // row pitch, pitch * ny, plane * nz (elements)
     const T *g_in;
     T *g_out;
@@ -58,6 +60,188 @@ struct Arg3 {
     T fx, fy, fz, ux0, uy0, uz0;
     int frozen;
 };
+
+// ------------------------------------------------------ z-marching kernels
+// Each CTA owns a TX x TY tile of the xy plane and a run of zl planes, and
+// walks the run in z.  The fields it differentiates pass through a ring of
+// SLOTS shared-memory planes, each the tile with a one-site periodic halo, so
+// that a value is loaded from global memory about HP / NT + 2 / zl times per
+// step instead of once per neighbour (nine xy rows per value with one thread
+// per site).  The planes arrive by cp.async, AHEAD planes ahead of the ones
+// being read.  One barrier per plane: at plane k, after each thread has waited
+// for its own copies of plane k + 1, the barrier makes every copy of plane
+// k + 1 visible and ends every read of plane k - 2, whose slot then receives
+// plane k + 3.  Two fields that are differentiated alike are stored as a pair
+// (interleaved), read with one shared-memory access and, in FP32, combined with
+// the packed FP32x2 instructions.
+constexpr int TX = 32, TY = 8, NT = TX * TY;
+constexpr int HX = TX + 2, HP = HX * (TY + 2);  // 340 values per halo plane
+constexpr int LPT = (HP + NT - 1) / NT;         // halo values a thread copies per plane
+constexpr int AHEAD = 2;
+constexpr int SLOTS = 3 + AHEAD;                // planes k - 1, k, k + 1 read, the rest in flight
+
+extern __shared__ __align__(16) unsigned char lbd3_smem[];
+
+// NP pair fields and NS single fields
+template <int NP, int NS>
+constexpr size_t ring_bytes(size_t esz) {
+    return (size_t)(2 * NP + NS) * SLOTS * HP * esz;
+}
+
+// Two values of one site in the lanes of a vector: FP32 uses the packed FP32x2
+// instructions (FMUL2 / FFMA2), FP64 plain component-wise arithmetic;
+// every lane is rounded as the scalar operation would be.
+template <typename T>
+struct V2t;
+template <>
+struct V2t<float> {
+    using type = float2;
+};
+template <>
+struct V2t<double> {
+    using type = double2;
+};
+template <typename T>
+using V2 = typename V2t<T>::type;
+
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, rounded once
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) {
+    return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 operator*(double2 a, double2 b) {
+    return make_double2(a.x * b.x, a.y * b.y);
+}
+__device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// the lane type of V and a lane value broadcast to V
+template <typename V>
+struct Lane {
+    using type = V;
+    static __device__ __forceinline__ V splat(V s) { return s; }
+};
+template <>
+struct Lane<float2> {
+    using type = float;
+    static __device__ __forceinline__ float2 splat(float s) { return make_float2(s, s); }
+};
+template <>
+struct Lane<double2> {
+    using type = double;
+    static __device__ __forceinline__ double2 splat(double s) { return make_double2(s, s); }
+};
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(unsigned dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(dst), "l"(src), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// The three halo planes around the site being computed.
+template <typename T>
+struct Planes {
+    const V2<T> *pp;  // pair fields, NP x SLOTS x HP pairs, offset by the site's index
+    const T *ps;      // single fields, NS x SLOTS x HP values, offset likewise
+    int om, o0, op;   // slot offsets of planes z - 1, z, z + 1
+    __device__ int off(int ex, int ey, int ez) const {
+        return (ez < 0 ? om : (ez > 0 ? op : o0)) + ey * HX + ex;
+    }
+    __device__ V2<T> pair(int f, int ex, int ey, int ez) const {
+        return pp[f * SLOTS * HP + off(ex, ey, ez)];
+    }
+    __device__ T one(int f, int ex, int ey, int ez) const {
+        return ps[f * SLOTS * HP + off(ex, ey, ez)];
+    }
+};
+
+// Walk the CTA's run of planes; site(x, y, z, s, planes) is called for every
+// lattice site of the tile, s its element offset.  src lists the two fields of
+// each pair, then the single fields.
+template <typename T, int NP, int NS, class Pre, class Site>
+__device__ __forceinline__ void march(const Arg3<T> &p, const T *const (&src)[2 * NP + NS],
+                                      Pre pre, Site site) {
+    T *sm = reinterpret_cast<T *>(lbd3_smem);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * p.zl;
+    const int z1 = min(p.nz, z0 + p.zl);
+    const int x = x0 + tid % TX, y = y0 + tid / TX;
+    const bool live = x < p.nx && y < p.ny;
+    const unsigned pitch = (unsigned)p.pitch, plane = (unsigned)p.plane;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(sm);
+    constexpr int SINGLES = 2 * NP * SLOTS * HP;  // element offset of the single fields
+    unsigned hxy[LPT];
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+        const int e = tid + j * NT;
+        int gx = (x0 + e % HX - 1) % p.nx, gy = (y0 + e / HX - 1) % p.ny;
+        gx += gx < 0 ? p.nx : 0;
+        gy += gy < 0 ? p.ny : 0;
+        hxy[j] = (unsigned)gy * pitch + (unsigned)gx;
+    }
+    // copy plane k (k in [z0 - 1, z1], periodic) into the slot at element offset o
+    auto issue = [&](int k, int o) {
+        if (k <= z1) {
+            const unsigned zo = (unsigned)(k < 0 ? k + p.nz : (k >= p.nz ? k - p.nz : k)) * plane;
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < HP) {
+#pragma unroll
+                    for (int f = 0; f < NP; ++f)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+                            cp_async<sizeof(T)>(
+                                sbase + (unsigned)((2 * (f * SLOTS * HP + o + e) + c) * sizeof(T)),
+                                src[2 * f + c] + zo + hxy[j]);
+#pragma unroll
+                    for (int f = 0; f < NS; ++f)
+                        cp_async<sizeof(T)>(
+                            sbase + (unsigned)((SINGLES + f * SLOTS * HP + o + e) * sizeof(T)),
+                            src[2 * NP + f] + zo + hxy[j]);
+                }
+            }
+        }
+        cp_commit();
+    };
+    int o[SLOTS];  // slot offsets of planes k - 1, k, k + 1, ..., k + AHEAD, and the free slot
+#pragma unroll
+    for (int q = 0; q < SLOTS; ++q) o[q] = q * HP;
+#pragma unroll
+    for (int q = 0; q < SLOTS - 1; ++q) issue(z0 - 1 + q, o[q]);
+    const int c = (tid / TX + 1) * HX + tid % TX + 1;
+    Planes<T> pl;
+    pl.pp = reinterpret_cast<const V2<T> *>(sm) + c;
+    pl.ps = sm + SINGLES + c;
+    for (int k = z0; k < z1; ++k) {
+        const unsigned s = (unsigned)k * plane + (unsigned)y * pitch + (unsigned)x;
+        if (live) pre(x, y, k, s);  // loads that need no ring, issued before the wait
+        cp_wait<AHEAD - 1>();  // this thread's copies of plane k + 1 have landed
+        __syncthreads();
+        issue(k + SLOTS - 2, o[SLOTS - 1]);
+        pl.om = o[0];
+        pl.o0 = o[1];
+        pl.op = o[2];
+        if (live) site(x, y, k, s, pl);
+        const int freed = o[0];
+#pragma unroll
+        for (int q = 0; q < SLOTS - 1; ++q) o[q] = o[q + 1];
+        o[SLOTS - 1] = freed;
+    }
+    cp_wait<0>();
+}
 
 // Offsets of the 27 sites around (x, y, z) (periodic), ox/oy/oz index -1, 0, 1;
 // 32-bit (the host keeps 19 * vol below 2^32).
@@ -84,175 +268,221 @@ __device__ inline Nb neighbours(const Arg3<T> &p, int x, int y, int z) {
     return n;
 }
 
-// The 19 values of field A around the site, in the D3Q19 order.
+// The 19 values of ring pair f (single field f) around the site, in the D3Q19 order.
 template <typename T>
-__device__ inline void gather(const T *A, const Nb &n, T v[Q]) {
+__device__ inline void gather_pair(const Planes<T> &pl, int f, V2<T> v[Q]) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) v[i] = A[n.at(c_ex(i), c_ey(i), c_ez(i))];
+    for (int i = 0; i < Q; ++i) v[i] = pl.pair(f, c_ex(i), c_ey(i), c_ez(i));
+}
+template <typename T>
+__device__ inline void gather_one(const Planes<T> &pl, int f, T v[Q]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) v[i] = pl.one(f, c_ex(i), c_ey(i), c_ez(i));
 }
 
-// Isotropic D3Q19 gradient and Laplacian of the gathered values.
-template <typename T>
-__device__ inline void grad_lap(const T v[Q], T &gx, T &gy, T &gz, T &lap) {
-    T sx = 0, sy = 0, sz = 0, sl = 0;
-#pragma unroll
-    for (int i = 1; i < Q; ++i) {
-        const T w = (T)wq(i);
-        sx += w * (T)c_ex(i) * v[i];
-        sy += w * (T)c_ey(i) * v[i];
-        sz += w * (T)c_ez(i) * v[i];
-        sl += w * (v[i] - v[0]);
+// acc + c * v for a compile-time velocity component c in {-1, 0, 1}: no code for
+// c = 0 (IEEE arithmetic cannot drop an explicit 0 * v), a sign for c = -1;
+// the value is the one of acc + (T)c * v.
+template <int C, typename T>
+__device__ __forceinline__ T acc_e(T acc, T v) {
+    return C > 0 ? acc + v : (C < 0 ? acc - v : acc);
+}
+// acc + c w v, rounded once, for scalars and pairs
+template <int C, typename V, typename S>
+__device__ __forceinline__ V acc_we(V acc, S w, V v) {
+    return C > 0 ? vfma(Lane<V>::splat(w), v, acc)
+                 : (C < 0 ? vfma(Lane<V>::splat(-w), v, acc) : acc);
+}
+// (T)c * v for a compile-time component
+template <int C, typename T>
+__device__ __forceinline__ T mul_e(T v) {
+    return C > 0 ? v : (C < 0 ? -v : T(0));
+}
+
+// f(std::integral_constant<int, i>) for i = I .. N-1, so that each direction's
+// velocity components are template arguments
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (I < N) {
+        f(std::integral_constant<int, I>{});
+        static_for<I + 1, N>(f);
     }
-    gx = T(3) * sx;
-    gy = T(3) * sy;
-    gz = T(3) * sz;
-    lap = T(6) * sl;
 }
 
-template <typename T>
-__device__ inline void grad3(const T v[Q], T &gx, T &gy, T &gz) {
-    T lap;
+// Isotropic D3Q19 gradient and Laplacian of the gathered values (scalars or pairs).
+template <typename V>
+__device__ inline void grad_lap(const V v[Q], V &gx, V &gy, V &gz, V &lap) {
+    using S = typename Lane<V>::type;
+    V sx = Lane<V>::splat(S(0)), sy = sx, sz = sx, sl = sx;
+    static_for<1, Q>([&](auto k) {
+        constexpr int i = decltype(k)::value;
+        const S w = (S)wq(i);
+        sx = acc_we<c_ex(i)>(sx, w, v[i]);
+        sy = acc_we<c_ey(i)>(sy, w, v[i]);
+        sz = acc_we<c_ez(i)>(sz, w, v[i]);
+        sl = vfma(Lane<V>::splat(w), v[i] - v[0], sl);
+    });
+    gx = Lane<V>::splat(S(3)) * sx;
+    gy = Lane<V>::splat(S(3)) * sy;
+    gz = Lane<V>::splat(S(3)) * sz;
+    lap = Lane<V>::splat(S(6)) * sl;
+}
+
+template <typename V>
+__device__ inline void grad3(const V v[Q], V &gx, V &gy, V &gz) {
+    V lap;
     grad_lap(v, gx, gy, gz, lap);
 }
 
-#define LBD3_SITE(p)                                                        \
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;                    \
-    const int y = blockIdx.y, z = blockIdx.z;                               \
-    if (x >= (p).nx) return;                                                \
-    const unsigned s = (unsigned)z * (unsigned)(p).plane + (unsigned)y * (unsigned)(p).pitch + x;
-
-// mu_phi and m at t^n (Eqs. 3, 5)
+// mu_phi and m at t^n (Eqs. 3, 5); ring: the pair (phi, psi)
 template <typename T>
-__global__ void k_chem(const Arg3<T> p) {
-    LBD3_SITE(p)
-    const Nb n = neighbours(p, x, y, z);
-    T P[Q], C[Q];
-    gather(p.phi, n, P);
-    gather(p.psi, n, C);
-    T px, py, pz, lp, cx, cy, cz;
-    grad_lap(P, px, py, pz, lp);
-    grad3(C, cx, cy, cz);
-    const T ph = P[0];
-    p.mu[s] = p.a * ph + p.b * (ph * ph * ph) - (p.B0 + p.B1 * C[0]) * lp -
-              p.B1 * (px * cx + py * cy + pz * cz);
-    p.mm[s] = T(0.5) * p.B1 * (px * px + py * py + pz * pz);
+__global__ void __launch_bounds__(NT) k_chem(const Arg3<T> p) {
+    const T *const src[2] = {p.phi, p.psi};
+    march<T, 1, 0>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+        V2<T> v[Q], gx, gy, gz, lap;
+        gather_pair(pl, 0, v);
+        grad_lap(v, gx, gy, gz, lap);
+        const T ph = v[0].x, c = v[0].y;
+        p.mu[s] = p.a * ph + p.b * (ph * ph * ph) - (p.B0 + p.B1 * c) * lap.x -
+                  p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
+        p.mm[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+    });
 }
 
 // F (Eq. 14), pulled populations, u (Eq. 11) and the BGK + Guo collision
 // (Eqs. 10, 12, 13) on the deviations g = f - w; with FIELDS, rho and u of the
 // current state to dense doubles (rho, ux, uy, uz at d, N + d, 2N + d, 3N + d).
+// Ring: the pair (mu, m) and psi.
 template <typename T, int FIELDS>
-__global__ void k_lb(const Arg3<T> p, double *out) {
-    LBD3_SITE(p)
-    const Nb n = neighbours(p, x, y, z);
-    T v[Q];
-    T gmx, gmy, gmz, gnx, gny, gnz, gcx, gcy, gcz;
-    gather(p.mu, n, v);
-    grad3(v, gmx, gmy, gmz);
-    gather(p.mm, n, v);
-    grad3(v, gnx, gny, gnz);
-    gather(p.psi, n, v);
-    grad3(v, gcx, gcy, gcz);
-    const T ph = p.phi[s], c = v[0];
-    // psi grad mu_psi = grad psi + psi grad m; (fx, fy, fz) is zero without a body force
-    const T Fx = -ph * gmx - (gcx + c * gnx) + p.fx;
-    const T Fy = -ph * gmy - (gcy + c * gny) + p.fy;
-    const T Fz = -ph * gmz - (gcz + c * gnz) + p.fz;
+__global__ void __launch_bounds__(NT, 3) k_lb(const Arg3<T> p, double *out) {
+    const T *const src[3] = {p.mu, p.mm, p.psi};
     T g[Q];
-    T dn = 0, jx = 0, jy = 0, jz = 0;
+    auto pull = [&](int x, int y, int z, unsigned) {
+        const Nb n = neighbours(p, x, y, z);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        g[i] = p.g_in[i * (unsigned)p.vol + n.at(-c_ex(i), -c_ey(i), -c_ez(i))];  // from x - e_i
-        dn += g[i];
-        jx += (T)c_ex(i) * g[i];
-        jy += (T)c_ey(i) * g[i];
-        jz += (T)c_ez(i) * g[i];
-    }
-    const T rho = T(1) + dn;
-    const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
-            uz = (jz + T(0.5) * Fz) / rho;
-    if (FIELDS) {
-        const long long N = (long long)p.nx * p.ny * p.nz;
-        const long long d = ((long long)z * p.ny + y) * p.nx + x;
-        out[d] = (double)rho;
-        out[N + d] = (double)ux;
-        out[2 * N + d] = (double)uy;
-        out[3 * N + d] = (double)uz;
-        return;
-    }
-    const T usq = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        const T w = (T)wq(i);
-        const T ex = (T)c_ex(i), ey = (T)c_ey(i), ez = (T)c_ez(i);
-        const T eu = ex * ux + ey * uy + ez * uz, eF = ex * Fx + ey * Fy + ez * Fz;
-        const T geq = w * (dn + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
-        const T Fi = p.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
-        p.g_out[i * (unsigned)p.vol + s] = g[i] - p.omega * (g[i] - geq) + Fi;
-    }
-    p.ux[s] = p.frozen ? p.ux0 : ux;
-    p.uy[s] = p.frozen ? p.uy0 : uy;
-    p.uz[s] = p.frozen ? p.uz0 : uz;
+        for (int i = 0; i < Q; ++i)
+            g[i] = p.g_in[i * (unsigned)p.vol + n.at(-c_ex(i), -c_ey(i), -c_ez(i))];  // x - e_i
+    };
+    march<T, 1, 1>(p, src, pull, [&](int x, int y, int z, unsigned s, const Planes<T> &pl) {
+        T Fx, Fy, Fz;
+        {
+            V2<T> v[Q], gx, gy, gz;
+            gather_pair(pl, 0, v);
+            grad3(v, gx, gy, gz);
+            T C[Q], gcx, gcy, gcz;
+            gather_one(pl, 0, C);
+            grad3(C, gcx, gcy, gcz);
+            const T ph = p.phi[s], c = C[0];
+            // psi grad mu_psi = grad psi + psi grad m; (fx, fy, fz) is zero without a body force
+            Fx = -ph * gx.x - (gcx + c * gx.y) + p.fx;
+            Fy = -ph * gy.x - (gcy + c * gy.y) + p.fy;
+            Fz = -ph * gz.x - (gcz + c * gz.y) + p.fz;
+        }
+        T dn = 0, jx = 0, jy = 0, jz = 0;
+        static_for<0, Q>([&](auto k) {
+            constexpr int i = decltype(k)::value;
+            dn += g[i];
+            jx = acc_e<c_ex(i)>(jx, g[i]);
+            jy = acc_e<c_ey(i)>(jy, g[i]);
+            jz = acc_e<c_ez(i)>(jz, g[i]);
+        });
+        const T rho = T(1) + dn;
+        const T ux = (jx + T(0.5) * Fx) / rho, uy = (jy + T(0.5) * Fy) / rho,
+                uz = (jz + T(0.5) * Fz) / rho;
+        if (FIELDS) {
+            const long long N = (long long)p.nx * p.ny * p.nz;
+            const long long d = ((long long)z * p.ny + y) * p.nx + x;
+            out[d] = (double)rho;
+            out[N + d] = (double)ux;
+            out[2 * N + d] = (double)uy;
+            out[3 * N + d] = (double)uz;
+            return;
+        }
+        const T usq = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+        static_for<0, Q>([&](auto k) {
+            constexpr int i = decltype(k)::value;
+            const T w = (T)wq(i);
+            const T eu = acc_e<c_ez(i)>(acc_e<c_ey(i)>(mul_e<c_ex(i)>(ux), uy), uz);
+            const T eF = acc_e<c_ez(i)>(acc_e<c_ey(i)>(mul_e<c_ex(i)>(Fx), Fy), Fz);
+            const T geq = w * (dn + rho * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * usq));
+            const T Fi = p.guo * w * (T(3) * (eF - uF) + T(9) * eu * eF);
+            p.g_out[i * (unsigned)p.vol + s] = g[i] - p.omega * (g[i] - geq) + Fi;
+        });
+        p.ux[s] = p.frozen ? p.ux0 : ux;
+        p.uy[s] = p.frozen ? p.uy0 : uy;
+        p.uz[s] = p.frozen ? p.uz0 : uz;
+    });
 }
 
 // phi*, psi* (Eqs. 16-17): g* = g - sum over the 6 faces of the outgoing flux
 // u_f g_upwind, u_f the mean of the two sites' normal velocities.
+// Ring: the pair (phi, psi), ux, uy, uz.
 template <typename T>
-__global__ void k_advect(const Arg3<T> p) {
-    LBD3_SITE(p)
-    const Nb n = neighbours(p, x, y, z);
-    T netp = 0, netc = 0;
-    const T P0 = p.phi[s], C0 = p.psi[s];
+__global__ void __launch_bounds__(NT) k_advect(const Arg3<T> p) {
+    const T *const src[5] = {p.phi, p.psi, p.ux, p.uy, p.uz};
+    march<T, 1, 3>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+        T netp = 0, netc = 0;
+        const V2<T> c0 = pl.pair(0, 0, 0, 0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const unsigned up = n.at(a == 0, a == 1, a == 2), dn = n.at(-(a == 0), -(a == 1), -(a == 2));
-        const T *U = a == 0 ? p.ux : (a == 1 ? p.uy : p.uz);
-        const T fp = T(0.5) * (U[s] + U[up]), fm = T(0.5) * (U[dn] + U[s]);
-        netp += fp * (fp > T(0) ? P0 : p.phi[up]) - fm * (fm > T(0) ? p.phi[dn] : P0);
-        netc += fp * (fp > T(0) ? C0 : p.psi[up]) - fm * (fm > T(0) ? p.psi[dn] : C0);
-    }
-    p.phs[s] = P0 - netp;
-    p.pss[s] = C0 - netc;
+        for (int a = 0; a < 3; ++a) {
+            const int ex = a == 0, ey = a == 1, ez = a == 2;
+            const T Us = pl.one(a, 0, 0, 0);
+            const T fp = T(0.5) * (Us + pl.one(a, ex, ey, ez)),
+                    fm = T(0.5) * (pl.one(a, -ex, -ey, -ez) + Us);
+            const V2<T> up = fp > T(0) ? c0 : pl.pair(0, ex, ey, ez);
+            const V2<T> dn = fm > T(0) ? pl.pair(0, -ex, -ey, -ez) : c0;
+            netp += fp * up.x - fm * dn.x;
+            netc += fp * up.y - fm * dn.y;
+        }
+        p.phs[s] = c0.x - netp;
+        p.pss[s] = c0.y - netc;
+    });
 }
 
-// mu*, m* from phi*, psi* (Eqs. 3, 5), the cubic from phi^n (Eq. 18)
+// mu*, m* from phi*, psi* (Eqs. 3, 5), the cubic from phi^n (Eq. 18); ring: the
+// pair (phi*, psi*)
 template <typename T>
-__global__ void k_chem2(const Arg3<T> p) {
-    LBD3_SITE(p)
-    const Nb n = neighbours(p, x, y, z);
-    T P[Q], C[Q];
-    gather(p.phs, n, P);
-    gather(p.pss, n, C);
-    T px, py, pz, lp, cx, cy, cz;
-    grad_lap(P, px, py, pz, lp);
-    grad3(C, cx, cy, cz);
-    const T pn = p.phi[s];
-    p.mus[s] = p.a * P[0] + p.b * (pn * pn * pn) - (p.B0 + p.B1 * C[0]) * lp -
-               p.B1 * (px * cx + py * cy + pz * cz);
-    p.mms[s] = T(0.5) * p.B1 * (px * px + py * py + pz * pz);
+__global__ void __launch_bounds__(NT) k_chem2(const Arg3<T> p) {
+    const T *const src[2] = {p.phs, p.pss};
+    march<T, 1, 0>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+        V2<T> v[Q], gx, gy, gz, lap;
+        gather_pair(pl, 0, v);
+        grad_lap(v, gx, gy, gz, lap);
+        const T pn = p.phi[s];
+        p.mus[s] = p.a * v[0].x + p.b * (pn * pn * pn) - (p.B0 + p.B1 * v[0].y) * lap.x -
+                   p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
+        p.mms[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+    });
 }
 
 // phi^{n+1} = phi* + M lap mu* (Eq. 18); psi^{n+1} = psi* + D sum_j 6 w_j
 // [(psi*_j - psi*) + (psi* + psi*_j)(m*_j - m*)/2] - gamma (psi* - c0) + A Theta (Eq. 19)
+// Ring: the pair (psi*, m*) and mu*.
 template <typename T>
-__global__ void k_update(const Arg3<T> p) {
-    LBD3_SITE(p)
-    const Nb n = neighbours(p, x, y, z);
-    T v[Q], C[Q], Mv[Q];
-    gather(p.mus, n, v);
-    T sl = 0;
+__global__ void __launch_bounds__(NT) k_update(const Arg3<T> p) {
+    const T *const src[3] = {p.pss, p.mms, p.mus};
+    march<T, 1, 1>(p, src, [](int, int, int, unsigned) {}, [&](int x, int y, int z, unsigned s, const Planes<T> &pl) {
+        {
+            T v[Q];
+            gather_one(pl, 0, v);
+            T sl = 0;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) sl += (T)wq(i) * (v[i] - v[0]);
-    p.phi_o[s] = p.phs[s] + p.M * (T(6) * sl);
-    gather(p.pss, n, C);
-    gather(p.mms, n, Mv);
-    T div = 0;
+            for (int i = 1; i < Q; ++i) sl += (T)wq(i) * (v[i] - v[0]);
+            p.phi_o[s] = p.phs[s] + p.M * (T(6) * sl);
+        }
+        V2<T> cm[Q];
+        gather_pair(pl, 0, cm);
+        const T C0 = cm[0].x;
+        T div = 0;
 #pragma unroll
-    for (int i = 1; i < Q; ++i)
-        div += (T)wq(i) * ((C[i] - C[0]) + T(0.5) * (C[0] + C[i]) * (Mv[i] - Mv[0]));
-    const int words = (p.nx + 31) / 32;
-    const uint32_t bit = (p.theta[((long long)z * p.ny + y) * words + (x >> 5)] >> (x & 31)) & 1u;
-    p.psi_o[s] = C[0] + (p.D * (T(6) * div) - p.gamma * (C[0] - p.c0) + (bit ? p.A : T(0)));
+        for (int i = 1; i < Q; ++i) {
+            const V2<T> d = cm[i] - cm[0];  // (psi*_j - psi*, m*_j - m*)
+            div += (T)wq(i) * (d.x + T(0.5) * (C0 + cm[i].x) * d.y);
+        }
+        const int words = (p.nx + 31) / 32;
+        const uint32_t bit = (p.theta[((long long)z * p.ny + y) * words + (x >> 5)] >> (x & 31)) & 1u;
+        p.psi_o[s] = C0 + (p.D * (T(6) * div) - p.gamma * (C0 - p.c0) + (bit ? p.A : T(0)));
+    });
 }
 
 // ------------------------------------------------------------ utility kernels
@@ -429,6 +659,8 @@ struct lbd3_ctx {
     double *staging = nullptr;       // 6N dense doubles
     double *pop_staging = nullptr;   // 19N, on demand
     double *red = nullptr;           // NRED3 * RED3_BLOCKS partials + NRED3 results
+    int zl = 0;                      // planes per CTA of the marching kernels
+    int sms = 1;
     int cur = 0;
     int64_t t = 0;
     int sticky = 0;
@@ -510,6 +742,7 @@ Arg3<T> args3(const lbd3_ctx *c) {
     a.nx = c->grid.nx;
     a.ny = c->grid.ny;
     a.nz = c->grid.nz;
+    a.zl = c->zl;
     a.pitch = c->pitch;
     a.plane = c->plane;
     a.vol = c->vol;
@@ -552,25 +785,59 @@ Arg3<T> args3(const lbd3_ctx *c) {
     return a;
 }
 
+// Planes per CTA of the marching kernels: enough CTAs for about sixteen per SM
+// over the whole lattice, runs of at least four planes.
+int auto_zrun(const lbd3_grid &g, int sms) {
+    const long long tiles = (long long)((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    long long runs = (16LL * sms + tiles - 1) / tiles;
+    const long long most = (g.nz + 3) / 4;
+    runs = runs < 1 ? 1 : (runs > most ? most : runs);
+    return (int)((g.nz + runs - 1) / runs);
+}
+
+template <typename T>
+dim3 march_grid(const Arg3<T> &a) {
+    return dim3((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zl - 1) / a.zl);
+}
+
 template <typename T>
 cudaError_t launch_step3(const Arg3<T> &a, cudaStream_t s) {
-    const dim3 blk(128), grd((a.nx + 127) / 128, a.ny, a.nz);
-    k_chem<T><<<grd, blk, 0, s>>>(a);
-    k_lb<T, 0><<<grd, blk, 0, s>>>(a, nullptr);
-    k_advect<T><<<grd, blk, 0, s>>>(a);
-    k_chem2<T><<<grd, blk, 0, s>>>(a);
-    k_update<T><<<grd, blk, 0, s>>>(a);
+    const dim3 grd = march_grid(a);
+    const size_t e = sizeof(T);
+    k_chem<T><<<grd, NT, ring_bytes<1, 0>(e), s>>>(a);
+    k_lb<T, 0><<<grd, NT, ring_bytes<1, 1>(e), s>>>(a, nullptr);
+    k_advect<T><<<grd, NT, ring_bytes<1, 3>(e), s>>>(a);
+    k_chem2<T><<<grd, NT, ring_bytes<1, 0>(e), s>>>(a);
+    k_update<T><<<grd, NT, ring_bytes<1, 1>(e), s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fields3(const Arg3<T> &a, const Geo3 &G, double *out, cudaStream_t s) {
-    const dim3 blk(128), grd((a.nx + 127) / 128, a.ny, a.nz);
+    const dim3 grd = march_grid(a);
     const long long N = (long long)a.nx * a.ny * a.nz;
-    k_chem<T><<<grd, blk, 0, s>>>(a);
-    k_lb<T, 1><<<grd, blk, 0, s>>>(a, out);
+    k_chem<T><<<grd, NT, ring_bytes<1, 0>(sizeof(T)), s>>>(a);
+    k_lb<T, 1><<<grd, NT, ring_bytes<1, 1>(sizeof(T)), s>>>(a, out);
     k_dense<T><<<1024, 256, 0, s>>>(G, a.phi, a.psi, out + 4 * N, out + 5 * N);
     return cudaGetLastError();
+}
+
+// The advection ring of FP64 exceeds the default 48 KB of dynamic shared memory.
+template <typename T>
+cudaError_t ring_limits() {
+    const int e = (int)sizeof(T);
+    cudaError_t r = cudaFuncSetAttribute(k_advect<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)ring_bytes<1, 3>(e));
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_lb<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ring_bytes<1, 1>(e));
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_lb<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ring_bytes<1, 1>(e));
+    if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ring_bytes<1, 1>(e));
+    return r;
 }
 
 int ensure_staging3(lbd3_ctx *c) {
@@ -630,11 +897,16 @@ int lbd3_create(const lbd3_grid *grid, const lbd3_params *params, void *stream, 
     c->plane = c->pitch * grid->ny;
     c->vol = c->plane * grid->nz;
     c->N = (long long)grid->nx * grid->ny * grid->nz;
-    if (cudaGetDevice(&c->dev) != cudaSuccess) {
+    int sms = 0;
+    if (cudaGetDevice(&c->dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess ||
+        (c->esz == sizeof(double) ? ring_limits<double>() : ring_limits<float>()) != cudaSuccess) {
         cudaGetLastError();
         delete c;
         return LBD_ECUDA;
     }
+    c->sms = sms;
+    c->zl = auto_zrun(c->grid, sms);
     const size_t fb = (size_t)c->vol * c->esz;
     const size_t words = (size_t)((grid->nx + 31) / 32) * grid->ny * grid->nz;
     bool ok = true;
@@ -830,6 +1102,20 @@ int lbd3_synchronize(lbd3_ctx *c) {
 int lbd3_get_time(const lbd3_ctx *c, int64_t *t) {
     if (!c || !t) return LBD_EINVAL;
     *t = c->t;
+    return LBD_OK;
+}
+
+int lbd3_set_zrun(lbd3_ctx *c, int32_t planes) {
+    if (!c) return LBD_EINVAL;
+    if (planes < 0 || planes > c->grid.nz)
+        return fail3(c, LBD_EINVAL, "planes must be in [0, nz]");
+    c->zl = planes ? planes : auto_zrun(c->grid, c->sms);
+    return LBD_OK;
+}
+
+int lbd3_get_zrun(const lbd3_ctx *c, int32_t *planes) {
+    if (!c || !planes) return LBD_EINVAL;
+    *planes = c->zl;
     return LBD_OK;
 }
 

@@ -43,6 +43,8 @@ SIGNATURES = {
                                         ctypes.POINTER(lbd3_diag)]),
     "lbd3_synchronize": (ctypes.c_int, [_P]),
     "lbd3_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "lbd3_set_zrun": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "lbd3_get_zrun": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32)]),
     "lbd3_destroy": (None, [_P]),
 }
 
@@ -113,6 +115,17 @@ class Sim3:
     def step(self, n=1):
         self._check(load().lbd3_step(self._h, int(n)))
         return self
+
+    @property
+    def zrun(self):
+        """z planes walked by each CTA of the step kernels."""
+        v = ctypes.c_int32()
+        self._check(load().lbd3_get_zrun(self._h, ctypes.byref(v)))
+        return v.value
+
+    @zrun.setter
+    def zrun(self, planes):
+        self._check(load().lbd3_set_zrun(self._h, int(planes)))
 
     def fields(self):
         """(rho, u (3, nz, ny, nx), phi, psi)."""

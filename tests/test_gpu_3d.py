@@ -131,3 +131,39 @@ def test_3d_rejects_bad_fields():
         sim.set_fields(bad, np.full((8, 8, 8), 0.1))
     assert e.value.code == lbd.LBD_ENONFINITE
     sim.close()
+
+
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32], ids=["fp64", "fp32"])
+def test_3d_zrun_does_not_change_results(prec):
+    """Every run length of the z-marching kernels gives bit-identical states,
+    including runs of one plane and a ragged last run."""
+    nx, ny, nz = 40, 20, 19
+    phi, psi, src = case(nx, ny, nz, seed=3)
+    outs = []
+    for zl in (0, 1, 3, 7, 19):
+        sim = lbd3.Sim3(nx, ny, nz, precision=prec, sources=src, **ACTIVE)
+        if zl:
+            sim.zrun = zl
+        assert sim.zrun == zl or zl == 0
+        sim.set_fields(phi, psi)
+        sim.step(40)
+        outs.append((sim.populations(), sim.fields()))
+        sim.close()
+    for f, fl in outs[1:]:
+        assert np.array_equal(f, outs[0][0])
+        for a, b in zip(fl, outs[0][1]):
+            assert np.array_equal(a, b)
+
+
+def test_3d_zrun_rejects_out_of_range():
+    sim = lbd3.Sim3(8, 8, 6, precision=lbd.LBD_FP32)
+    auto = sim.zrun
+    assert 1 <= auto <= 6
+    for bad in (-1, 7):
+        with pytest.raises(lbd.LbdError) as e:
+            sim.zrun = bad
+        assert e.value.code == lbd.LBD_EINVAL
+    sim.zrun = 6
+    sim.zrun = 0
+    assert sim.zrun == auto
+    sim.close()
