@@ -74,18 +74,29 @@ struct Arg3 {
 // plane k + 3.  Two fields that are differentiated alike are stored as a pair
 // (interleaved), read with one shared-memory access and, in FP32, combined with
 // the packed FP32x2 instructions.
-constexpr int TX = 32, TY = 8, NT = TX * TY;
-constexpr int HX = TX + 2, HP = HX * (TY + 2);  // 340 values per halo plane
-constexpr int LPT = (HP + NT - 1) / NT;         // halo values a thread copies per plane
+constexpr int TX = 32, TY = 8, NT = TX * TY;  // threads of a CTA
+constexpr int HX = TX + 2;                     // halo row length
 constexpr int AHEAD = 2;
-constexpr int SLOTS = 3 + AHEAD;                // planes k - 1, k, k + 1 read, the rest in flight
+constexpr int SLOTS = 3 + AHEAD;  // planes k - 1, k, k + 1 read, the rest in flight
+
+// A tile of TX x (TY RY) sites: thread (tx, ty) computes rows ty + TY r, r < RY.
+template <int RY>
+struct Tile {
+    static constexpr int H = TY * RY;              // rows of the tile
+    static constexpr int HP = HX * (H + 2);        // values per halo plane
+    static constexpr int LPT = (HP + NT - 1) / NT;  // halo values a thread copies per plane
+};
+
+// rows per thread of the step kernels (k_lb keeps one: its 19 pulls per site
+// are held in registers across the barrier)
+constexpr int R_CHEM = 1, R_LB = 1, R_ADVECT = 2, R_CHEM2 = 1, R_UPDATE = 1;
 
 extern __shared__ __align__(16) unsigned char lbd3_smem[];
 
 // NP pair fields and NS single fields
-template <int NP, int NS>
+template <int NP, int NS, int RY>
 constexpr size_t ring_bytes(size_t esz) {
-    return (size_t)(2 * NP + NS) * SLOTS * HP * esz;
+    return (size_t)(2 * NP + NS) * SLOTS * Tile<RY>::HP * esz;
 }
 
 // Two values of one site in the lanes of a vector: FP32 uses the packed FP32x2
@@ -150,7 +161,7 @@ __device__ __forceinline__ void cp_wait() {
 }
 
 // The three halo planes around the site being computed.
-template <typename T>
+template <typename T, int HP>
 struct Planes {
     const V2<T> *pp;  // pair fields, NP x SLOTS x HP pairs, offset by the site's index
     const T *ps;      // single fields, NS x SLOTS x HP values, offset likewise
@@ -167,34 +178,36 @@ struct Planes {
 };
 
 // Walk the CTA's run of planes; site(x, y, z, s, planes) is called for every
-// lattice site of the tile, s its element offset.  src lists the two fields of
-// each pair, then the single fields.
-template <typename T, int NP, int NS, class Pre, class Site>
+// lattice site of the tile, s its element offset, and pre(x, y, z, s) before
+// the wait for the plane (loads that need no ring).  src lists the two fields
+// of each pair, then the single fields.
+template <typename T, int NP, int NS, int RY, class Pre, class Site>
 __device__ __forceinline__ void march(const Arg3<T> &p, const T *const (&src)[2 * NP + NS],
                                       Pre pre, Site site) {
+    constexpr int HP = Tile<RY>::HP, LPT = Tile<RY>::LPT;
+    constexpr int SINGLES = 2 * NP * SLOTS * HP;  // element offset of the single fields
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
     T *sm = reinterpret_cast<T *>(lbd3_smem);
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * Tile<RY>::H;
     const int z0 = blockIdx.z * p.zl;
-    const int z1 = min(p.nz, z0 + p.zl);
+    const int z1 = min(nz, z0 + p.zl);
     const int x = x0 + tid % TX, y = y0 + tid / TX;
-    const bool live = x < p.nx && y < p.ny;
     const unsigned pitch = (unsigned)p.pitch, plane = (unsigned)p.plane;
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(sm);
-    constexpr int SINGLES = 2 * NP * SLOTS * HP;  // element offset of the single fields
     unsigned hxy[LPT];
 #pragma unroll
     for (int j = 0; j < LPT; ++j) {
         const int e = tid + j * NT;
-        int gx = (x0 + e % HX - 1) % p.nx, gy = (y0 + e / HX - 1) % p.ny;
-        gx += gx < 0 ? p.nx : 0;
-        gy += gy < 0 ? p.ny : 0;
+        int gx = (x0 + e % HX - 1) % nx, gy = (y0 + e / HX - 1) % ny;
+        gx += gx < 0 ? nx : 0;
+        gy += gy < 0 ? ny : 0;
         hxy[j] = (unsigned)gy * pitch + (unsigned)gx;
     }
     // copy plane k (k in [z0 - 1, z1], periodic) into the slot at element offset o
     auto issue = [&](int k, int o) {
         if (k <= z1) {
-            const unsigned zo = (unsigned)(k < 0 ? k + p.nz : (k >= p.nz ? k - p.nz : k)) * plane;
+            const unsigned zo = (unsigned)(k < 0 ? k + nz : (k >= nz ? k - nz : k)) * plane;
 #pragma unroll
             for (int j = 0; j < LPT; ++j) {
                 const int e = tid + j * NT;
@@ -222,19 +235,26 @@ __device__ __forceinline__ void march(const Arg3<T> &p, const T *const (&src)[2 
 #pragma unroll
     for (int q = 0; q < SLOTS - 1; ++q) issue(z0 - 1 + q, o[q]);
     const int c = (tid / TX + 1) * HX + tid % TX + 1;
-    Planes<T> pl;
-    pl.pp = reinterpret_cast<const V2<T> *>(sm) + c;
-    pl.ps = sm + SINGLES + c;
+    const bool xin = x < nx;
     for (int k = z0; k < z1; ++k) {
         const unsigned s = (unsigned)k * plane + (unsigned)y * pitch + (unsigned)x;
-        if (live) pre(x, y, k, s);  // loads that need no ring, issued before the wait
+#pragma unroll
+        for (int r = 0; r < RY; ++r)
+            if (xin && y + TY * r < ny) pre(x, y + TY * r, k, s + (unsigned)(TY * r) * pitch);
         cp_wait<AHEAD - 1>();  // this thread's copies of plane k + 1 have landed
         __syncthreads();
         issue(k + SLOTS - 2, o[SLOTS - 1]);
-        pl.om = o[0];
-        pl.o0 = o[1];
-        pl.op = o[2];
-        if (live) site(x, y, k, s, pl);
+#pragma unroll
+        for (int r = 0; r < RY; ++r) {
+            Planes<T, HP> pl;
+            pl.pp = reinterpret_cast<const V2<T> *>(sm) + c + TY * r * HX;
+            pl.ps = sm + SINGLES + c + TY * r * HX;
+            pl.om = o[0];
+            pl.o0 = o[1];
+            pl.op = o[2];
+            if (xin && y + TY * r < ny)
+                site(x, y + TY * r, k, s + (unsigned)(TY * r) * pitch, pl);
+        }
         const int freed = o[0];
 #pragma unroll
         for (int q = 0; q < SLOTS - 1; ++q) o[q] = o[q + 1];
@@ -269,13 +289,13 @@ __device__ inline Nb neighbours(const Arg3<T> &p, int x, int y, int z) {
 }
 
 // The 19 values of ring pair f (single field f) around the site, in the D3Q19 order.
-template <typename T>
-__device__ inline void gather_pair(const Planes<T> &pl, int f, V2<T> v[Q]) {
+template <typename V, class P>
+__device__ inline void gather_pair(const P &pl, int f, V v[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i] = pl.pair(f, c_ex(i), c_ey(i), c_ez(i));
 }
-template <typename T>
-__device__ inline void gather_one(const Planes<T> &pl, int f, T v[Q]) {
+template <typename T, class P>
+__device__ inline void gather_one(const P &pl, int f, T v[Q]) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) v[i] = pl.one(f, c_ex(i), c_ey(i), c_ez(i));
 }
@@ -337,8 +357,9 @@ __device__ inline void grad3(const V v[Q], V &gx, V &gy, V &gz) {
 // mu_phi and m at t^n (Eqs. 3, 5); ring: the pair (phi, psi)
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chem(const Arg3<T> p) {
+    constexpr int ROWS = R_CHEM;
     const T *const src[2] = {p.phi, p.psi};
-    march<T, 1, 0>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+    march<T, 1, 0, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int, int, int, unsigned s, const auto &pl) {
         V2<T> v[Q], gx, gy, gz, lap;
         gather_pair(pl, 0, v);
         grad_lap(v, gx, gy, gz, lap);
@@ -354,7 +375,7 @@ __global__ void __launch_bounds__(NT) k_chem(const Arg3<T> p) {
 // current state to dense doubles (rho, ux, uy, uz at d, N + d, 2N + d, 3N + d).
 // Ring: the pair (mu, m) and psi.
 template <typename T, int FIELDS>
-__global__ void __launch_bounds__(NT, 3) k_lb(const Arg3<T> p, double *out) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_lb(const Arg3<T> p, double *out) {
     const T *const src[3] = {p.mu, p.mm, p.psi};
     T g[Q];
     auto pull = [&](int x, int y, int z, unsigned) {
@@ -363,7 +384,7 @@ __global__ void __launch_bounds__(NT, 3) k_lb(const Arg3<T> p, double *out) {
         for (int i = 0; i < Q; ++i)
             g[i] = p.g_in[i * (unsigned)p.vol + n.at(-c_ex(i), -c_ey(i), -c_ez(i))];  // x - e_i
     };
-    march<T, 1, 1>(p, src, pull, [&](int x, int y, int z, unsigned s, const Planes<T> &pl) {
+    march<T, 1, 1, R_LB>(p, src, pull, [&](int x, int y, int z, unsigned s, const auto &pl) {
         T Fx, Fy, Fz;
         {
             V2<T> v[Q], gx, gy, gz;
@@ -419,8 +440,9 @@ __global__ void __launch_bounds__(NT, 3) k_lb(const Arg3<T> p, double *out) {
 // Ring: the pair (phi, psi), ux, uy, uz.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_advect(const Arg3<T> p) {
+    constexpr int ROWS = R_ADVECT;
     const T *const src[5] = {p.phi, p.psi, p.ux, p.uy, p.uz};
-    march<T, 1, 3>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+    march<T, 1, 3, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int, int, int, unsigned s, const auto &pl) {
         T netp = 0, netc = 0;
         const V2<T> c0 = pl.pair(0, 0, 0, 0);
 #pragma unroll
@@ -443,8 +465,9 @@ __global__ void __launch_bounds__(NT) k_advect(const Arg3<T> p) {
 // pair (phi*, psi*)
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chem2(const Arg3<T> p) {
+    constexpr int ROWS = R_CHEM2;
     const T *const src[2] = {p.phs, p.pss};
-    march<T, 1, 0>(p, src, [](int, int, int, unsigned) {}, [&](int, int, int, unsigned s, const Planes<T> &pl) {
+    march<T, 1, 0, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int, int, int, unsigned s, const auto &pl) {
         V2<T> v[Q], gx, gy, gz, lap;
         gather_pair(pl, 0, v);
         grad_lap(v, gx, gy, gz, lap);
@@ -460,8 +483,9 @@ __global__ void __launch_bounds__(NT) k_chem2(const Arg3<T> p) {
 // Ring: the pair (psi*, m*) and mu*.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_update(const Arg3<T> p) {
+    constexpr int ROWS = R_UPDATE;
     const T *const src[3] = {p.pss, p.mms, p.mus};
-    march<T, 1, 1>(p, src, [](int, int, int, unsigned) {}, [&](int x, int y, int z, unsigned s, const Planes<T> &pl) {
+    march<T, 1, 1, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int x, int y, int z, unsigned s, const auto &pl) {
         {
             T v[Q];
             gather_one(pl, 0, v);
@@ -795,48 +819,46 @@ int auto_zrun(const lbd3_grid &g, int sms) {
     return (int)((g.nz + runs - 1) / runs);
 }
 
-template <typename T>
+template <int RY, typename T>
 dim3 march_grid(const Arg3<T> &a) {
-    return dim3((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + a.zl - 1) / a.zl);
+    return dim3((a.nx + TX - 1) / TX, (a.ny + Tile<RY>::H - 1) / Tile<RY>::H,
+                (a.nz + a.zl - 1) / a.zl);
 }
 
 template <typename T>
 cudaError_t launch_step3(const Arg3<T> &a, cudaStream_t s) {
-    const dim3 grd = march_grid(a);
     const size_t e = sizeof(T);
-    k_chem<T><<<grd, NT, ring_bytes<1, 0>(e), s>>>(a);
-    k_lb<T, 0><<<grd, NT, ring_bytes<1, 1>(e), s>>>(a, nullptr);
-    k_advect<T><<<grd, NT, ring_bytes<1, 3>(e), s>>>(a);
-    k_chem2<T><<<grd, NT, ring_bytes<1, 0>(e), s>>>(a);
-    k_update<T><<<grd, NT, ring_bytes<1, 1>(e), s>>>(a);
+    k_chem<T><<<march_grid<R_CHEM>(a), NT, ring_bytes<1, 0, R_CHEM>(e), s>>>(a);
+    k_lb<T, 0><<<march_grid<R_LB>(a), NT, ring_bytes<1, 1, R_LB>(e), s>>>(a, nullptr);
+    k_advect<T><<<march_grid<R_ADVECT>(a), NT, ring_bytes<1, 3, R_ADVECT>(e), s>>>(a);
+    k_chem2<T><<<march_grid<R_CHEM2>(a), NT, ring_bytes<1, 0, R_CHEM2>(e), s>>>(a);
+    k_update<T><<<march_grid<R_UPDATE>(a), NT, ring_bytes<1, 1, R_UPDATE>(e), s>>>(a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_fields3(const Arg3<T> &a, const Geo3 &G, double *out, cudaStream_t s) {
-    const dim3 grd = march_grid(a);
+    const size_t e = sizeof(T);
     const long long N = (long long)a.nx * a.ny * a.nz;
-    k_chem<T><<<grd, NT, ring_bytes<1, 0>(sizeof(T)), s>>>(a);
-    k_lb<T, 1><<<grd, NT, ring_bytes<1, 1>(sizeof(T)), s>>>(a, out);
+    k_chem<T><<<march_grid<R_CHEM>(a), NT, ring_bytes<1, 0, R_CHEM>(e), s>>>(a);
+    k_lb<T, 1><<<march_grid<R_LB>(a), NT, ring_bytes<1, 1, R_LB>(e), s>>>(a, out);
     k_dense<T><<<1024, 256, 0, s>>>(G, a.phi, a.psi, out + 4 * N, out + 5 * N);
     return cudaGetLastError();
 }
 
-// The advection ring of FP64 exceeds the default 48 KB of dynamic shared memory.
+// Rings above the default 48 KB of dynamic shared memory (the FP64 ones).
 template <typename T>
 cudaError_t ring_limits() {
-    const int e = (int)sizeof(T);
-    cudaError_t r = cudaFuncSetAttribute(k_advect<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)ring_bytes<1, 3>(e));
+    const size_t e = sizeof(T);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t r = cudaFuncSetAttribute(k_chem<T>, A, (int)ring_bytes<1, 0, R_CHEM>(e));
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_lb<T, 0>, A, (int)ring_bytes<1, 1, R_LB>(e));
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_lb<T, 1>, A, (int)ring_bytes<1, 1, R_LB>(e));
     if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(k_lb<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ring_bytes<1, 1>(e));
+        r = cudaFuncSetAttribute(k_advect<T>, A, (int)ring_bytes<1, 3, R_ADVECT>(e));
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_chem2<T>, A, (int)ring_bytes<1, 0, R_CHEM2>(e));
     if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(k_lb<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ring_bytes<1, 1>(e));
-    if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(k_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ring_bytes<1, 1>(e));
+        r = cudaFuncSetAttribute(k_update<T>, A, (int)ring_bytes<1, 1, R_UPDATE>(e));
     return r;
 }
 
