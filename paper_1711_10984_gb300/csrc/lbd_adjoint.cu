@@ -21,6 +21,11 @@
 //   mu, m       (Eqs. 3, 5)                  -> lambda phi, lambda psi
 // with dL/dB1 accumulated per site in double.  The transposes use that the isotropic
 // gradient stencil is antisymmetric (G^T = -G) and the Laplacian symmetric.
+// A reversed step is nine kernels, one thread per site: every kernel but the
+// first reads a neighbourhood of its predecessor's output.  Pointwise products
+// that feed a transposed stencil are formed at each neighbour inside the
+// stencil kernel instead of being stored, and the reverse of the collision runs
+// in the kernel that produces its lambda u.
 // The upwind choices and the phi >= 0 mask of the centroid are taken from the
 // forward state (they are piecewise constant).
 #include <cmath>
@@ -37,34 +42,55 @@ struct Nbr {
     long long c, e, w, n, s, ne, nw, se, sw;
 };
 
-__device__ __forceinline__ Nbr nbr(long long s, int nx, int ny) {
-    const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+// the 3 x 3 neighbourhood of (x, y) in a periodic row-major array with rows of `row`
+// elements
+__device__ __forceinline__ Nbr nbr(int x, int y, int nx, int ny, long long row) {
     const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
     const int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
-    const long long r0 = (long long)y * nx, rm = (long long)ym * nx, rp = (long long)yp * nx;
-    return Nbr{s, r0 + xp, r0 + xm, rp + x, rm + x, rp + xp, rp + xm, rm + xp, rm + xm};
+    const long long r0 = (long long)y * row, rm = (long long)ym * row, rp = (long long)yp * row;
+    return Nbr{r0 + x, r0 + xp, r0 + xm, rp + x, rm + x, rp + xp, rp + xm, rm + xp, rm + xm};
 }
 
-// isotropic D2Q9 stencils on dense arrays
-template <typename R>
-__device__ __forceinline__ R Gx(const R *A, const Nbr &q) {
-    return (A[q.e] - A[q.w]) / R(3.0) + ((A[q.ne] - A[q.nw]) + (A[q.se] - A[q.sw])) / R(12.0);
+// isotropic D2Q9 stencils of a site function A(j) (an array read or a product
+// formed at each neighbour)
+template <class F>
+__device__ __forceinline__ auto Gx(const F &A, const Nbr &q) {
+    using R = decltype(A(q.c));
+    return (A(q.e) - A(q.w)) / R(3.0) + ((A(q.ne) - A(q.nw)) + (A(q.se) - A(q.sw))) / R(12.0);
 }
-template <typename R>
-__device__ __forceinline__ R Gy(const R *A, const Nbr &q) {
-    return (A[q.n] - A[q.s]) / R(3.0) + ((A[q.ne] - A[q.se]) + (A[q.nw] - A[q.sw])) / R(12.0);
+template <class F>
+__device__ __forceinline__ auto Gy(const F &A, const Nbr &q) {
+    using R = decltype(A(q.c));
+    return (A(q.n) - A(q.s)) / R(3.0) + ((A(q.ne) - A(q.se)) + (A(q.nw) - A(q.sw))) / R(12.0);
 }
-template <typename R>
-__device__ __forceinline__ R Lap(const R *A, const Nbr &q) {
-    const R c = A[q.c];
-    return (R(2.0) / R(3.0)) * ((A[q.e] - c) + (A[q.w] - c) + (A[q.n] - c) + (A[q.s] - c)) +
-           (R(1.0) / R(6.0)) * ((A[q.ne] - c) + (A[q.nw] - c) + (A[q.se] - c) + (A[q.sw] - c));
+template <class F>
+__device__ __forceinline__ auto Lap(const F &A, const Nbr &q) {
+    using R = decltype(A(q.c));
+    const R c = A(q.c);
+    return (R(2.0) / R(3.0)) * ((A(q.e) - c) + (A(q.w) - c) + (A(q.n) - c) + (A(q.s) - c)) +
+           (R(1.0) / R(6.0)) * ((A(q.ne) - c) + (A(q.nw) - c) + (A(q.se) - c) + (A(q.sw) - c));
 }
 // sum_alpha G_alpha(V_alpha)
-template <typename R>
-__device__ __forceinline__ R Div(const R *Vx, const R *Vy, const Nbr &q) {
+template <class F, class G>
+__device__ __forceinline__ auto Div(const F &Vx, const G &Vy, const Nbr &q) {
     return Gx(Vx, q) + Gy(Vy, q);
 }
+// an array as a site function
+template <typename R>
+struct At {
+    const R *a;
+    __device__ R operator()(long long j) const { return a[j]; }
+};
+template <typename R>
+__device__ __forceinline__ At<R> at(const R *a) {
+    return At<R>{a};
+}
+
+// One thread per site on a 2D grid of 32 x 8 blocks: (x, y) and the dense index s.
+#define LBD_SITE(p)                                                                       \
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;        \
+    if (x >= (p).nx || y >= (p).ny) return;                                               \
+    const long long s = (long long)y * (p).nx + x;
 
 #define LBD_SITES(N)                                                                   \
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (N);       \
@@ -102,61 +128,49 @@ struct Work {
     // adjoints
     R *Lphi, *Lpsi, *Lbuf;       // of the step output (9 planes for Lbuf)
     R *Lphi0, *Lpsi0, *Lbuf0;    // of the step input
-    R *LMUS, *LMS, *LPHS, *LPSS, *LUX, *LUY, *LFX, *LFY, *LMU, *LMM;
-    R *T1, *T2, *T3, *T4, *T5, *T6, *T7;  // products for the transposed stencils
+    R *LMUS, *LMS, *LPHS, *LPSS, *LFX, *LFY, *LMU, *LMM;
     double *dB1;                           // per-site accumulator of dL/dB1 (double)
 };
 
 // ---- forward intermediates ----------------------------------------------------
-template <typename T, typename R>
-__global__ void fwd1(AdjPar<R> p, const T *phi, const T *psi, Work<R> w) {
-    LBD_SITES(p.N) {
-        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
-        const long long o = (long long)y * p.pitch + x;
-        w.PH[s] = (R)phi[o];
-        w.PS[s] = (R)psi[o];
-    }
+// phi^n, psi^n to dense arrays; their gradients and Laplacian; mu, m (Eqs. 3, 5)
+template <typename R>
+__global__ void fwd12(AdjPar<R> p, const R *phi, const R *psi, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.pitch);  // into the pitched state
+    const R px = Gx(at(phi), q), py = Gy(at(phi), q), lp = Lap(at(phi), q);
+    const R cx = Gx(at(psi), q), cy = Gy(at(psi), q);
+    const R ph = phi[q.c], c = psi[q.c];
+    w.PH[s] = ph; w.PS[s] = c;
+    w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
+    w.MU[s] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * c) * lp - p.B1 * (px * cx + py * cy);
+    w.MM[s] = R(0.5) * p.B1 * (px * px + py * py);
 }
 
 template <typename R>
-__global__ void fwd2(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        const R px = Gx(w.PH, q), py = Gy(w.PH, q), lp = Lap(w.PH, q);
-        const R cx = Gx(w.PS, q), cy = Gy(w.PS, q);
-        const R ph = w.PH[s];
-        w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
-        w.MU[s] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * w.PS[s]) * lp -
-                  p.B1 * (px * cx + py * cy);
-        w.MM[s] = R(0.5) * p.B1 * (px * px + py * py);
+__global__ void fwd3(AdjPar<R> p, const R *g, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R gmx = Gx(at(w.MU), q), gmy = Gy(at(w.MU), q);
+    const R gnx = Gx(at(w.MM), q), gny = Gy(at(w.MM), q);
+    w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
+    const R ph = w.PH[s], c = w.PS[s];
+    R Fx = -ph * gmx - (w.GSx[s] + c * gnx);
+    R Fy = -ph * gmy - (w.GSy[s] + c * gny);
+    if (p.body) { Fx += p.fx; Fy += p.fy; }
+    w.Fx[s] = Fx; w.Fy[s] = Fy;
+    R n = 0, jx = 0, jy = 0;
+    for (int i = 0; i < 9; ++i) {
+        int xs = x - EX(i), ys = y - EY(i);
+        xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+        const R f = wgt<R>(i) + g[i * p.plane + (long long)ys * p.pitch + xs];
+        w.FP[i * p.N + s] = f;
+        n += f; jx += f * EX(i); jy += f * EY(i);
     }
-}
-
-template <typename T, typename R>
-__global__ void fwd3(AdjPar<R> p, const T *g, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
-        const R gmx = Gx(w.MU, q), gmy = Gy(w.MU, q), gnx = Gx(w.MM, q), gny = Gy(w.MM, q);
-        w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
-        const R ph = w.PH[s], c = w.PS[s];
-        R Fx = -ph * gmx - (w.GSx[s] + c * gnx);
-        R Fy = -ph * gmy - (w.GSy[s] + c * gny);
-        if (p.body) { Fx += p.fx; Fy += p.fy; }
-        w.Fx[s] = Fx; w.Fy[s] = Fy;
-        R n = 0, jx = 0, jy = 0;
-        for (int i = 0; i < 9; ++i) {
-            int xs = x - EX(i), ys = y - EY(i);
-            xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
-            ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-            const R f = wgt<R>(i) + (R)g[i * p.plane + (long long)ys * p.pitch + xs];
-            w.FP[i * p.N + s] = f;
-            n += f; jx += f * EX(i); jy += f * EY(i);
-        }
-        w.RHO[s] = n;
-        w.UX[s] = (jx + R(0.5) * Fx) / n;
-        w.UY[s] = (jy + R(0.5) * Fy) / n;
-    }
+    w.RHO[s] = n;
+    w.UX[s] = (jx + R(0.5) * Fx) / n;
+    w.UY[s] = (jy + R(0.5) * Fy) / n;
 }
 
 template <typename R>
@@ -164,199 +178,187 @@ __device__ __forceinline__ R up(R u, R a, R b) { return u > R(0.0) ? a : b; }
 
 template <typename R>
 __global__ void fwd4(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        const R *UX = w.UX, *UY = w.UY;
-        const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
-        const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
-        const R *P = w.PH, *C = w.PS;
-        const R fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
-        const R fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
-        const R ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
-        const R gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
-        w.PHS[s] = P[s] - ((fe - fw) + (fn - fs));
-        w.PSS[s] = C[s] - ((ge - gw) + (gn - gs));
-    }
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R *UX = w.UX, *UY = w.UY;
+    const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
+    const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
+    const R *P = w.PH, *C = w.PS;
+    const R fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
+    const R fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
+    const R ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
+    const R gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
+    w.PHS[s] = P[s] - ((fe - fw) + (fn - fs));
+    w.PSS[s] = C[s] - ((ge - gw) + (gn - gs));
 }
 
 template <typename R>
 __global__ void fwd5(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        const R px = Gx(w.PHS, q), py = Gy(w.PHS, q);
-        w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(w.PHS, q);
-        w.GRx[s] = Gx(w.PSS, q); w.GRy[s] = Gy(w.PSS, q);
-        w.MS[s] = R(0.5) * p.B1 * (px * px + py * py);
-    }
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R px = Gx(at(w.PHS), q), py = Gy(at(w.PHS), q);
+    w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(at(w.PHS), q);
+    w.GRx[s] = Gx(at(w.PSS), q); w.GRy[s] = Gy(at(w.PSS), q);
+    w.MS[s] = R(0.5) * p.B1 * (px * px + py * py);
 }
 
 // ---- reverse of the phi and psi updates (Eqs. 18, 19) ---------------------------
 template <typename R>
 __global__ void adj_e(AdjPar<R> p, const R *gam, int j, Work<R> w) {
     const R gamma = gam[j];  // sink rate of the reversed step (j-th of its segment)
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        w.LMUS[s] = p.M * Lap(w.Lphi, q);
-        const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
-        const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
-        R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
-        for (int k = 0; k < 8; ++k) {
-            const R lam = k < 4 ? R(2.0) / R(3.0) : R(1.0) / R(6.0);
-            const long long j = nb[k];
-            // psi'_s's own link to j, and psi'_j's link back to s
-            lpss += p.D * lam * (Lp[s] * (-R(1.0) + R(0.5) * (m[j] - m[s])) +
-                                 Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
-            lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
-        }
-        w.LPSS[s] = lpss;
-        w.LMS[s] = lms;
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    w.LMUS[s] = p.M * Lap(at(w.Lphi), q);
+    const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
+    const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
+    R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const R lam = k < 4 ? R(2.0) / R(3.0) : R(1.0) / R(6.0);
+        const long long j = nb[k];
+        // psi'_s's own link to j, and psi'_j's link back to s
+        lpss += p.D * lam * (Lp[s] * (-R(1.0) + R(0.5) * (m[j] - m[s])) +
+                             Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
+        lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
+    }
+    w.LPSS[s] = lpss;
+    w.LMS[s] = lms;
+}
+
+// reverse of mu*, m* (Eq. 3 on phi*, psi*): the local terms, dB1, and the
+// transposed stencils of the products below, formed at each neighbour
+template <typename R>
+__global__ void adj_d(AdjPar<R> p, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R *LMUS = w.LMUS, *LMS = w.LMS, *PSS = w.PSS;
+    const R *GQx = w.GQx, *GQy = w.GQy, *GRx = w.GRx, *GRy = w.GRy;
+    const R B0 = p.B0, B1 = p.B1;
+    auto T1 = [=](long long j) { return (B0 + B1 * PSS[j]) * LMUS[j]; };  // for -L(.)
+    auto T2 = [=](long long j) { return LMUS[j] * GRx[j]; };  // B1 div(lambda mu* grad psi*) -> phi*
+    auto T3 = [=](long long j) { return LMUS[j] * GRy[j]; };
+    auto T4 = [=](long long j) { return LMUS[j] * GQx[j]; };  // B1 div(lambda mu* grad phi*) -> psi*
+    auto T5 = [=](long long j) { return LMUS[j] * GQy[j]; };
+    auto T6 = [=](long long j) { return LMS[j] * GQx[j]; };   // -B1 div(lambda m* grad phi*) -> phi*
+    auto T7 = [=](long long j) { return LMS[j] * GQy[j]; };
+    const R lmu = LMUS[s], lm = LMS[s];
+    const R qx = GQx[s], qy = GQy[s], rx = GRx[s], ry = GRy[s];
+    const R ph = w.PH[s];
+    w.Lphi0[s] = R(3.0) * p.b * ph * ph * lmu;  // cubic term uses phi^n
+    w.dB1[s] += (double)(lmu * (-PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
+                         lm * R(0.5) * (qx * qx + qy * qy));
+    w.LPHS[s] = w.Lphi[s] + p.a * lmu - Lap(T1, q) + B1 * Div(T2, T3, q) - B1 * Div(T6, T7, q);
+    w.LPSS[s] = (w.LPSS[s] + -B1 * w.LQ[s] * lmu) + B1 * Div(T4, T5, q);
+}
+
+// ---- reverse of the donor-cell advection (Eqs. 16-17), then of the collision
+// (Eqs. 10-13), moments (Eq. 11) and streaming at the same site ------------------
+template <typename R>
+__global__ void adj_cb(AdjPar<R> p, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
+    const R *LP = w.LPHS, *LC = w.LPSS;
+    const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
+    const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
+    // adjoint of each face flux: (lambda at the right/upper site) - (left/lower)
+    const R lpe = LP[q.e] - LP[s], lpw = LP[s] - LP[q.w];
+    const R lpn = LP[q.n] - LP[s], lps = LP[s] - LP[q.s];
+    const R lce = LC[q.e] - LC[s], lcw = LC[s] - LC[q.w];
+    const R lcn = LC[q.n] - LC[s], lcs = LC[s] - LC[q.s];
+    R lphi = LP[s], lpsi = LC[s];
+    // this site is upwind of the east / north face when u_f > 0, of west / south when u_f <= 0
+    if (ue > 0) { lphi += lpe * ue; lpsi += lce * ue; }
+    if (!(uw > 0)) { lphi += lpw * uw; lpsi += lcw * uw; }
+    if (un > 0) { lphi += lpn * un; lpsi += lcn * un; }
+    if (!(us > 0)) { lphi += lps * us; lpsi += lcs * us; }
+    w.Lphi0[s] += lphi;
+    w.Lpsi0[s] = lpsi;
+    R lux = R(0.5) * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
+                      lpw * up(uw, P[q.w], P[s]) + lcw * up(uw, C[q.w], C[s]));
+    R luy = R(0.5) * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
+                      lps * up(us, P[q.s], P[s]) + lcs * up(us, C[q.s], C[s]));
+    // collision, moments and streaming
+    const R n = w.RHO[s], ux = UX[s], uy = UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
+    const R om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
+    R ln = 0, lFx = 0, lFy = 0;
+    R lpost[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R lp = w.Lbuf[i * p.N + s];
+        lpost[i] = lp;
+        const R ex = EX(i), ey = EY(i), wi = wgt<R>(i);
+        const R eu = ex * ux + ey * uy, eF = ex * Fx + ey * Fy;
+        ln += lp * om * wi * (R(1.0) + R(3.0) * eu + R(4.5) * eu * eu - R(1.5) * usq);
+        // d feq/du and d F_i/du
+        lux += lp * (om * wi * n * (R(3.0) * ex + R(9.0) * eu * ex - R(3.0) * ux) +
+                     gk * wi * (-R(3.0) * Fx + R(9.0) * eF * ex));
+        luy += lp * (om * wi * n * (R(3.0) * ey + R(9.0) * eu * ey - R(3.0) * uy) +
+                     gk * wi * (-R(3.0) * Fy + R(9.0) * eF * ey));
+        lFx += lp * gk * wi * (R(3.0) * (ex - ux) + R(9.0) * eu * ex);
+        lFy += lp * gk * wi * (R(3.0) * (ey - uy) + R(9.0) * eu * ey);
+    }
+    // u = (j + F/2) / n
+    const R ljx = lux / n, ljy = luy / n;
+    lFx += R(0.5) * lux / n;
+    lFy += R(0.5) * luy / n;
+    ln += -(lux * ux + luy * uy) / n;
+    w.LFX[s] = lFx;
+    w.LFY[s] = lFy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const R lf = (R(1.0) - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
+        // f_i(x) was pulled from buffer_i(x - e_i)
+        int xs = x - EX(i), ys = y - EY(i);
+        xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
+        ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
+        w.Lbuf0[i * p.N + (long long)ys * p.nx + xs] = lf;
     }
 }
 
-// products for the transposed stencils of mu*, m*; local terms; dB1
+// ---- reverse of the force (Eq. 14) ----------------------------------------------
+// local terms, then lambda mu = div(phi lambda F), lambda m = div(psi lambda F) and
+// the grad psi term, with the products formed at each neighbour
 template <typename R>
-__global__ void adj_d1(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const R lmu = w.LMUS[s], lm = w.LMS[s];
-        const R qx = w.GQx[s], qy = w.GQy[s], rx = w.GRx[s], ry = w.GRy[s];
-        w.T1[s] = (p.B0 + p.B1 * w.PSS[s]) * lmu;  // for -L(.)
-        w.T2[s] = lmu * rx; w.T3[s] = lmu * ry;    // B1 div(lambda mu* grad psi*)  -> phi*
-        w.T4[s] = lmu * qx; w.T5[s] = lmu * qy;    // B1 div(lambda mu* grad phi*)  -> psi*
-        w.T6[s] = lm * qx;  w.T7[s] = lm * qy;     // -B1 div(lambda m* grad phi*)  -> phi*
-        const R ph = w.PH[s];
-        w.Lphi0[s] = R(3.0) * p.b * ph * ph * lmu;     // cubic term uses phi^n
-        w.LPSS[s] += -p.B1 * w.LQ[s] * lmu;
-        w.dB1[s] += (double)(lmu * (-w.PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
-                             lm * R(0.5) * (qx * qx + qy * qy));
-    }
+__global__ void adj_a12(AdjPar<R> p, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R *LFX = w.LFX, *LFY = w.LFY, *PH = w.PH, *PS = w.PS;
+    const R lfx = LFX[s], lfy = LFY[s];
+    w.Lphi0[s] += -(lfx * w.GMx[s] + lfy * w.GMy[s]);
+    const R lpsi = w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s]);
+    auto T1 = [=](long long j) { return PH[j] * LFX[j]; };  // -> lambda mu
+    auto T2 = [=](long long j) { return PH[j] * LFY[j]; };
+    auto T3 = [=](long long j) { return PS[j] * LFX[j]; };  // -> lambda m
+    auto T4 = [=](long long j) { return PS[j] * LFY[j]; };
+    w.LMU[s] = Div(T1, T2, q);
+    w.LMM[s] = Div(T3, T4, q);
+    w.Lpsi0[s] = lpsi + Div(at(LFX), at(LFY), q);
 }
 
+// ---- reverse of mu, m (Eqs. 3, 5) ------------------------------------------------
 template <typename R>
-__global__ void adj_d2(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        w.LPHS[s] = w.Lphi[s] + p.a * w.LMUS[s] - Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) -
-                    p.B1 * Div(w.T6, w.T7, q);
-        w.LPSS[s] += p.B1 * Div(w.T4, w.T5, q);
-    }
-}
-
-// ---- reverse of the donor-cell advection (Eqs. 16-17) ---------------------------
-template <typename R>
-__global__ void adj_c(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        const R *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
-        const R *LP = w.LPHS, *LC = w.LPSS;
-        const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
-        const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
-        // adjoint of each face flux: (lambda at the right/upper site) - (left/lower)
-        const R lpe = LP[q.e] - LP[s], lpw = LP[s] - LP[q.w];
-        const R lpn = LP[q.n] - LP[s], lps = LP[s] - LP[q.s];
-        const R lce = LC[q.e] - LC[s], lcw = LC[s] - LC[q.w];
-        const R lcn = LC[q.n] - LC[s], lcs = LC[s] - LC[q.s];
-        R lphi = LP[s], lpsi = LC[s];
-        // this site is upwind of the east / north face when u_f > 0, of west / south when u_f <= 0
-        if (ue > 0) { lphi += lpe * ue; lpsi += lce * ue; }
-        if (!(uw > 0)) { lphi += lpw * uw; lpsi += lcw * uw; }
-        if (un > 0) { lphi += lpn * un; lpsi += lcn * un; }
-        if (!(us > 0)) { lphi += lps * us; lpsi += lcs * us; }
-        w.Lphi0[s] += lphi;
-        w.Lpsi0[s] = lpsi;
-        w.LUX[s] = R(0.5) * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
-                          lpw * up(uw, P[q.w], P[s]) + lcw * up(uw, C[q.w], C[s]));
-        w.LUY[s] = R(0.5) * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
-                          lps * up(us, P[q.s], P[s]) + lcs * up(us, C[q.s], C[s]));
-    }
-}
-
-// ---- reverse of the collision (Eqs. 10-13), moments (Eq. 11) and streaming -------
-template <typename R>
-__global__ void adj_b(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const int y = (int)(s / p.nx), x = (int)(s - (long long)y * p.nx);
-        const R n = w.RHO[s], ux = w.UX[s], uy = w.UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
-        const R om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
-        R ln = 0, lux = w.LUX[s], luy = w.LUY[s], lFx = 0, lFy = 0;
-        R lpost[9];
-        for (int i = 0; i < 9; ++i) {
-            const R lp = w.Lbuf[i * p.N + s];
-            lpost[i] = lp;
-            const R ex = EX(i), ey = EY(i), wi = wgt<R>(i);
-            const R eu = ex * ux + ey * uy, eF = ex * Fx + ey * Fy;
-            ln += lp * om * wi * (R(1.0) + R(3.0) * eu + R(4.5) * eu * eu - R(1.5) * usq);
-            // d feq/du and d F_i/du
-            lux += lp * (om * wi * n * (R(3.0) * ex + R(9.0) * eu * ex - R(3.0) * ux) +
-                         gk * wi * (-R(3.0) * Fx + R(9.0) * eF * ex));
-            luy += lp * (om * wi * n * (R(3.0) * ey + R(9.0) * eu * ey - R(3.0) * uy) +
-                         gk * wi * (-R(3.0) * Fy + R(9.0) * eF * ey));
-            lFx += lp * gk * wi * (R(3.0) * (ex - ux) + R(9.0) * eu * ex);
-            lFy += lp * gk * wi * (R(3.0) * (ey - uy) + R(9.0) * eu * ey);
-        }
-        // u = (j + F/2) / n
-        const R ljx = lux / n, ljy = luy / n;
-        lFx += R(0.5) * lux / n;
-        lFy += R(0.5) * luy / n;
-        ln += -(lux * ux + luy * uy) / n;
-        w.LFX[s] = lFx;
-        w.LFY[s] = lFy;
-        for (int i = 0; i < 9; ++i) {
-            const R lf = (R(1.0) - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
-            // f_i(x) was pulled from buffer_i(x - e_i)
-            int xs = x - EX(i), ys = y - EY(i);
-            xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
-            ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
-            w.Lbuf0[i * p.N + (long long)ys * p.nx + xs] = lf;
-        }
-    }
-}
-
-// ---- reverse of the force (Eq. 14) and of mu, m (Eqs. 3, 5) ----------------------
-template <typename R>
-__global__ void adj_a1(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const R lfx = w.LFX[s], lfy = w.LFY[s];
-        w.T1[s] = w.PH[s] * lfx; w.T2[s] = w.PH[s] * lfy;   // -> lambda mu
-        w.T3[s] = w.PS[s] * lfx; w.T4[s] = w.PS[s] * lfy;   // -> lambda m
-        w.Lphi0[s] += -(lfx * w.GMx[s] + lfy * w.GMy[s]);
-        w.Lpsi0[s] += -(lfx * w.GNx[s] + lfy * w.GNy[s]);
-    }
-}
-
-template <typename R>
-__global__ void adj_a2(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        w.LMU[s] = Div(w.T1, w.T2, q);
-        w.LMM[s] = Div(w.T3, w.T4, q);
-        w.Lpsi0[s] += Div(w.LFX, w.LFY, q);
-    }
-}
-
-template <typename R>
-__global__ void adj_a3(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const R lmu = w.LMU[s], lm = w.LMM[s];
-        const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
-        const R ph = w.PH[s];
-        w.T1[s] = (p.B0 + p.B1 * w.PS[s]) * lmu;
-        w.T2[s] = lmu * cx; w.T3[s] = lmu * cy;
-        w.T4[s] = lmu * px; w.T5[s] = lmu * py;
-        w.T6[s] = lm * px;  w.T7[s] = lm * py;
-        w.Lphi0[s] += (p.a + R(3.0) * p.b * ph * ph) * lmu;
-        w.Lpsi0[s] += -p.B1 * w.LP[s] * lmu;
-        w.dB1[s] += (double)(lmu * (-w.PS[s] * w.LP[s] - (px * cx + py * cy)) +
-                             lm * R(0.5) * (px * px + py * py));
-    }
-}
-
-template <typename R>
-__global__ void adj_a4(AdjPar<R> p, Work<R> w) {
-    LBD_SITES(p.N) {
-        const Nbr q = nbr(s, p.nx, p.ny);
-        w.Lphi0[s] += -Lap(w.T1, q) + p.B1 * Div(w.T2, w.T3, q) - p.B1 * Div(w.T6, w.T7, q);
-        w.Lpsi0[s] += p.B1 * Div(w.T4, w.T5, q);
-    }
+__global__ void adj_a34(AdjPar<R> p, Work<R> w) {
+    LBD_SITE(p)
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+    const R *LMU = w.LMU, *LMM = w.LMM, *PS = w.PS;
+    const R *GPx = w.GPx, *GPy = w.GPy, *GSx = w.GSx, *GSy = w.GSy;
+    const R B0 = p.B0, B1 = p.B1;
+    auto T1 = [=](long long j) { return (B0 + B1 * PS[j]) * LMU[j]; };
+    auto T2 = [=](long long j) { return LMU[j] * GSx[j]; };
+    auto T3 = [=](long long j) { return LMU[j] * GSy[j]; };
+    auto T4 = [=](long long j) { return LMU[j] * GPx[j]; };
+    auto T5 = [=](long long j) { return LMU[j] * GPy[j]; };
+    auto T6 = [=](long long j) { return LMM[j] * GPx[j]; };
+    auto T7 = [=](long long j) { return LMM[j] * GPy[j]; };
+    const R lmu = LMU[s], lm = LMM[s];
+    const R px = GPx[s], py = GPy[s], cx = GSx[s], cy = GSy[s];
+    const R ph = w.PH[s];
+    w.dB1[s] += (double)(lmu * (-PS[s] * w.LP[s] - (px * cx + py * cy)) +
+                         lm * R(0.5) * (px * px + py * py));
+    w.Lphi0[s] = (w.Lphi0[s] + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
+                 (-Lap(T1, q) + B1 * Div(T2, T3, q) - B1 * Div(T6, T7, q));
+    w.Lpsi0[s] = (w.Lpsi0[s] + -B1 * w.LP[s] * lmu) + B1 * Div(T4, T5, q);
 }
 
 // ---- loss: centroid x of the phi >= 0 region and its gradient ---------------------
@@ -444,6 +446,7 @@ int adjoint_run(const AdjointJob<T> &job) {
         st = own;
     }
     const int nb = (int)((N + 255) / 256 < 2048 ? (N + 255) / 256 : 2048);
+    const dim3 b2(32, 8), g2((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8));  // one thread per site
     const int64_t nsteps = job.nsteps, K = job.ckpt_every;
     const int64_t nseg = (nsteps + K - 1) / K;
 
@@ -475,17 +478,19 @@ int adjoint_run(const AdjointJob<T> &job) {
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
-    const int n_dense = 74;  // dense arrays of the step's precision carved out below
-    // ... followed by the per-site dL/dB1 accumulator in double
-    T *dense = (T *)dalloc(sizeof(T) * (size_t)N * n_dense + sizeof(double) * (size_t)N);
+    const int n_dense = 65;  // dense arrays of the step's precision carved out below,
+                             // after the per-site dL/dB1 accumulator in double
+    void *dense_raw = dalloc(sizeof(double) * (size_t)N + sizeof(T) * (size_t)N * n_dense);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
     T *gam = (T *)dalloc(sizeof(T) * (size_t)K);  // sink rate of each step of a segment
-    if (!ckpt || !seg || !dense || !part || !gam) {
+    if (!ckpt || !seg || !dense_raw || !part || !gam) {
         release();
         return LBD_ENOMEM;
     }
     Work<T> w;
     {
+        w.dB1 = reinterpret_cast<double *>(dense_raw);
+        T *const dense = reinterpret_cast<T *>(w.dB1 + N);
         T *d = dense;
         auto take = [&](int k) { T *r = d; d += (size_t)k * N; return r; };
         w.PH = take(1); w.PS = take(1); w.GPx = take(1); w.GPy = take(1); w.LP = take(1);
@@ -497,11 +502,8 @@ int adjoint_run(const AdjointJob<T> &job) {
         w.Lphi = take(1); w.Lpsi = take(1); w.Lbuf = take(9);
         w.Lphi0 = take(1); w.Lpsi0 = take(1); w.Lbuf0 = take(9);
         w.LMUS = take(1); w.LMS = take(1); w.LPHS = take(1); w.LPSS = take(1);
-        w.LUX = take(1); w.LUY = take(1); w.LFX = take(1); w.LFY = take(1);
+        w.LFX = take(1); w.LFY = take(1);
         w.LMU = take(1); w.LMM = take(1);
-        w.T1 = take(1); w.T2 = take(1); w.T3 = take(1); w.T4 = take(1); w.T5 = take(1);
-        w.T6 = take(1); w.T7 = take(1);
-        w.dB1 = reinterpret_cast<double *>(d);  // 8-byte aligned: N * 74 * sizeof(T) is
         if (d - dense != (ptrdiff_t)n_dense * N) {  // carve-out must match the allocation
             release();
             return LBD_EINVAL;
@@ -600,20 +602,15 @@ int adjoint_run(const AdjointJob<T> &job) {
     auto reverse_steps = [&](int64_t k0, int64_t k1) -> cudaError_t {
         for (int64_t k = k1 - 1; k >= k0; --k) {
             const T *in = slot(seg, k - k0);
-            fwd1<T, T><<<nb, 256, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
-            fwd2<T><<<nb, 256, 0, st>>>(ap, w);
-            fwd3<T, T><<<nb, 256, 0, st>>>(ap, in, w);
-            fwd4<T><<<nb, 256, 0, st>>>(ap, w);
-            fwd5<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_e<T><<<nb, 256, 0, st>>>(ap, gam, (int)(k - k0), w);
-            adj_d1<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_d2<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_c<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_b<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_a1<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_a2<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_a3<T><<<nb, 256, 0, st>>>(ap, w);
-            adj_a4<T><<<nb, 256, 0, st>>>(ap, w);
+            fwd12<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
+            fwd3<T><<<g2, b2, 0, st>>>(ap, in, w);
+            fwd4<T><<<g2, b2, 0, st>>>(ap, w);
+            fwd5<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_e<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
+            adj_d<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_cb<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_a12<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_a34<T><<<g2, b2, 0, st>>>(ap, w);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             // the input adjoints become the output adjoints of the previous step
