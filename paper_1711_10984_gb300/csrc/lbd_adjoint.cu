@@ -21,11 +21,12 @@
 //   mu, m       (Eqs. 3, 5)                  -> lambda phi, lambda psi
 // with dL/dB1 accumulated per site in double.  The transposes use that the isotropic
 // gradient stencil is antisymmetric (G^T = -G) and the Laplacian symmetric.
-// A reversed step is nine kernels, one thread per site: every kernel but the
-// first reads a neighbourhood of its predecessor's output.  Pointwise products
-// that feed a transposed stencil are formed at each neighbour inside the
-// stencil kernel instead of being stored, and the reverse of the collision runs
-// in the kernel that produces its lambda u.
+// A reversed step is six kernels, one thread per site.  Where a stage
+// differentiates the output of the stage before it, the two share a kernel: the
+// first is evaluated on the block's tile and a one-site halo into shared
+// memory.  Pointwise products that feed a transposed stencil are formed at each
+// neighbour instead of being stored, and the reverse of the collision runs in
+// the kernel that produces its lambda u.
 // The upwind choices and the phi >= 0 mask of the centroid are taken from the
 // forward state (they are piecewise constant).
 #include <cmath>
@@ -38,12 +39,18 @@
 namespace lbd {
 namespace {
 
+// The 3 x 3 neighbourhood of a site as indices into some array; slot k of
+// operator[] is C, E, W, N, S, NE, NW, SE, SW (N: y + 1, E: x + 1).
+enum { C_, E_, W_, N_, S_, NE_, NW_, SE_, SW_ };
 struct Nbr {
     long long c, e, w, n, s, ne, nw, se, sw;
+    __device__ __forceinline__ long long operator[](int k) const {
+        return k == C_ ? c : k == E_ ? e : k == W_ ? w : k == N_ ? n : k == S_ ? s
+             : k == NE_ ? ne : k == NW_ ? nw : k == SE_ ? se : sw;
+    }
 };
 
-// the 3 x 3 neighbourhood of (x, y) in a periodic row-major array with rows of `row`
-// elements
+// periodic neighbourhood of (x, y) in a row-major array with rows of `row` elements
 __device__ __forceinline__ Nbr nbr(int x, int y, int nx, int ny, long long row) {
     const int xm = x ? x - 1 : nx - 1, xp = x + 1 < nx ? x + 1 : 0;
     const int ym = y ? y - 1 : ny - 1, yp = y + 1 < ny ? y + 1 : 0;
@@ -51,46 +58,69 @@ __device__ __forceinline__ Nbr nbr(int x, int y, int nx, int ny, long long row) 
     return Nbr{r0 + x, r0 + xp, r0 + xm, rp + x, rm + x, rp + xp, rp + xm, rm + xp, rm + xm};
 }
 
-// isotropic D2Q9 stencils of a site function A(j) (an array read or a product
-// formed at each neighbour)
+// isotropic D2Q9 stencils of a function A(k) of the neighbourhood slot (an array
+// read, a value in shared memory, or a product formed at the neighbour)
 template <class F>
-__device__ __forceinline__ auto Gx(const F &A, const Nbr &q) {
-    using R = decltype(A(q.c));
-    return (A(q.e) - A(q.w)) / R(3.0) + ((A(q.ne) - A(q.nw)) + (A(q.se) - A(q.sw))) / R(12.0);
+__device__ __forceinline__ auto Gx(const F &A) {
+    using R = decltype(A(C_));
+    return (A(E_) - A(W_)) / R(3.0) + ((A(NE_) - A(NW_)) + (A(SE_) - A(SW_))) / R(12.0);
 }
 template <class F>
-__device__ __forceinline__ auto Gy(const F &A, const Nbr &q) {
-    using R = decltype(A(q.c));
-    return (A(q.n) - A(q.s)) / R(3.0) + ((A(q.ne) - A(q.se)) + (A(q.nw) - A(q.sw))) / R(12.0);
+__device__ __forceinline__ auto Gy(const F &A) {
+    using R = decltype(A(C_));
+    return (A(N_) - A(S_)) / R(3.0) + ((A(NE_) - A(SE_)) + (A(NW_) - A(SW_))) / R(12.0);
 }
 template <class F>
-__device__ __forceinline__ auto Lap(const F &A, const Nbr &q) {
-    using R = decltype(A(q.c));
-    const R c = A(q.c);
-    return (R(2.0) / R(3.0)) * ((A(q.e) - c) + (A(q.w) - c) + (A(q.n) - c) + (A(q.s) - c)) +
-           (R(1.0) / R(6.0)) * ((A(q.ne) - c) + (A(q.nw) - c) + (A(q.se) - c) + (A(q.sw) - c));
+__device__ __forceinline__ auto Lap(const F &A) {
+    using R = decltype(A(C_));
+    const R c = A(C_);
+    return (R(2.0) / R(3.0)) * ((A(E_) - c) + (A(W_) - c) + (A(N_) - c) + (A(S_) - c)) +
+           (R(1.0) / R(6.0)) * ((A(NE_) - c) + (A(NW_) - c) + (A(SE_) - c) + (A(SW_) - c));
 }
 // sum_alpha G_alpha(V_alpha)
 template <class F, class G>
-__device__ __forceinline__ auto Div(const F &Vx, const G &Vy, const Nbr &q) {
-    return Gx(Vx, q) + Gy(Vy, q);
+__device__ __forceinline__ auto Div(const F &Vx, const G &Vy) {
+    return Gx(Vx) + Gy(Vy);
 }
-// an array as a site function
+// array A over the neighbourhood q
 template <typename R>
 struct At {
     const R *a;
-    __device__ R operator()(long long j) const { return a[j]; }
+    Nbr q;
+    __device__ __forceinline__ R operator()(int k) const { return a[q[k]]; }
 };
 template <typename R>
-__device__ __forceinline__ At<R> at(const R *a) {
-    return At<R>{a};
+__device__ __forceinline__ At<R> at(const R *a, const Nbr &q) {
+    return At<R>{a, q};
 }
 
-// One thread per site on a 2D grid of 32 x 8 blocks: (x, y) and the dense index s.
+// One thread per site on a 2D grid of TBX x TBY blocks: (x, y) and the dense index s.
+constexpr int TBX = 32, TBY = 8;
 #define LBD_SITE(p)                                                                       \
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;        \
+    const int x = blockIdx.x * TBX + threadIdx.x, y = blockIdx.y * TBY + threadIdx.y;     \
     if (x >= (p).nx || y >= (p).ny) return;                                               \
     const long long s = (long long)y * (p).nx + x;
+
+// Two-stage kernels: the first stage is evaluated on the block's tile and a
+// one-site halo (THN sites, periodic) into shared memory, then the second stage
+// differentiates it on the tile.  f(e, x, y) evaluates halo-tile site e.
+constexpr int THX = TBX + 2, THN = THX * (TBY + 2);
+template <class F>
+__device__ __forceinline__ void over_halo_tile(int nx, int ny, F f) {
+    const int x0 = blockIdx.x * TBX - 1, y0 = blockIdx.y * TBY - 1;
+    for (int e = threadIdx.y * TBX + threadIdx.x; e < THN; e += TBX * TBY) {
+        int x = (x0 + e % THX) % nx, y = (y0 + e / THX) % ny;
+        x += x < 0 ? nx : 0;
+        y += y < 0 ? ny : 0;
+        f(e, x, y);
+    }
+}
+// the neighbourhood of the thread's own site in a halo tile
+__device__ __forceinline__ Nbr tile_nbr() {
+    const long long c = (threadIdx.y + 1) * THX + threadIdx.x + 1;
+    return Nbr{c, c + 1, c - 1, c + THX, c - THX, c + THX + 1, c + THX - 1, c - THX + 1,
+               c - THX - 1};
+}
 
 #define LBD_SITES(N)                                                                   \
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < (N);       \
@@ -123,12 +153,12 @@ template <typename R>
 struct Work {
     // forward intermediates
     R *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy, *MU, *MM;
-    R *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *FP, *RHO, *UX, *UY;
-    R *PHS, *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
+    R *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *RHO, *UX, *UY;
+    R *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
     // adjoints
     R *Lphi, *Lpsi, *Lbuf;       // of the step output (9 planes for Lbuf)
     R *Lphi0, *Lpsi0, *Lbuf0;    // of the step input
-    R *LMUS, *LMS, *LPHS, *LPSS, *LFX, *LFY, *LMU, *LMM;
+    R *LPHS, *LPSS, *LFX, *LFY;
     double *dB1;                           // per-site accumulator of dL/dB1 (double)
 };
 
@@ -138,8 +168,8 @@ template <typename R>
 __global__ void fwd12(AdjPar<R> p, const R *phi, const R *psi, Work<R> w) {
     LBD_SITE(p)
     const Nbr q = nbr(x, y, p.nx, p.ny, p.pitch);  // into the pitched state
-    const R px = Gx(at(phi), q), py = Gy(at(phi), q), lp = Lap(at(phi), q);
-    const R cx = Gx(at(psi), q), cy = Gy(at(psi), q);
+    const R px = Gx(at(phi, q)), py = Gy(at(phi, q)), lp = Lap(at(phi, q));
+    const R cx = Gx(at(psi, q)), cy = Gy(at(psi, q));
     const R ph = phi[q.c], c = psi[q.c];
     w.PH[s] = ph; w.PS[s] = c;
     w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
@@ -147,12 +177,13 @@ __global__ void fwd12(AdjPar<R> p, const R *phi, const R *psi, Work<R> w) {
     w.MM[s] = R(0.5) * p.B1 * (px * px + py * py);
 }
 
+// F (Eq. 14), pulled populations, n and u (Eq. 11)
 template <typename R>
 __global__ void fwd3(AdjPar<R> p, const R *g, Work<R> w) {
     LBD_SITE(p)
     const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R gmx = Gx(at(w.MU), q), gmy = Gy(at(w.MU), q);
-    const R gnx = Gx(at(w.MM), q), gny = Gy(at(w.MM), q);
+    const R gmx = Gx(at(w.MU, q)), gmy = Gy(at(w.MU, q));
+    const R gnx = Gx(at(w.MM, q)), gny = Gy(at(w.MM, q));
     w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
     const R ph = w.PH[s], c = w.PS[s];
     R Fx = -ph * gmx - (w.GSx[s] + c * gnx);
@@ -160,12 +191,12 @@ __global__ void fwd3(AdjPar<R> p, const R *g, Work<R> w) {
     if (p.body) { Fx += p.fx; Fy += p.fy; }
     w.Fx[s] = Fx; w.Fy[s] = Fy;
     R n = 0, jx = 0, jy = 0;
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
         int xs = x - EX(i), ys = y - EY(i);
         xs = xs < 0 ? xs + p.nx : (xs >= p.nx ? xs - p.nx : xs);
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         const R f = wgt<R>(i) + g[i * p.plane + (long long)ys * p.pitch + xs];
-        w.FP[i * p.N + s] = f;
         n += f; jx += f * EX(i); jy += f * EY(i);
     }
     w.RHO[s] = n;
@@ -176,79 +207,81 @@ __global__ void fwd3(AdjPar<R> p, const R *g, Work<R> w) {
 template <typename R>
 __device__ __forceinline__ R up(R u, R a, R b) { return u > R(0.0) ? a : b; }
 
+// phi*, psi* by donor-cell advection (Eqs. 16-17) on the tile and its halo, then
+// their gradients, the Laplacian of phi* and m* on the tile
 template <typename R>
-__global__ void fwd4(AdjPar<R> p, Work<R> w) {
+__global__ void fwd45(AdjPar<R> p, Work<R> w) {
+    __shared__ R sP[THN], sC[THN];
+    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
+        const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+        const long long s = q.c;
+        const R *UX = w.UX, *UY = w.UY;
+        const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
+        const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
+        const R *P = w.PH, *C = w.PS;
+        const R fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
+        const R fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
+        const R ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
+        const R gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
+        sP[e] = P[s] - ((fe - fw) + (fn - fs));
+        sC[e] = C[s] - ((ge - gw) + (gn - gs));
+    });
+    __syncthreads();
     LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R *UX = w.UX, *UY = w.UY;
-    const R ue = R(0.5) * (UX[s] + UX[q.e]), uw = R(0.5) * (UX[q.w] + UX[s]);
-    const R un = R(0.5) * (UY[s] + UY[q.n]), us = R(0.5) * (UY[q.s] + UY[s]);
-    const R *P = w.PH, *C = w.PS;
-    const R fe = ue * up(ue, P[s], P[q.e]), fw = uw * up(uw, P[q.w], P[s]);
-    const R fn = un * up(un, P[s], P[q.n]), fs = us * up(us, P[q.s], P[s]);
-    const R ge = ue * up(ue, C[s], C[q.e]), gw = uw * up(uw, C[q.w], C[s]);
-    const R gn = un * up(un, C[s], C[q.n]), gs = us * up(us, C[q.s], C[s]);
-    w.PHS[s] = P[s] - ((fe - fw) + (fn - fs));
-    w.PSS[s] = C[s] - ((ge - gw) + (gn - gs));
-}
-
-template <typename R>
-__global__ void fwd5(AdjPar<R> p, Work<R> w) {
-    LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R px = Gx(at(w.PHS), q), py = Gy(at(w.PHS), q);
-    w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(at(w.PHS), q);
-    w.GRx[s] = Gx(at(w.PSS), q); w.GRy[s] = Gy(at(w.PSS), q);
+    const Nbr t = tile_nbr();
+    const R px = Gx(at((const R *)sP, t)), py = Gy(at((const R *)sP, t));
+    w.PSS[s] = sC[t.c];
+    w.GQx[s] = px; w.GQy[s] = py; w.LQ[s] = Lap(at((const R *)sP, t));
+    w.GRx[s] = Gx(at((const R *)sC, t)); w.GRy[s] = Gy(at((const R *)sC, t));
     w.MS[s] = R(0.5) * p.B1 * (px * px + py * py);
 }
 
-// ---- reverse of the phi and psi updates (Eqs. 18, 19) ---------------------------
+// ---- reverse of the phi and psi updates (Eqs. 18, 19) on the tile and its halo,
+// then of mu*, m* (Eq. 3 on phi*, psi*) on the tile: the local terms, dB1, and
+// the transposed stencils of products formed at each neighbour -----------------
 template <typename R>
-__global__ void adj_e(AdjPar<R> p, const R *gam, int j, Work<R> w) {
-    const R gamma = gam[j];  // sink rate of the reversed step (j-th of its segment)
-    LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    w.LMUS[s] = p.M * Lap(at(w.Lphi), q);
-    const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
-    const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
-    R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
+__global__ void adj_ed(AdjPar<R> p, const R *gam, int jstep, Work<R> w) {
+    __shared__ R sMU[THN], sM[THN], sPSS[THN];  // lambda mu*, lambda m*, lambda psi* (partial)
+    const R gamma = gam[jstep];  // sink rate of the reversed step (j-th of its segment)
+    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
+        const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+        const long long s = q.c;
+        sMU[e] = p.M * Lap(at(w.Lphi, q));
+        const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
+        const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
+        R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const R lam = k < 4 ? R(2.0) / R(3.0) : R(1.0) / R(6.0);
-        const long long j = nb[k];
-        // psi'_s's own link to j, and psi'_j's link back to s
-        lpss += p.D * lam * (Lp[s] * (-R(1.0) + R(0.5) * (m[j] - m[s])) +
-                             Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
-        lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
-    }
-    w.LPSS[s] = lpss;
-    w.LMS[s] = lms;
-}
-
-// reverse of mu*, m* (Eq. 3 on phi*, psi*): the local terms, dB1, and the
-// transposed stencils of the products below, formed at each neighbour
-template <typename R>
-__global__ void adj_d(AdjPar<R> p, Work<R> w) {
+        for (int k = 0; k < 8; ++k) {
+            const R lam = k < 4 ? R(2.0) / R(3.0) : R(1.0) / R(6.0);
+            const long long j = nb[k];
+            // psi'_s's own link to j, and psi'_j's link back to s
+            lpss += p.D * lam * (Lp[s] * (-R(1.0) + R(0.5) * (m[j] - m[s])) +
+                                 Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
+            lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
+        }
+        sPSS[e] = lpss;
+        sM[e] = lms;
+    });
+    __syncthreads();
     LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R *LMUS = w.LMUS, *LMS = w.LMS, *PSS = w.PSS;
-    const R *GQx = w.GQx, *GQy = w.GQy, *GRx = w.GRx, *GRy = w.GRy;
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx), t = tile_nbr();
+    const R *PSS = w.PSS, *GQx = w.GQx, *GQy = w.GQy, *GRx = w.GRx, *GRy = w.GRy;
     const R B0 = p.B0, B1 = p.B1;
-    auto T1 = [=](long long j) { return (B0 + B1 * PSS[j]) * LMUS[j]; };  // for -L(.)
-    auto T2 = [=](long long j) { return LMUS[j] * GRx[j]; };  // B1 div(lambda mu* grad psi*) -> phi*
-    auto T3 = [=](long long j) { return LMUS[j] * GRy[j]; };
-    auto T4 = [=](long long j) { return LMUS[j] * GQx[j]; };  // B1 div(lambda mu* grad phi*) -> psi*
-    auto T5 = [=](long long j) { return LMUS[j] * GQy[j]; };
-    auto T6 = [=](long long j) { return LMS[j] * GQx[j]; };   // -B1 div(lambda m* grad phi*) -> phi*
-    auto T7 = [=](long long j) { return LMS[j] * GQy[j]; };
-    const R lmu = LMUS[s], lm = LMS[s];
+    auto T1 = [&](int k) { return (B0 + B1 * PSS[q[k]]) * sMU[t[k]]; };  // for -L(.)
+    auto T2 = [&](int k) { return sMU[t[k]] * GRx[q[k]]; };  // B1 div(lambda mu* grad psi*) -> phi*
+    auto T3 = [&](int k) { return sMU[t[k]] * GRy[q[k]]; };
+    auto T4 = [&](int k) { return sMU[t[k]] * GQx[q[k]]; };  // B1 div(lambda mu* grad phi*) -> psi*
+    auto T5 = [&](int k) { return sMU[t[k]] * GQy[q[k]]; };
+    auto T6 = [&](int k) { return sM[t[k]] * GQx[q[k]]; };   // -B1 div(lambda m* grad phi*) -> phi*
+    auto T7 = [&](int k) { return sM[t[k]] * GQy[q[k]]; };
+    const R lmu = sMU[t.c], lm = sM[t.c];
     const R qx = GQx[s], qy = GQy[s], rx = GRx[s], ry = GRy[s];
     const R ph = w.PH[s];
     w.Lphi0[s] = R(3.0) * p.b * ph * ph * lmu;  // cubic term uses phi^n
     w.dB1[s] += (double)(lmu * (-PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
                          lm * R(0.5) * (qx * qx + qy * qy));
-    w.LPHS[s] = w.Lphi[s] + p.a * lmu - Lap(T1, q) + B1 * Div(T2, T3, q) - B1 * Div(T6, T7, q);
-    w.LPSS[s] = (w.LPSS[s] + -B1 * w.LQ[s] * lmu) + B1 * Div(T4, T5, q);
+    w.LPHS[s] = w.Lphi[s] + p.a * lmu - Lap(T1) + B1 * Div(T2, T3) - B1 * Div(T6, T7);
+    w.LPSS[s] = (sPSS[t.c] + -B1 * w.LQ[s] * lmu) + B1 * Div(T4, T5);
 }
 
 // ---- reverse of the donor-cell advection (Eqs. 16-17), then of the collision
@@ -316,49 +349,45 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
     }
 }
 
-// ---- reverse of the force (Eq. 14) ----------------------------------------------
-// local terms, then lambda mu = div(phi lambda F), lambda m = div(psi lambda F) and
-// the grad psi term, with the products formed at each neighbour
+// ---- reverse of the force (Eq. 14) on the tile and its halo: lambda mu =
+// div(phi lambda F), lambda m = div(psi lambda F); then the force's local terms
+// and grad psi term, and the reverse of mu, m (Eqs. 3, 5) on the tile ----------
 template <typename R>
-__global__ void adj_a12(AdjPar<R> p, Work<R> w) {
-    LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+__global__ void adj_a(AdjPar<R> p, Work<R> w) {
+    __shared__ R sMU[THN], sM[THN];  // lambda mu, lambda m
     const R *LFX = w.LFX, *LFY = w.LFY, *PH = w.PH, *PS = w.PS;
-    const R lfx = LFX[s], lfy = LFY[s];
-    w.Lphi0[s] += -(lfx * w.GMx[s] + lfy * w.GMy[s]);
-    const R lpsi = w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s]);
-    auto T1 = [=](long long j) { return PH[j] * LFX[j]; };  // -> lambda mu
-    auto T2 = [=](long long j) { return PH[j] * LFY[j]; };
-    auto T3 = [=](long long j) { return PS[j] * LFX[j]; };  // -> lambda m
-    auto T4 = [=](long long j) { return PS[j] * LFY[j]; };
-    w.LMU[s] = Div(T1, T2, q);
-    w.LMM[s] = Div(T3, T4, q);
-    w.Lpsi0[s] = lpsi + Div(at(LFX), at(LFY), q);
-}
-
-// ---- reverse of mu, m (Eqs. 3, 5) ------------------------------------------------
-template <typename R>
-__global__ void adj_a34(AdjPar<R> p, Work<R> w) {
+    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
+        const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+        auto T1 = [&](int k) { return PH[q[k]] * LFX[q[k]]; };  // -> lambda mu
+        auto T2 = [&](int k) { return PH[q[k]] * LFY[q[k]]; };
+        auto T3 = [&](int k) { return PS[q[k]] * LFX[q[k]]; };  // -> lambda m
+        auto T4 = [&](int k) { return PS[q[k]] * LFY[q[k]]; };
+        sMU[e] = Div(T1, T2);
+        sM[e] = Div(T3, T4);
+    });
+    __syncthreads();
     LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R *LMU = w.LMU, *LMM = w.LMM, *PS = w.PS;
+    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx), t = tile_nbr();
+    const R lfx = LFX[s], lfy = LFY[s];
+    R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
+    R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) + Div(at(LFX, q), at(LFY, q));
     const R *GPx = w.GPx, *GPy = w.GPy, *GSx = w.GSx, *GSy = w.GSy;
     const R B0 = p.B0, B1 = p.B1;
-    auto T1 = [=](long long j) { return (B0 + B1 * PS[j]) * LMU[j]; };
-    auto T2 = [=](long long j) { return LMU[j] * GSx[j]; };
-    auto T3 = [=](long long j) { return LMU[j] * GSy[j]; };
-    auto T4 = [=](long long j) { return LMU[j] * GPx[j]; };
-    auto T5 = [=](long long j) { return LMU[j] * GPy[j]; };
-    auto T6 = [=](long long j) { return LMM[j] * GPx[j]; };
-    auto T7 = [=](long long j) { return LMM[j] * GPy[j]; };
-    const R lmu = LMU[s], lm = LMM[s];
+    auto T1 = [&](int k) { return (B0 + B1 * PS[q[k]]) * sMU[t[k]]; };
+    auto T2 = [&](int k) { return sMU[t[k]] * GSx[q[k]]; };
+    auto T3 = [&](int k) { return sMU[t[k]] * GSy[q[k]]; };
+    auto T4 = [&](int k) { return sMU[t[k]] * GPx[q[k]]; };
+    auto T5 = [&](int k) { return sMU[t[k]] * GPy[q[k]]; };
+    auto T6 = [&](int k) { return sM[t[k]] * GPx[q[k]]; };
+    auto T7 = [&](int k) { return sM[t[k]] * GPy[q[k]]; };
+    const R lmu = sMU[t.c], lm = sM[t.c];
     const R px = GPx[s], py = GPy[s], cx = GSx[s], cy = GSy[s];
-    const R ph = w.PH[s];
+    const R ph = PH[s];
     w.dB1[s] += (double)(lmu * (-PS[s] * w.LP[s] - (px * cx + py * cy)) +
                          lm * R(0.5) * (px * px + py * py));
-    w.Lphi0[s] = (w.Lphi0[s] + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
-                 (-Lap(T1, q) + B1 * Div(T2, T3, q) - B1 * Div(T6, T7, q));
-    w.Lpsi0[s] = (w.Lpsi0[s] + -B1 * w.LP[s] * lmu) + B1 * Div(T4, T5, q);
+    w.Lphi0[s] = (lphi + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
+                 (-Lap(T1) + B1 * Div(T2, T3) - B1 * Div(T6, T7));
+    w.Lpsi0[s] = (lpsi + -B1 * w.LP[s] * lmu) + B1 * Div(T4, T5);
 }
 
 // ---- loss: centroid x of the phi >= 0 region and its gradient ---------------------
@@ -446,7 +475,7 @@ int adjoint_run(const AdjointJob<T> &job) {
         st = own;
     }
     const int nb = (int)((N + 255) / 256 < 2048 ? (N + 255) / 256 : 2048);
-    const dim3 b2(32, 8), g2((unsigned)((nx + 31) / 32), (unsigned)((ny + 7) / 8));  // one thread per site
+    const dim3 b2(TBX, TBY), g2((unsigned)((nx + TBX - 1) / TBX), (unsigned)((ny + TBY - 1) / TBY));
     const int64_t nsteps = job.nsteps, K = job.ckpt_every;
     const int64_t nseg = (nsteps + K - 1) / K;
 
@@ -478,7 +507,7 @@ int adjoint_run(const AdjointJob<T> &job) {
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
-    const int n_dense = 65;  // dense arrays of the step's precision carved out below,
+    const int n_dense = 51;  // dense arrays of the step's precision carved out below,
                              // after the per-site dL/dB1 accumulator in double
     void *dense_raw = dalloc(sizeof(double) * (size_t)N + sizeof(T) * (size_t)N * n_dense);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
@@ -496,14 +525,12 @@ int adjoint_run(const AdjointJob<T> &job) {
         w.PH = take(1); w.PS = take(1); w.GPx = take(1); w.GPy = take(1); w.LP = take(1);
         w.GSx = take(1); w.GSy = take(1); w.MU = take(1); w.MM = take(1);
         w.GMx = take(1); w.GMy = take(1); w.GNx = take(1); w.GNy = take(1);
-        w.Fx = take(1); w.Fy = take(1); w.FP = take(9); w.RHO = take(1); w.UX = take(1);
-        w.UY = take(1); w.PHS = take(1); w.PSS = take(1); w.GQx = take(1); w.GQy = take(1);
+        w.Fx = take(1); w.Fy = take(1); w.RHO = take(1); w.UX = take(1);
+        w.UY = take(1); w.PSS = take(1); w.GQx = take(1); w.GQy = take(1);
         w.LQ = take(1); w.GRx = take(1); w.GRy = take(1); w.MS = take(1);
         w.Lphi = take(1); w.Lpsi = take(1); w.Lbuf = take(9);
         w.Lphi0 = take(1); w.Lpsi0 = take(1); w.Lbuf0 = take(9);
-        w.LMUS = take(1); w.LMS = take(1); w.LPHS = take(1); w.LPSS = take(1);
-        w.LFX = take(1); w.LFY = take(1);
-        w.LMU = take(1); w.LMM = take(1);
+        w.LPHS = take(1); w.LPSS = take(1); w.LFX = take(1); w.LFY = take(1);
         if (d - dense != (ptrdiff_t)n_dense * N) {  // carve-out must match the allocation
             release();
             return LBD_EINVAL;
@@ -604,13 +631,10 @@ int adjoint_run(const AdjointJob<T> &job) {
             const T *in = slot(seg, k - k0);
             fwd12<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
             fwd3<T><<<g2, b2, 0, st>>>(ap, in, w);
-            fwd4<T><<<g2, b2, 0, st>>>(ap, w);
-            fwd5<T><<<g2, b2, 0, st>>>(ap, w);
-            adj_e<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
-            adj_d<T><<<g2, b2, 0, st>>>(ap, w);
+            fwd45<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
             adj_cb<T><<<g2, b2, 0, st>>>(ap, w);
-            adj_a12<T><<<g2, b2, 0, st>>>(ap, w);
-            adj_a34<T><<<g2, b2, 0, st>>>(ap, w);
+            adj_a<T><<<g2, b2, 0, st>>>(ap, w);
             const cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
             // the input adjoints become the output adjoints of the previous step

@@ -89,6 +89,35 @@ def test_adjoint_matches_torch_autograd():
     assert np.abs(g).max() > 0 and B1_t.grad.item() != 0
 
 
+@pytest.mark.parametrize("nx,ny", [(40, 27), (20, 6)])
+def test_adjoint_ragged_lattice(nx, ny):
+    """Lattices that leave partial 32 x 8 blocks (and one smaller than a block)
+    against torch autograd: the halo tiles of the fused reverse kernels wrap
+    periodically through the partial blocks."""
+    steps = 60
+    d = dict(x=nx / 2 - 0.6, y=ny / 2 + 0.3, R=min(nx, ny) / 3, psi_mean=0.1, noise=0.01,
+             gx=0.01)
+    phi, psi = inputs.droplet_fields(nx, ny, [d], seed=5)
+    src = [inputs.default_source(d, nx, ny)]
+    sim = lbd.Sim(nx, ny, precision=lbd.LBD_FP64, sources=src, **PAR)
+    sim.set_fields(phi, psi)
+    L, dpsi, dB1 = sim.adjoint(steps, 9, nx / 2)
+    sim.close()
+    P = dict(PAR)
+    psi_t = torch.tensor(psi, requires_grad=True)
+    B1_t = torch.tensor(PAR["B1"], dtype=torch.float64, requires_grad=True)
+    P["B1"] = B1_t
+    phi_t = torch.tensor(phi)
+    f, ph, c = T.run(P, phi_t, psi_t, steps, sources=src)
+    Lt = T.centroid_x(ph, nx / 2) - T.centroid_x(phi_t, nx / 2)
+    Lt.backward()
+    assert L == pytest.approx(Lt.item(), rel=1e-10, abs=1e-12)
+    g = psi_t.grad.numpy()
+    assert np.abs(g).max() > 0
+    assert np.abs(dpsi - g).max() <= 1e-8 * np.abs(g).max()
+    assert dB1 == pytest.approx(B1_t.grad.item(), rel=1e-8, abs=1e-14)
+
+
 def test_adjoint_matches_central_differences():
     """64^2, 300 steps: directional derivatives along seeded random directions
     in psi(0), single sites, and B1, against central differences of the FP64
