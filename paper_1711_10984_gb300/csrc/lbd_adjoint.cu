@@ -21,7 +21,7 @@
 //   mu, m       (Eqs. 3, 5)                  -> lambda phi, lambda psi
 // with dL/dB1 accumulated per site in double.  The transposes use that the isotropic
 // gradient stencil is antisymmetric (G^T = -G) and the Laplacian symmetric.
-// A reversed step is six kernels, one thread per site.  Where a stage
+// A reversed step is five kernels, one thread per site.  Where a stage
 // differentiates the output of the stage before it, the two share a kernel: the
 // first is evaluated on the block's tile and a one-site halo into shared
 // memory.  Pointwise products that feed a transposed stencil are formed at each
@@ -152,7 +152,7 @@ struct AdjPar {
 template <typename R>
 struct Work {
     // forward intermediates
-    R *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy, *MU, *MM;
+    R *PH, *PS, *GPx, *GPy, *LP, *GSx, *GSy;
     R *GMx, *GMy, *GNx, *GNy, *Fx, *Fy, *RHO, *UX, *UY;
     R *PSS, *GQx, *GQy, *LQ, *GRx, *GRy, *MS;
     // adjoints
@@ -163,29 +163,35 @@ struct Work {
 };
 
 // ---- forward intermediates ----------------------------------------------------
-// phi^n, psi^n to dense arrays; their gradients and Laplacian; mu, m (Eqs. 3, 5)
+// On the tile and its halo: gradients and Laplacian of phi^n, psi^n and mu, m
+// (Eqs. 3, 5), kept for the tile's own sites; on the tile: F (Eq. 14), the
+// pulled populations, n and u (Eq. 11).
 template <typename R>
-__global__ void fwd12(AdjPar<R> p, const R *phi, const R *psi, Work<R> w) {
+__global__ void fwd123(AdjPar<R> p, const R *phi, const R *psi, const R *g, Work<R> w) {
+    __shared__ R sMU[THN], sMM[THN];
+    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
+        const Nbr q = nbr(x, y, p.nx, p.ny, p.pitch);  // into the pitched state
+        const R px = Gx(at(phi, q)), py = Gy(at(phi, q)), lp = Lap(at(phi, q));
+        const R cx = Gx(at(psi, q)), cy = Gy(at(psi, q));
+        const R ph = phi[q.c], c = psi[q.c];
+        sMU[e] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * c) * lp - p.B1 * (px * cx + py * cy);
+        sMM[e] = R(0.5) * p.B1 * (px * px + py * py);
+        const int ex = e % THX, ey = e / THX;  // the tile's own sites keep the rest
+        if (ex >= 1 && ex <= TBX && ey >= 1 && ey <= TBY &&
+            (int)blockIdx.x * TBX + ex - 1 < p.nx && (int)blockIdx.y * TBY + ey - 1 < p.ny) {
+            const long long s = (long long)y * p.nx + x;
+            w.PH[s] = ph; w.PS[s] = c;
+            w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
+        }
+    });
+    __syncthreads();
     LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.pitch);  // into the pitched state
-    const R px = Gx(at(phi, q)), py = Gy(at(phi, q)), lp = Lap(at(phi, q));
-    const R cx = Gx(at(psi, q)), cy = Gy(at(psi, q));
-    const R ph = phi[q.c], c = psi[q.c];
-    w.PH[s] = ph; w.PS[s] = c;
-    w.GPx[s] = px; w.GPy[s] = py; w.LP[s] = lp; w.GSx[s] = cx; w.GSy[s] = cy;
-    w.MU[s] = p.a * ph + p.b * ph * ph * ph - (p.B0 + p.B1 * c) * lp - p.B1 * (px * cx + py * cy);
-    w.MM[s] = R(0.5) * p.B1 * (px * px + py * py);
-}
-
-// F (Eq. 14), pulled populations, n and u (Eq. 11)
-template <typename R>
-__global__ void fwd3(AdjPar<R> p, const R *g, Work<R> w) {
-    LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-    const R gmx = Gx(at(w.MU, q)), gmy = Gy(at(w.MU, q));
-    const R gnx = Gx(at(w.MM, q)), gny = Gy(at(w.MM, q));
+    const Nbr t = tile_nbr();
+    const R gmx = Gx(at((const R *)sMU, t)), gmy = Gy(at((const R *)sMU, t));
+    const R gnx = Gx(at((const R *)sMM, t)), gny = Gy(at((const R *)sMM, t));
     w.GMx[s] = gmx; w.GMy[s] = gmy; w.GNx[s] = gnx; w.GNy[s] = gny;
-    const R ph = w.PH[s], c = w.PS[s];
+    const long long o = (long long)y * p.pitch + x;
+    const R ph = phi[o], c = psi[o];
     R Fx = -ph * gmx - (w.GSx[s] + c * gnx);
     R Fy = -ph * gmy - (w.GSy[s] + c * gny);
     if (p.body) { Fx += p.fx; Fy += p.fy; }
@@ -507,7 +513,7 @@ int adjoint_run(const AdjointJob<T> &job) {
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
-    const int n_dense = 51;  // dense arrays of the step's precision carved out below,
+    const int n_dense = 49;  // dense arrays of the step's precision carved out below,
                              // after the per-site dL/dB1 accumulator in double
     void *dense_raw = dalloc(sizeof(double) * (size_t)N + sizeof(T) * (size_t)N * n_dense);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
@@ -523,7 +529,7 @@ int adjoint_run(const AdjointJob<T> &job) {
         T *d = dense;
         auto take = [&](int k) { T *r = d; d += (size_t)k * N; return r; };
         w.PH = take(1); w.PS = take(1); w.GPx = take(1); w.GPy = take(1); w.LP = take(1);
-        w.GSx = take(1); w.GSy = take(1); w.MU = take(1); w.MM = take(1);
+        w.GSx = take(1); w.GSy = take(1);
         w.GMx = take(1); w.GMy = take(1); w.GNx = take(1); w.GNy = take(1);
         w.Fx = take(1); w.Fy = take(1); w.RHO = take(1); w.UX = take(1);
         w.UY = take(1); w.PSS = take(1); w.GQx = take(1); w.GQy = take(1);
@@ -629,8 +635,7 @@ int adjoint_run(const AdjointJob<T> &job) {
     auto reverse_steps = [&](int64_t k0, int64_t k1) -> cudaError_t {
         for (int64_t k = k1 - 1; k >= k0; --k) {
             const T *in = slot(seg, k - k0);
-            fwd12<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, w);
-            fwd3<T><<<g2, b2, 0, st>>>(ap, in, w);
+            fwd123<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, in, w);
             fwd45<T><<<g2, b2, 0, st>>>(ap, w);
             adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
             adj_cb<T><<<g2, b2, 0, st>>>(ap, w);
