@@ -125,8 +125,10 @@ int lbd_set_params(lbd_ctx *ctx, const lbd_params *params);
 
 /* Set the state from host arrays of nx*ny doubles: populations become the
  * equilibrium f_i^eq(rho, u) of Eq. (12) (rho NULL = 1, ux/uy NULL = 0); phi and
- * psi are required.  Returns LBD_ENONFINITE for a NaN/Inf and LBD_EUNSTABLE if
- * B0 + B1 psi <= 0 or psi <= 0 anywhere (nothing is changed then). */
+ * psi are required.  Returns LBD_ENONFINITE for a NaN/Inf, LBD_EUNSTABLE if
+ * B0 + B1 psi <= 0 or psi <= 0, LBD_EINVAL if rho <= 0, for the first such site in
+ * index order (named by lbd_last_error); nothing is changed then.  The arrays
+ * are uploaded and checked on the device.  Synchronises. */
 int lbd_set_fields(lbd_ctx *ctx, const double *rho, const double *ux, const double *uy,
                    const double *phi, const double *psi);
 

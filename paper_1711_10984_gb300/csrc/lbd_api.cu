@@ -112,14 +112,39 @@ int fail(lbd_ctx *c, int code, const char *fmt, ...) {
 
 // ---------------------------------------------------------------- kernels
 
+// The first invalid site of an upload, in index order, as 4 s + reason:
+// 1 a non-finite value, 2 psi <= 0 or B(psi) = B0 + B1 psi <= 0, 3 rho <= 0 (the
+// first failing test of the site).  *first must hold all bits set on entry.
+__global__ void check_fields_kernel(long long N, const double *rho, const double *ux,
+                                    const double *uy, const double *phi, const double *psi,
+                                    int has_rho, int has_ux, int has_uy, double B0, double B1,
+                                    unsigned long long *first) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const double ph = phi[s], ps = psi[s];
+        unsigned code = 0;
+        if (!isfinite(ph) || !isfinite(ps) || (has_rho && !isfinite(rho[s])) ||
+            (has_ux && !isfinite(ux[s])) || (has_uy && !isfinite(uy[s])))
+            code = 1;
+        else if (!(ps > 0.0) || !(__dadd_rn(B0, __dmul_rn(B1, ps)) > 0.0))
+            code = 2;
+        else if (has_rho && !(rho[s] > 0.0))
+            code = 3;
+        if (code) atomicMin(first, (unsigned long long)s * 4ull + code);
+    }
+}
+
 // f_i = f_i^eq(rho, u) of Eq. (12) stored as g_i = f_i - w_i in the pull
 // layout: buffer_i(x) is what site x + e_i reads, so it holds f_i^eq at x + e_i;
 // with walls, a buffer whose reader lies beyond a plate is read back by its own
 // site as the reversed population (bounce-back), so it holds f_{-i}^eq at x.
+// Nothing is written unless *bad holds no invalid site (all bits set).
 template <typename T>
 __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, const double *rho,
                             const double *ux, const double *uy, const double *phi,
-                            const double *psi, int walls, T *g, T *phi_o, T *psi_o) {
+                            const double *psi, int walls, const unsigned long long *bad, T *g,
+                            T *phi_o, T *psi_o) {
+    if (*bad != ~0ull) return;
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
@@ -487,11 +512,12 @@ bool tile_ok(const lbd_ctx *c, Tile t) {
 
 int ensure_staging(lbd_ctx *c) {
     if (c->staging) return LBD_OK;
-    if (cudaMalloc(&c->staging, 5 * c->N * sizeof(double)) != cudaSuccess) {
+    // five fields of doubles, then the first-invalid-site word of an upload
+    if (cudaMalloc(&c->staging, (5 * c->N + 1) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->staging = nullptr;
         return fail(c, LBD_ENOMEM, "staging allocation of %zu bytes failed",
-                    5 * c->N * sizeof(double));
+                    (5 * c->N + 1) * sizeof(double));
     }
     return LBD_OK;
 }
@@ -790,20 +816,16 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     if (!phi || !psi) return fail(c, LBD_EINVAL, "phi and psi are required");
     const size_t N = c->N;
     const lbd_params &p = c->params;
-    for (size_t s = 0; s < N; ++s) {
-        if (!std::isfinite(phi[s]) || !std::isfinite(psi[s]) || (rho && !std::isfinite(rho[s])) ||
-            (ux && !std::isfinite(ux[s])) || (uy && !std::isfinite(uy[s])))
-            return fail(c, LBD_ENONFINITE, "non-finite initial value at site %zu", s);
-        if (!(psi[s] > 0.0) || !(p.B0 + p.B1 * psi[s] > 0.0))
-            return fail(c, LBD_EUNSTABLE, "psi <= 0 or B(psi) <= 0 at site %zu", s);
-        if (rho && !(rho[s] > 0.0)) return fail(c, LBD_EINVAL, "rho <= 0 at site %zu", s);
-    }
     int rc = ensure_staging(c);
     if (rc != LBD_OK) return rc;
     CK(c, cudaSetDevice(c->dev));
+    // upload into the staging area, validate there, and build the state only if
+    // every site is valid (the state is left as it was otherwise)
     double *d = c->staging;
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(d + 5 * N);
     const size_t B = N * sizeof(double);
     const int nb = grid_for(N);
+    CK(c, cudaMemsetAsync(bad, 0xFF, sizeof *bad, c->stream));
     if (rho) CK(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
     else {
         fill_kernel<<<nb, 256, 0, c->stream>>>(d, (long long)N, 1.0);
@@ -815,16 +837,32 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     else CK(c, cudaMemsetAsync(d + 2 * N, 0, B, c->stream));
     CK(c, cudaMemcpyAsync(d + 3 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaMemcpyAsync(d + 4 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
+    check_fields_kernel<<<nb, 256, 0, c->stream>>>((long long)N, d, d + N, d + 2 * N, d + 3 * N,
+                                                   d + 4 * N, rho != nullptr, ux != nullptr,
+                                                   uy != nullptr, p.B0, p.B1, bad);
+    CK(c, cudaGetLastError());
     if (p.precision == LBD_FP64)
         init_kernel<double><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
-            (p.flags & LBD_WALLS) ? 1 : 0, (double *)c->g[c->cur], (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+            (p.flags & LBD_WALLS) ? 1 : 0, bad, (double *)c->g[c->cur], (double *)c->phi[c->cur],
+            (double *)c->psi[c->cur]);
     else
         init_kernel<float><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
-            (p.flags & LBD_WALLS) ? 1 : 0, (float *)c->g[c->cur], (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+            (p.flags & LBD_WALLS) ? 1 : 0, bad, (float *)c->g[c->cur], (float *)c->phi[c->cur],
+            (float *)c->psi[c->cur]);
     CK(c, cudaGetLastError());
+    unsigned long long first = 0;
+    CK(c, cudaMemcpyAsync(&first, bad, sizeof first, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (first != ~0ull) {
+        const size_t site = (size_t)(first >> 2);
+        switch ((int)(first & 3ull)) {
+            case 1: return fail(c, LBD_ENONFINITE, "non-finite initial value at site %zu", site);
+            case 2: return fail(c, LBD_EUNSTABLE, "psi <= 0 or B(psi) <= 0 at site %zu", site);
+            default: return fail(c, LBD_EINVAL, "rho <= 0 at site %zu", site);
+        }
+    }
     return LBD_OK;
 }
 

@@ -274,6 +274,32 @@ def test_error_paths():
     with pytest.raises(lbd.LbdError) as e:
         sim.set_fields(phi, np.full((ny, nx), 0.2))  # B = 0.006 - 0.05*0.2 < 0
     assert e.value.code == lbd.LBD_EUNSTABLE
+    # the first bad site in index order, and the first failing test of that site
+    two = psi.copy()
+    two[2, 7] = -1.0   # site 39: psi <= 0
+    bad2 = phi.copy()
+    bad2[5, 1] = np.inf  # site 81
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields(bad2, two)
+    assert e.value.code == lbd.LBD_EUNSTABLE and "site 39" in str(e.value)
+    bad3 = phi.copy()
+    bad3[2, 7] = np.nan  # site 39 is both non-finite (phi) and unstable (psi)
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields(bad3, two)
+    assert e.value.code == lbd.LBD_ENONFINITE and "site 39" in str(e.value)
+    rho = np.ones((ny, nx))
+    rho[0, 3] = 0.0
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields(phi, psi, rho=rho)
+    assert e.value.code == lbd.LBD_EINVAL and "site 3" in str(e.value)
+    # a rejected upload leaves the state as it was
+    good = np.tanh(np.linspace(-2, 2, nx))[None, :].repeat(ny, 0)
+    sim.set_fields(good, psi)
+    before = sim.fields()
+    with pytest.raises(lbd.LbdError):
+        sim.set_fields(bad, psi)
+    for a, b in zip(sim.fields(), before):
+        assert np.array_equal(a, b)
     with pytest.raises(lbd.LbdError) as e:
         sim.set_tile(48, 48)
     assert e.value.code == lbd.LBD_EINVAL
