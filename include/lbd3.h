@@ -67,7 +67,9 @@ const char *lbd3_last_error(const lbd3_ctx *ctx);
 int lbd3_set_params(lbd3_ctx *ctx, const lbd3_params *params);
 /* phi, psi required; rho (default 1) and u (default 0) may be NULL; the
  * populations become f^eq(rho, u) (Eq. 12).  LBD_ENONFINITE for NaN/Inf,
- * LBD_EUNSTABLE for B(psi) <= 0 or psi <= 0, as in 2D.  Synchronises. */
+ * LBD_EUNSTABLE for B(psi) <= 0 or psi <= 0, LBD_EINVAL for rho <= 0, for the
+ * first such site in index order (nothing is changed then), as in 2D; the
+ * arrays are uploaded and checked on the device.  Synchronises. */
 int lbd3_set_fields(lbd3_ctx *ctx, const double *rho, const double *ux, const double *uy,
                     const double *uz, const double *phi, const double *psi);
 /* Advance by n coupled steps (asynchronous). */

@@ -525,11 +525,41 @@ __device__ inline void coords(const Geo3 &G, long long d, int &x, int &y, int &z
 
 __device__ inline int pw(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
+// The first invalid site of an upload (dense doubles rho, ux, uy, uz, phi, psi at
+// d, N + d, ..., 5N + d), in index order, as 4 d + reason: 1 a non-finite value,
+// 2 psi <= 0 or B(psi) = B0 + B1 psi <= 0, 3 rho <= 0.  *first must hold all
+// bits set on entry.
+__global__ void k_check(long long N, const double *in, double B0, double B1,
+                        unsigned long long *first) {
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
+         d += (long long)gridDim.x * blockDim.x) {
+        const double n = in[d], ps = in[5 * N + d];
+        unsigned code = 0;
+        if (!isfinite(n) || !isfinite(in[N + d]) || !isfinite(in[2 * N + d]) ||
+            !isfinite(in[3 * N + d]) || !isfinite(in[4 * N + d]) || !isfinite(ps))
+            code = 1;
+        else if (!(ps > 0.0) || !(__dadd_rn(B0, __dmul_rn(B1, ps)) > 0.0))
+            code = 2;
+        else if (!(n > 0.0))
+            code = 3;
+        if (code) atomicMin(first, (unsigned long long)d * 4ull + code);
+    }
+}
+
+__global__ void k_fill(long long n, double v, double *a) {
+    for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < n;
+         d += (long long)gridDim.x * blockDim.x)
+        a[d] = v;
+}
+
 // f_i = f_i^eq(rho, u) (Eq. 12) in the pull layout: buffer_i(x) holds the value
 // site x + e_i reads, f_i^eq at x + e_i; phi, psi copied.  Inputs: dense doubles
 // rho, ux, uy, uz, phi, psi at d, N + d, ..., 5N + d.
+// Nothing is written unless *bad holds no invalid site (all bits set).
 template <typename T>
-__global__ void k_init(const Geo3 G, const double *in, T *g, T *phi, T *psi) {
+__global__ void k_init(const Geo3 G, const double *in, const unsigned long long *bad, T *g, T *phi,
+                       T *psi) {
+    if (*bad != ~0ull) return;
     const long long N = (long long)G.nx * G.ny * G.nz;
     for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < N;
          d += (long long)gridDim.x * blockDim.x) {
@@ -864,7 +894,8 @@ cudaError_t ring_limits() {
 
 int ensure_staging3(lbd3_ctx *c) {
     if (c->staging) return LBD_OK;
-    if (cudaMalloc(&c->staging, sizeof(double) * 6 * c->N) != cudaSuccess) {
+    // six fields of doubles, then the first-invalid-site word of an upload
+    if (cudaMalloc(&c->staging, sizeof(double) * (6 * c->N + 1)) != cudaSuccess) {
         cudaGetLastError();
         c->staging = nullptr;
         return fail3(c, LBD_ENOMEM, "staging allocation failed");
@@ -978,48 +1009,44 @@ int lbd3_set_fields(lbd3_ctx *c, const double *rho, const double *ux, const doub
     if (!phi || !psi) return fail3(c, LBD_EINVAL, "phi and psi are required");
     const long long N = c->N;
     const lbd_params &p = c->params.base;
-    for (long long d = 0; d < N; ++d) {
-        if (!std::isfinite(phi[d]) || !std::isfinite(psi[d]) || (rho && !std::isfinite(rho[d])) ||
-            (ux && !std::isfinite(ux[d])) || (uy && !std::isfinite(uy[d])) ||
-            (uz && !std::isfinite(uz[d])))
-            return fail3(c, LBD_ENONFINITE, "non-finite value at site %lld", d);
-        if (!(psi[d] > 0.0) || !(p.B0 + p.B1 * psi[d] > 0.0))
-            return fail3(c, LBD_EUNSTABLE, "B(psi) <= 0 or psi <= 0 at site %lld", d);
-    }
     int rc = ensure_staging3(c);
     if (rc != LBD_OK) return rc;
     CK3(c, cudaSetDevice(c->dev));
+    // upload into the staging area, validate there, and build the state only if
+    // every site is valid (the state is left as it was otherwise)
     double *d = c->staging;
+    unsigned long long *bad = reinterpret_cast<unsigned long long *>(d + 6 * N);
     const size_t B = sizeof(double) * N;
+    CK3(c, cudaMemsetAsync(bad, 0xFF, sizeof *bad, c->stream));
     if (rho) CK3(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
+    else k_fill<<<1024, 256, 0, c->stream>>>(N, 1.0, d);
     const double *u[3] = {ux, uy, uz};
     for (int k = 0; k < 3; ++k)
         if (u[k]) CK3(c, cudaMemcpyAsync(d + (k + 1) * N, u[k], B, cudaMemcpyHostToDevice, c->stream));
         else CK3(c, cudaMemsetAsync(d + (k + 1) * N, 0, B, c->stream));
     CK3(c, cudaMemcpyAsync(d + 4 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
     CK3(c, cudaMemcpyAsync(d + 5 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
-    if (!rho) {
-        // rho = 1: fill on the host side of the copy to keep this path simple
-        double *h = nullptr;
-        if (cudaMallocHost(&h, B) != cudaSuccess) {
-            cudaGetLastError();
-            return fail3(c, LBD_ENOMEM, "host staging allocation failed");
-        }
-        for (long long k = 0; k < N; ++k) h[k] = 1.0;
-        cudaError_t e = cudaMemcpyAsync(d, h, B, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        cudaFreeHost(h);
-        CK3(c, e);
-    }
+    k_check<<<1024, 256, 0, c->stream>>>(N, d, p.B0, p.B1, bad);
+    CK3(c, cudaGetLastError());
     const Geo3 G = geo(c);
     if (p.precision == LBD_FP64)
-        k_init<double><<<1024, 256, 0, c->stream>>>(G, d, (double *)c->g[c->cur],
+        k_init<double><<<1024, 256, 0, c->stream>>>(G, d, bad, (double *)c->g[c->cur],
                                                     (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
     else
-        k_init<float><<<1024, 256, 0, c->stream>>>(G, d, (float *)c->g[c->cur],
+        k_init<float><<<1024, 256, 0, c->stream>>>(G, d, bad, (float *)c->g[c->cur],
                                                    (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
     CK3(c, cudaGetLastError());
+    unsigned long long first = 0;
+    CK3(c, cudaMemcpyAsync(&first, bad, sizeof first, cudaMemcpyDeviceToHost, c->stream));
     CK3(c, cudaStreamSynchronize(c->stream));
+    if (first != ~0ull) {
+        const long long site = (long long)(first >> 2);
+        switch ((int)(first & 3ull)) {
+            case 1: return fail3(c, LBD_ENONFINITE, "non-finite value at site %lld", site);
+            case 2: return fail3(c, LBD_EUNSTABLE, "B(psi) <= 0 or psi <= 0 at site %lld", site);
+            default: return fail3(c, LBD_EINVAL, "rho <= 0 at site %lld", site);
+        }
+    }
     return LBD_OK;
 }
 

@@ -130,6 +130,20 @@ def test_3d_rejects_bad_fields():
     with pytest.raises(lbd.LbdError) as e:
         sim.set_fields(bad, np.full((8, 8, 8), 0.1))
     assert e.value.code == lbd.LBD_ENONFINITE
+    assert "site %d" % ((1 * 8 + 2) * 8 + 3) in str(e.value)
+    rho = np.ones((8, 8, 8))
+    rho[0, 0, 5] = -1.0
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields(z, np.full((8, 8, 8), 0.1), rho=rho)
+    assert e.value.code == lbd.LBD_EINVAL
+    # a rejected upload leaves the state as it was
+    good = np.tanh(np.linspace(-2, 2, 8))[None, None, :].repeat(8, 0).repeat(8, 1)
+    sim.set_fields(good, np.full((8, 8, 8), 0.1))
+    before = sim.fields()
+    with pytest.raises(lbd.LbdError):
+        sim.set_fields(bad, np.full((8, 8, 8), 0.1))
+    for a, b in zip(sim.fields(), before):
+        assert np.array_equal(a, b)
     sim.close()
 
 
