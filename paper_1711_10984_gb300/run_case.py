@@ -4,6 +4,8 @@
         --precision fp32 --steps 10 [--tile 32x16]
     python -m paper_1711_10984_gb300.run_case --workload emulsion3 --n 128 \
         --droplets 8 --radius 12 --steps 7          (the 3D step on an n^3 box)
+    python -m paper_1711_10984_gb300.run_case --workload adjoint --n 256 \
+        --steps 200 --ckpt 100                      (FP32 forward + hand adjoint)
 
 Prints the final diagnostics.  Used as the profiling target of the ncu
 summaries under profiles/.
@@ -27,13 +29,14 @@ def make(workload, n):
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="emulsion",
-                    choices=["emulsion", "single", "two", "emulsion3"])
+                    choices=["emulsion", "single", "two", "emulsion3", "adjoint"])
     ap.add_argument("--droplets", type=int, default=64, help="emulsion3: droplet count")
     ap.add_argument("--radius", type=float, default=16.0, help="emulsion3: droplet radius")
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--tile", default=None)
+    ap.add_argument("--ckpt", type=int, default=100, help="adjoint: checkpoint interval")
     a = ap.parse_args(argv)
     prec = lbd.LBD_FP32 if a.precision == "fp32" else lbd.LBD_FP64
     if a.workload == "emulsion3":
@@ -45,6 +48,18 @@ def main(argv=None):
         sim.step(a.steps)
         d0 = w["droplets"][0]
         print(json.dumps(sim.diagnostics(d0["x"] % a.n, d0["y"] % a.n, d0["z"] % a.n)))
+        sim.close()
+        return
+    if a.workload == "adjoint":
+        # one droplet R = 30 on n x n, source on; gradient of the centroid x-shift
+        n = a.n
+        d = dict(x=n / 2, y=n / 2, R=30.0, psi_mean=0.1, noise=0.01, gx=0.005)
+        phi, psi = inputs.droplet_fields(n, n, [d], seed=4)
+        kw = dict(inputs.PAPER, gamma=1.5e-3, c0=0.09, A0=1.5e-10, A_max=1e-4, t_on=0)
+        sim = lbd.Sim(n, n, precision=prec, sources=[inputs.default_source(d, n, n)], **kw)
+        sim.set_fields(phi, psi)
+        L, _, dB1 = sim.adjoint(a.steps, a.ckpt, n / 2, want_dpsi=False)
+        print(json.dumps(dict(loss=L, dL_dB1=dB1)))
         sim.close()
         return
     w = make(a.workload, a.n)
