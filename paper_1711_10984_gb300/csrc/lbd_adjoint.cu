@@ -243,16 +243,19 @@ __global__ void fwd45(AdjPar<R> p, Work<R> w) {
 }
 
 // ---- reverse of the phi and psi updates (Eqs. 18, 19) on the tile and its halo,
-// then of mu*, m* (Eq. 3 on phi*, psi*) on the tile: the local terms, dB1, and
-// the transposed stencils of products formed at each neighbour -----------------
+// with the products that the transposed stencils of mu*, m* need formed there;
+// then the reverse of mu*, m* (Eq. 3 on phi*, psi*) on the tile: the local
+// terms, dB1, and the transposed stencils ------------------------------------------
 template <typename R>
 __global__ void adj_ed(AdjPar<R> p, const R *gam, int jstep, Work<R> w) {
     __shared__ R sMU[THN], sM[THN], sPSS[THN];  // lambda mu*, lambda m*, lambda psi* (partial)
+    __shared__ R sT[7][THN];                     // products at each halo-tile site
     const R gamma = gam[jstep];  // sink rate of the reversed step (j-th of its segment)
+    const R B0 = p.B0, B1 = p.B1;
     over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
         const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
         const long long s = q.c;
-        sMU[e] = p.M * Lap(at(w.Lphi, q));
+        const R lmus = p.M * Lap(at(w.Lphi, q));
         const long long nb[8] = {q.e, q.w, q.n, q.s, q.ne, q.nw, q.se, q.sw};
         const R *Lp = w.Lpsi, *m = w.MS, *c = w.PSS;
         R lpss = Lp[s] * (R(1.0) - gamma), lms = R(0.0);
@@ -265,29 +268,30 @@ __global__ void adj_ed(AdjPar<R> p, const R *gam, int jstep, Work<R> w) {
                                  Lp[j] * (R(1.0) + R(0.5) * (m[s] - m[j])));
             lms += p.D * lam * R(0.5) * (c[s] + c[j]) * (Lp[j] - Lp[s]);
         }
-        sPSS[e] = lpss;
+        sMU[e] = lmus;
         sM[e] = lms;
+        sPSS[e] = lpss;
+        const R gqx = w.GQx[s], gqy = w.GQy[s];
+        sT[0][e] = (B0 + B1 * c[s]) * lmus;  // for -L(.)
+        sT[1][e] = lmus * w.GRx[s];         // B1 div(lambda mu* grad psi*) -> phi*
+        sT[2][e] = lmus * w.GRy[s];
+        sT[3][e] = lmus * gqx;              // B1 div(lambda mu* grad phi*) -> psi*
+        sT[4][e] = lmus * gqy;
+        sT[5][e] = lms * gqx;               // -B1 div(lambda m* grad phi*) -> phi*
+        sT[6][e] = lms * gqy;
     });
     __syncthreads();
     LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx), t = tile_nbr();
-    const R *PSS = w.PSS, *GQx = w.GQx, *GQy = w.GQy, *GRx = w.GRx, *GRy = w.GRy;
-    const R B0 = p.B0, B1 = p.B1;
-    auto T1 = [&](int k) { return (B0 + B1 * PSS[q[k]]) * sMU[t[k]]; };  // for -L(.)
-    auto T2 = [&](int k) { return sMU[t[k]] * GRx[q[k]]; };  // B1 div(lambda mu* grad psi*) -> phi*
-    auto T3 = [&](int k) { return sMU[t[k]] * GRy[q[k]]; };
-    auto T4 = [&](int k) { return sMU[t[k]] * GQx[q[k]]; };  // B1 div(lambda mu* grad phi*) -> psi*
-    auto T5 = [&](int k) { return sMU[t[k]] * GQy[q[k]]; };
-    auto T6 = [&](int k) { return sM[t[k]] * GQx[q[k]]; };   // -B1 div(lambda m* grad phi*) -> phi*
-    auto T7 = [&](int k) { return sM[t[k]] * GQy[q[k]]; };
+    const Nbr t = tile_nbr();
+    auto T = [&](int i) { return At<R>{sT[i], t}; };
     const R lmu = sMU[t.c], lm = sM[t.c];
-    const R qx = GQx[s], qy = GQy[s], rx = GRx[s], ry = GRy[s];
+    const R qx = w.GQx[s], qy = w.GQy[s], rx = w.GRx[s], ry = w.GRy[s];
     const R ph = w.PH[s];
     w.Lphi0[s] = R(3.0) * p.b * ph * ph * lmu;  // cubic term uses phi^n
-    w.dB1[s] += (double)(lmu * (-PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
+    w.dB1[s] += (double)(lmu * (-w.PSS[s] * w.LQ[s] - (qx * rx + qy * ry)) +
                          lm * R(0.5) * (qx * qx + qy * qy));
-    w.LPHS[s] = w.Lphi[s] + p.a * lmu - Lap(T1) + B1 * Div(T2, T3) - B1 * Div(T6, T7);
-    w.LPSS[s] = (sPSS[t.c] + -B1 * w.LQ[s] * lmu) + B1 * Div(T4, T5);
+    w.LPHS[s] = w.Lphi[s] + p.a * lmu - Lap(T(0)) + B1 * Div(T(1), T(2)) - B1 * Div(T(5), T(6));
+    w.LPSS[s] = (sPSS[t.c] + -B1 * w.LQ[s] * lmu) + B1 * Div(T(3), T(4));
 }
 
 // ---- reverse of the donor-cell advection (Eqs. 16-17), then of the collision
@@ -356,44 +360,49 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
 }
 
 // ---- reverse of the force (Eq. 14) on the tile and its halo: lambda mu =
-// div(phi lambda F), lambda m = div(psi lambda F); then the force's local terms
-// and grad psi term, and the reverse of mu, m (Eqs. 3, 5) on the tile ----------
+// div(phi lambda F), lambda m = div(psi lambda F), and there the products that
+// the transposed stencils of mu, m need; then the force's local terms and grad
+// psi term, and the reverse of mu, m (Eqs. 3, 5) on the tile -------------------
 template <typename R>
 __global__ void adj_a(AdjPar<R> p, Work<R> w) {
     __shared__ R sMU[THN], sM[THN];  // lambda mu, lambda m
+    __shared__ R sT[7][THN];         // products at each halo-tile site
     const R *LFX = w.LFX, *LFY = w.LFY, *PH = w.PH, *PS = w.PS;
+    const R B0 = p.B0, B1 = p.B1;
     over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
         const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
         auto T1 = [&](int k) { return PH[q[k]] * LFX[q[k]]; };  // -> lambda mu
         auto T2 = [&](int k) { return PH[q[k]] * LFY[q[k]]; };
         auto T3 = [&](int k) { return PS[q[k]] * LFX[q[k]]; };  // -> lambda m
         auto T4 = [&](int k) { return PS[q[k]] * LFY[q[k]]; };
-        sMU[e] = Div(T1, T2);
-        sM[e] = Div(T3, T4);
+        const R lmu = Div(T1, T2), lm = Div(T3, T4);
+        sMU[e] = lmu;
+        sM[e] = lm;
+        const long long s = q.c;
+        const R gpx = w.GPx[s], gpy = w.GPy[s];
+        sT[0][e] = (B0 + B1 * PS[s]) * lmu;
+        sT[1][e] = lmu * w.GSx[s];
+        sT[2][e] = lmu * w.GSy[s];
+        sT[3][e] = lmu * gpx;
+        sT[4][e] = lmu * gpy;
+        sT[5][e] = lm * gpx;
+        sT[6][e] = lm * gpy;
     });
     __syncthreads();
     LBD_SITE(p)
     const Nbr q = nbr(x, y, p.nx, p.ny, p.nx), t = tile_nbr();
+    auto T = [&](int i) { return At<R>{sT[i], t}; };
     const R lfx = LFX[s], lfy = LFY[s];
-    R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
-    R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) + Div(at(LFX, q), at(LFY, q));
-    const R *GPx = w.GPx, *GPy = w.GPy, *GSx = w.GSx, *GSy = w.GSy;
-    const R B0 = p.B0, B1 = p.B1;
-    auto T1 = [&](int k) { return (B0 + B1 * PS[q[k]]) * sMU[t[k]]; };
-    auto T2 = [&](int k) { return sMU[t[k]] * GSx[q[k]]; };
-    auto T3 = [&](int k) { return sMU[t[k]] * GSy[q[k]]; };
-    auto T4 = [&](int k) { return sMU[t[k]] * GPx[q[k]]; };
-    auto T5 = [&](int k) { return sMU[t[k]] * GPy[q[k]]; };
-    auto T6 = [&](int k) { return sM[t[k]] * GPx[q[k]]; };
-    auto T7 = [&](int k) { return sM[t[k]] * GPy[q[k]]; };
+    const R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
+    const R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) + Div(at(LFX, q), at(LFY, q));
     const R lmu = sMU[t.c], lm = sM[t.c];
-    const R px = GPx[s], py = GPy[s], cx = GSx[s], cy = GSy[s];
+    const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
     const R ph = PH[s];
     w.dB1[s] += (double)(lmu * (-PS[s] * w.LP[s] - (px * cx + py * cy)) +
                          lm * R(0.5) * (px * px + py * py));
     w.Lphi0[s] = (lphi + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
-                 (-Lap(T1) + B1 * Div(T2, T3) - B1 * Div(T6, T7));
-    w.Lpsi0[s] = (lpsi + -B1 * w.LP[s] * lmu) + B1 * Div(T4, T5);
+                 (-Lap(T(0)) + B1 * Div(T(1), T(2)) - B1 * Div(T(5), T(6)));
+    w.Lpsi0[s] = (lpsi + -B1 * w.LP[s] * lmu) + B1 * Div(T(3), T(4));
 }
 
 // ---- loss: centroid x of the phi >= 0 region and its gradient ---------------------

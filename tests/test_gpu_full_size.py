@@ -1,7 +1,8 @@
 """Parity at the bench's full size: the 2048 x 2048 emulsion (64 droplets R = 25
 with seeded psi ramps, 64 sources, sink on), in the launch shape the bench
 times (the autotuner's choice for this lattice) and in every stripe shape it
-chooses from.
+chooses from; and the bench's walls leg, the same emulsion between bounce-back
+plates at y = -1/2 and 2047.5.
 
 The GPU runs from the seeded initial state into developed flow; its state then
 (pre-collision populations, phi, psi, t) is handed to the FP64 oracle, and both
@@ -32,8 +33,9 @@ def work():
     return inputs.emulsion(n=N, count=64, seed=5)
 
 
-def advance_both(w, prec, tile):
-    sim = lbd.Sim(N, N, precision=prec, sources=w["sources"], **w["params"])
+def advance_both(w, prec, tile, walls=False):
+    sim = lbd.Sim(N, N, precision=prec, sources=w["sources"],
+                  flags=lbd.LBD_WALLS if walls else 0, **w["params"])
     if tile == "bench":
         import torch
         tile = autotune.tune(sim, torch.cuda.get_device_name())
@@ -42,7 +44,8 @@ def advance_both(w, prec, tile):
     sim.set_fields(w["phi"], w["psi"])
     sim.step(LEAD)
     _, _, _, phi, psi = sim.fields()
-    ref = oracle.State(oracle.Params(N, N, sources=w["sources"], **w["params"]), phi, psi, t=sim.t)
+    ref = oracle.State(oracle.Params(N, N, sources=w["sources"], flags=oracle.WALLS if walls else 0,
+                                     **w["params"]), phi, psi, t=sim.t)
     ref.f[...] = sim.populations()
     sim.step(STEPS)
     ref.step(STEPS)
@@ -67,3 +70,16 @@ def test_fp32_full_size(work, tile):
     for k in (1, 2, 3, 4):  # ux, uy, phi, psi
         assert np.abs(g[k] - r[k]).max() <= 1e-4, (k, used)
     assert np.abs(g[0] - r[0]).max() <= 1e-5
+
+
+@pytest.mark.parametrize("prec,tile", [(lbd.LBD_FP32, "bench"), (lbd.LBD_FP64, (118, 64))],
+                         ids=["fp32-bench", "fp64-118x64"])
+def test_walls_full_size(work, prec, tile):
+    g, gf, r, rf, used = advance_both(work, prec, tile, walls=True)
+    if prec == lbd.LBD_FP64:
+        for a, b in zip(g, r):
+            assert np.abs(a - b).max() / np.abs(b).max() <= 1e-10, used
+        assert np.abs(gf - rf).max() / np.abs(rf).max() <= 1e-10
+    else:
+        for k in (1, 2, 3, 4):
+            assert np.abs(g[k] - r[k]).max() <= 1e-4, (k, used)
