@@ -24,9 +24,10 @@
 // A reversed step is five kernels, one thread per site.  Where a stage
 // differentiates the output of the stage before it, the two share a kernel: the
 // first is evaluated on the block's tile and a one-site halo into shared
-// memory.  Pointwise products that feed a transposed stencil are formed at each
-// neighbour instead of being stored, and the reverse of the collision runs in
-// the kernel that produces its lambda u.
+// memory.  Pointwise products that feed a transposed stencil are formed once per
+// halo-tile site there (or, where their factors come from the previous kernel,
+// at each neighbour) instead of being stored in global memory, and the reverse
+// of the collision runs in the kernel that produces its lambda u.
 // The upwind choices and the phi >= 0 mask of the centroid are taken from the
 // forward state (they are piecewise constant).
 #include <cmath>
