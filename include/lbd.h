@@ -66,8 +66,8 @@ extern "C" {
  * mirrored across each plate (row -1-k is row k, row ny+k is row ny-1-k), so
  * their normal derivatives vanish; no advective flux crosses a plate; source
  * disks do not wrap through the plates.  Needs ny >= 8; steps run on the
- * stripe launch shapes (bx 118 or 246); not available to batches or to
- * lbd_adjoint (LBD_EINVAL). */
+ * stripe and tiled launch shapes (not the column-pair one); not available to
+ * batches or to lbd_adjoint (LBD_EINVAL). */
 #define LBD_WALLS 16u
 
 #define LBD_MAX_SOURCES 64
@@ -229,7 +229,7 @@ int lbd_squirmer(lbd_ctx *ctx, int32_t n, const lbd_droplet *drops, double *b1, 
  * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
  * column per thread, segments of by rows); bx 240: FP32 column-pair kernel
  * with packed FP32x2 arithmetic (needs nx % 4 == 0 and nx >= 264).  With
- * LBD_WALLS only the stripe shapes are valid.  Shapes not
+ * LBD_WALLS the column-pair shapes are not valid.  Shapes not
  * compiled in, or not valid for the context's precision and lattice, return
  * LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
  * kernels agree to rounding. */

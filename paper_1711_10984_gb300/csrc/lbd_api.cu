@@ -507,7 +507,7 @@ int update_theta(lbd_ctx *c) {
 // its precision and lattice, and a stripe shape when the lattice has walls.
 bool tile_ok(const lbd_ctx *c, Tile t) {
     if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane)) return false;
-    return !(c->params.flags & LBD_WALLS) || t.bx == 118 || t.bx == 246;
+    return !(c->params.flags & LBD_WALLS) || t.bx != 240;  // no walls in the column-pair kernel
 }
 
 int ensure_staging(lbd_ctx *c) {
@@ -768,19 +768,7 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
             sms = 1;
         }
         const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
-        if (params->flags & LBD_WALLS) {
-            // stripe shapes only: shorter segments where 64 rows leave SMs idle
-            for (int by : {32, 16})
-                if ((long long)((grid->nx + 117) / 118) * ((grid->ny + c->tile.by - 1) / c->tile.by) <
-                    2LL * sms)
-                    c->tile = Tile{118, by};
-            if (!tile_ok(c, c->tile)) {
-                lbd_destroy(c);
-                return LBD_EINVAL;  // too large for the stripe kernel's 32-bit offsets
-            }
-        } else if (stripe_ctas < 2LL * sms || !tile_ok(c, c->tile)) {
-            c->tile = Tile{32, 8};
-        }
+        if (stripe_ctas < 2LL * sms || !tile_ok(c, c->tile)) c->tile = Tile{32, 8};
     }
     if (update_theta(c) != LBD_OK) {
         lbd_destroy(c);
@@ -798,11 +786,12 @@ int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
         return fail(c, LBD_EINVAL, "precision cannot change after creation");
     const lbd_params keep = c->params;
     c->params = *p;
-    if ((p->flags & LBD_WALLS) && !tile_ok(c, c->tile)) {
+    if ((p->flags & LBD_WALLS) && !tile_ok(c, c->tile)) {  // the column-pair shape
         c->tile = Tile{118, 64};
+        if (!tile_ok(c, c->tile)) c->tile = Tile{32, 8};
         if (!tile_ok(c, c->tile)) {
             c->params = keep;
-            return fail(c, LBD_EINVAL, "walls need the stripe kernel, which this lattice exceeds");
+            return fail(c, LBD_EINVAL, "no launch shape runs walls on this lattice");
         }
     }
     CK(c, cudaSetDevice(c->dev));

@@ -294,13 +294,40 @@ __global__ void __launch_bounds__(NT) step_kernel(const StepArgs<T> p) {
         const T ue = T(0.5) * (UX[0] + UX[1]), uw = T(0.5) * (UX[-1] + UX[0]);
         const T un = T(0.5) * (UY[0] + UY[W3]), us = T(0.5) * (UY[-W3] + UY[0]);
         const T pe = ue * (ue > T(0) ? P[0] : P[1]), pw = uw * (uw > T(0) ? P[-1] : P[0]);
-        const T pn = un * (un > T(0) ? P[0] : P[W5]), ps = us * (us > T(0) ? P[-W5] : P[0]);
+        T pn = un * (un > T(0) ? P[0] : P[W5]), ps = us * (us > T(0) ? P[-W5] : P[0]);
         const T ce = ue * (ue > T(0) ? C[0] : C[1]), cw = uw * (uw > T(0) ? C[-1] : C[0]);
-        const T cn = un * (un > T(0) ? C[0] : C[W5]), cs = us * (us > T(0) ? C[-W5] : C[0]);
+        T cn = un * (un > T(0) ? C[0] : C[W5]), cs = us * (us > T(0) ? C[-W5] : C[0]);
+        if (walls) {  // no advective flux through a plate face
+            const int yr = y0 - 2 + ly;
+            if (yr == 0) {
+                ps = T(0);
+                cs = T(0);
+            }
+            if (yr == ny - 1) {
+                pn = T(0);
+                cn = T(0);
+            }
+        }
         s_phs[k] = P[0] - ((pe - pw) + (pn - ps));
         s_pss[k] = C[0] - ((ce - cw) + (cn - cs));
     }
     __syncthreads();
+    // With plates, phi* and psi* on the two rows beyond a plate are the mirror
+    // of the two rows inside (row -1 - k is row k); every output row reads no
+    // further, and the mirrored rows lie in the same R2 region.
+    if (walls && (y0 - 2 < 0 || y0 + BY + 2 > ny)) {
+        for (int k = tid; k < W2 * H2; k += NT) {
+            const int ly = k / W2, lx = k - ly * W2;
+            const int yr = y0 - 2 + ly;
+            if (yr == -2 || yr == -1 || yr == ny || yr == ny + 1) {
+                const int ym = yr < 0 ? -1 - yr : 2 * ny - 1 - yr;
+                const int m = (ym - (y0 - 2)) * W2 + lx;
+                s_phs[k] = s_phs[m];
+                s_pss[k] = s_pss[m];
+            }
+        }
+        __syncthreads();
+    }
 
     // ---- stage D: mu* and m* on R1 (into the R4 buffers, R1 stride) --------
     for (int k = tid; k < W1 * H1; k += NT) {

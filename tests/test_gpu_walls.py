@@ -54,7 +54,12 @@ def run_both(nx, ny, steps, prec, tile, seed, flags=0, **kw):
 
 @pytest.mark.parametrize("nx,ny,tile", [(128, 64, (118, 64)), (128, 64, (246, 32)),
                                         (161, 70, (118, 32)), (100, 23, (118, 64)),
-                                        (40, 8, (118, 32)), (300, 130, (246, 64))])
+                                        (40, 8, (118, 32)), (300, 130, (246, 64)),
+                                        # tiled kernel: whole and partial last tiles
+                                        (128, 64, (32, 8)), (161, 70, (32, 16)),
+                                        (100, 23, (64, 8)), (40, 8, (32, 8)),
+                                        (64, 9, (32, 8)), (300, 130, (32, 32)),
+                                        (70, 13, (64, 16))])
 def test_fp64_walls_match_oracle(nx, ny, tile):
     sim, ref = run_both(nx, ny, 300, lbd.LBD_FP64, tile, seed=nx + 7 * ny)
     for g, r in zip(sim.fields(), ref.fields()):
@@ -63,8 +68,9 @@ def test_fp64_walls_match_oracle(nx, ny, tile):
     sim.close()
 
 
-def test_fp32_walls_match_oracle():
-    sim, ref = run_both(256, 96, 600, lbd.LBD_FP32, (118, 64), seed=3)
+@pytest.mark.parametrize("tile", [(118, 64), (32, 8)])
+def test_fp32_walls_match_oracle(tile):
+    sim, ref = run_both(256, 96, 600, lbd.LBD_FP32, tile, seed=3)
     g, r = sim.fields(), ref.fields()
     for k in (1, 2, 3, 4):
         assert np.abs(g[k] - r[k]).max() <= 1e-4, k
@@ -139,13 +145,13 @@ def test_conservation_with_walls_on_gpu(prec):
 
 
 def test_walls_rejected_where_unsupported():
-    sim = lbd.Sim(128, 64, precision=lbd.LBD_FP32, flags=lbd.LBD_WALLS)
-    for tile in ((32, 16), (64, 8), (240, 64)):
-        with pytest.raises(lbd.LbdError) as e:
-            sim.set_tile(*tile)
-        assert e.value.code == lbd.LBD_EINVAL
+    sim = lbd.Sim(264, 64, precision=lbd.LBD_FP32, flags=lbd.LBD_WALLS)
+    with pytest.raises(lbd.LbdError) as e:  # the column-pair kernel has no walls
+        sim.set_tile(240, 64)
+    assert e.value.code == lbd.LBD_EINVAL
+    sim.set_tile(32, 16)
     with pytest.raises(lbd.LbdError) as e:
-        sim.adjoint(10, 5, 64.0)
+        sim.adjoint(10, 5, 132.0)
     assert e.value.code == lbd.LBD_EINVAL
     sim.close()
     with pytest.raises(lbd.LbdError) as e:
