@@ -151,8 +151,9 @@ class Clocks:
 
 # ------------------------------------------------------------------ ours
 def kernel_source_hash():
+    """Hash of the sources of the profiled step kernel (stripe_kernel)."""
     h = hashlib.sha256()
-    for name in ("lbd_step.cu", "lbd_stripe.cu", "lbd_stripe2.cu", "lbd_internal.h"):
+    for name in ("lbd_stripe.cu", "lbd_internal.h"):
         with open(os.path.join(ROOT, "paper_1711_10984_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
