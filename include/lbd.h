@@ -66,8 +66,8 @@ extern "C" {
  * mirrored across each plate (row -1-k is row k, row ny+k is row ny-1-k), so
  * their normal derivatives vanish; no advective flux crosses a plate; source
  * disks do not wrap through the plates.  Needs ny >= 8; steps run on the
- * stripe and tiled launch shapes (not the column-pair one); not available to
- * batches or to lbd_adjoint (LBD_EINVAL). */
+ * stripe and tiled launch shapes (not the column-pair one) and in batches; not
+ * available to lbd_adjoint (LBD_EINVAL). */
 #define LBD_WALLS 16u
 
 #define LBD_MAX_SOURCES 64
@@ -303,7 +303,8 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
  * (instance, stripe, row segment) items, and lbd_batch_step replays chunks of
  * 100 such launches from a captured CUDA graph (the activity schedule is
  * evaluated on the device from a device-side step count).  Instance k behaves
- * exactly like a context of its own: same state layout, same results. */
+ * exactly like a context of its own: same state layout, same results; the
+ * instances may mix periodic lattices and lattices with plates (LBD_WALLS). */
 typedef struct lbd_batch lbd_batch;
 
 /* grids[k], params[k]: as for lbd_create (params[k].precision must agree).

@@ -54,8 +54,10 @@ struct lbd_batch {
     bool own_stream = false;
     int prec = LBD_FP32;
     void *args_dev[2] = {nullptr, nullptr};  // StepArgs<T>[n] for buffer parity 0 / 1
-    lbd::BatchItem *items_dev = nullptr;
+    lbd::BatchItem *items_dev = nullptr;  // periodic instances' items, then those with plates
     int n_items = 0;
+    int n_plain = 0;                       // items of periodic instances
+    int ctas_walls = 1;
     long long *t_dev = nullptr;
     Tile tile{118, 64};
     int ctas = 1;
@@ -598,8 +600,11 @@ int batch_build(lbd_batch *b) {
             for (int x0 = 0; x0 < nx; x0 += bxo)
                 items.push_back(lbd::BatchItem{k, x0, y0, seg});
     }
-    // largest lattices first, so that the tail of the persistent walk is short
+    // periodic instances first (the plates take a launch of their own); within
+    // each, largest lattices first, so that the tail of the persistent walk is short
+    auto walls = [&](const lbd::BatchItem &u) { return (b->ctx[u.k]->params.flags & LBD_WALLS) != 0; };
     std::stable_sort(items.begin(), items.end(), [&](const lbd::BatchItem &u, const lbd::BatchItem &v) {
+        if (walls(u) != walls(v)) return !walls(u);
         return b->ctx[u.k]->N > b->ctx[v.k]->N;
     });
     if (b->items_dev) cudaFree(b->items_dev);
@@ -609,19 +614,28 @@ int batch_build(lbd_batch *b) {
                            cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
+    b->n_plain = (int)std::count_if(items.begin(), items.end(), [&](const lbd::BatchItem &u) { return !walls(u); });
     int sms = 0;
     BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
     const int per_sm = lbd::stripe_batch_ctas_per_sm<T>(bxo + 10);
-    b->ctas = std::min(b->n_items, sms * per_sm);
+    b->ctas = std::min(b->n_plain, sms * per_sm);
+    b->ctas_walls = std::min(b->n_items - b->n_plain, sms * per_sm);
     batch_drop_graphs(b);
     return LBD_OK;
 }
 
 template <typename T>
 cudaError_t batch_launch(lbd_batch *b, int parity, int t_off) {
-    return lbd::launch_stripe_batch<T>((const StepArgs<T> *)b->args_dev[parity], b->items_dev,
-                                       b->n_items, b->tile.bx + 10, b->ctas, b->t_dev, t_off,
-                                       b->stream);
+    const StepArgs<T> *args = (const StepArgs<T> *)b->args_dev[parity];
+    cudaError_t e = cudaSuccess;
+    if (b->n_plain > 0)
+        e = lbd::launch_stripe_batch<T>(args, b->items_dev, b->n_plain, b->tile.bx + 10, false,
+                                        b->ctas, b->t_dev, t_off, b->stream);
+    if (e == cudaSuccess && b->n_items > b->n_plain)
+        e = lbd::launch_stripe_batch<T>(args, b->items_dev + b->n_plain, b->n_items - b->n_plain,
+                                        b->tile.bx + 10, true, b->ctas_walls, b->t_dev, t_off,
+                                        b->stream);
+    return e;
 }
 
 template <typename T>
@@ -1313,8 +1327,7 @@ int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params,
     if (!out || !grids || !params || n < 1) return LBD_EINVAL;
     *out = nullptr;
     for (int k = 0; k < n; ++k)
-        if (params[k].precision != params[0].precision || (params[k].flags & LBD_WALLS))
-            return LBD_EINVAL;
+        if (params[k].precision != params[0].precision) return LBD_EINVAL;
     lbd_batch *b = new (std::nothrow) lbd_batch();
     if (!b) return LBD_ENOMEM;
     b->n = n;

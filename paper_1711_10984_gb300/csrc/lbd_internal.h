@@ -77,12 +77,13 @@ cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s)
 template <typename T>
 size_t stripe_smem_bytes(int nt);
 
-// One step of every instance of a batch: a persistent grid of ctas CTAs walks
-// the work list; instance k reads its arguments from args[k]; the step count of
+// One step of the instances of a batch that share one variant (walls false:
+// periodic; true: with plates): a persistent grid of ctas CTAs walks the n_items
+// work items; instance k reads its arguments from args[k]; the step count of
 // this launch is *t_dev + t_off.
 template <typename T>
 cudaError_t launch_stripe_batch(const StepArgs<T> *args, const BatchItem *items, int n_items,
-                                int nt, int ctas, const long long *t_dev, int t_off,
+                                int nt, bool walls, int ctas, const long long *t_dev, int t_off,
                                 cudaStream_t s);
 
 // Resident CTAs per SM of the batched kernel (occupancy calculator).

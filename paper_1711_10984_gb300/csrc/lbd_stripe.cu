@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
 // Batched step: CTAs walk the work list; the arguments of the item's instance
 // are staged in shared memory and the activity is evaluated from the device
 // step count (so that the launch can be replayed from a CUDA graph).
-template <typename T, int NT>
+template <typename T, int NT, bool WALLS>
 __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
     stripe_batch_kernel(const StepArgs<T> *args, const BatchItem *items, const int n_items,
                         const long long *t_dev, const int t_off) {
@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
             s_gamma = (T)g;
         }
         __syncthreads();
-        stripe_body<T, NT, false>(sp, item.x0, item.y0, item.rows, s_A, s_gamma, smem_raw);
+        stripe_body<T, NT, WALLS>(sp, item.x0, item.y0, item.rows, s_A, s_gamma, smem_raw);
         __syncthreads();
     }
 }
@@ -597,33 +597,39 @@ cudaError_t launch_stripe(const StepArgs<T> &a, int nt, int seg, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
-template <typename T>
-cudaError_t launch_stripe_batch(const StepArgs<T> *args, const BatchItem *items, int n_items,
-                                int nt, int ctas, const long long *t_dev, int t_off,
-                                cudaStream_t s) {
-    const size_t smem = stripe_smem_bytes<T>(nt);
-    static unsigned long long configured[2] = {0, 0};
+// One launch of the batch walk over n_items items of one variant (periodic, or
+// with plates: each is its own instantiation, so that an instance computes
+// exactly as it would in a context of its own).
+template <typename T, int NT, bool WALLS>
+cudaError_t launch_stripe_batch_as(const StepArgs<T> *args, const BatchItem *items, int n_items,
+                                   int ctas, const long long *t_dev, int t_off, cudaStream_t s) {
+    const size_t smem = stripe_smem_bytes<T>(NT);
+    static unsigned long long configured = 0;  // one bit per device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    const int which = nt == 128 ? 0 : 1;
     const unsigned long long bit = 1ull << (dev & 63);
-    if (!(configured[which] & bit)) {
-        e = nt == 128
-                ? cudaFuncSetAttribute(stripe_batch_kernel<T, 128>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                : cudaFuncSetAttribute(stripe_batch_kernel<T, 256>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(stripe_batch_kernel<T, NT, WALLS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        configured[which] |= bit;
+        configured |= bit;
     }
-    if (nt == 128)
-        stripe_batch_kernel<T, 128><<<ctas, 128, smem, s>>>(args, items, n_items, t_dev, t_off);
-    else if (nt == 256)
-        stripe_batch_kernel<T, 256><<<ctas, 256, smem, s>>>(args, items, n_items, t_dev, t_off);
-    else
-        return cudaErrorInvalidValue;
+    stripe_batch_kernel<T, NT, WALLS><<<ctas, NT, smem, s>>>(args, items, n_items, t_dev, t_off);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stripe_batch(const StepArgs<T> *args, const BatchItem *items, int n_items,
+                                int nt, bool walls, int ctas, const long long *t_dev, int t_off,
+                                cudaStream_t s) {
+    if (nt == 128)
+        return walls ? launch_stripe_batch_as<T, 128, true>(args, items, n_items, ctas, t_dev, t_off, s)
+                     : launch_stripe_batch_as<T, 128, false>(args, items, n_items, ctas, t_dev, t_off, s);
+    if (nt == 256)
+        return walls ? launch_stripe_batch_as<T, 256, true>(args, items, n_items, ctas, t_dev, t_off, s)
+                     : launch_stripe_batch_as<T, 256, false>(args, items, n_items, ctas, t_dev, t_off, s);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -631,9 +637,9 @@ int stripe_batch_ctas_per_sm(int nt) {
     int n = 0;
     const size_t smem = stripe_smem_bytes<T>(nt);
     cudaError_t e = nt == 128 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &n, stripe_batch_kernel<T, 128>, 128, smem)
+                                    &n, stripe_batch_kernel<T, 128, false>, 128, smem)
                               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                                    &n, stripe_batch_kernel<T, 256>, 256, smem);
+                                    &n, stripe_batch_kernel<T, 256, false>, 256, smem);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return 1;
@@ -653,9 +659,11 @@ cudaError_t launch_time_set(long long *t_dev, long long value, cudaStream_t s) {
 }
 
 template cudaError_t launch_stripe_batch<float>(const StepArgs<float> *, const BatchItem *, int,
-                                                int, int, const long long *, int, cudaStream_t);
+                                                int, bool, int, const long long *, int,
+                                                cudaStream_t);
 template cudaError_t launch_stripe_batch<double>(const StepArgs<double> *, const BatchItem *, int,
-                                                 int, int, const long long *, int, cudaStream_t);
+                                                 int, bool, int, const long long *, int,
+                                                 cudaStream_t);
 template cudaError_t launch_stripe<float>(const StepArgs<float> &, int, int, cudaStream_t);
 template cudaError_t launch_stripe<double>(const StepArgs<double> &, int, int, cudaStream_t);
 template size_t stripe_smem_bytes<float>(int);

@@ -69,6 +69,31 @@ def test_batch_equals_instances_alone(prec, tile):
     b.close()
 
 
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
+def test_batch_with_plates_equals_instances_alone(prec):
+    """A batch mixing periodic instances and instances between plates
+    (LBD_WALLS): each one still equals the same instance run on its own."""
+    inst = instances()
+    walls = [k % 2 == 1 for k in range(len(inst))]
+    params = [lbd.make_params(prec, src, flags=lbd.LBD_WALLS if wl else 0, **kw)
+              for wl, (_, _, _, _, src, kw) in zip(walls, inst)]
+    b = lbd.Batch([(nx, ny) for (nx, ny, *_r) in inst], params)
+    b.set_tile(118, 32)
+    for k, (nx, ny, phi, psi, src, kw) in enumerate(inst):
+        b.set_fields(k, phi, psi)
+    b.step(130)
+    for k, (nx, ny, phi, psi, src, kw) in enumerate(inst):
+        s = lbd.Sim(nx, ny, precision=prec, sources=src,
+                    flags=lbd.LBD_WALLS if walls[k] else 0, **kw)
+        s.set_tile(118, 32)
+        s.set_fields(phi, psi)
+        s.step(130)
+        for a, r in zip(b.fields(k), s.fields()):
+            assert np.array_equal(a, r), k
+        s.close()
+    b.close()
+
+
 def test_graph_and_direct_launches_agree():
     b1, _ = make_batch(lbd.LBD_FP32)
     b2, _ = make_batch(lbd.LBD_FP32)

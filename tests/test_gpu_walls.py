@@ -157,6 +157,3 @@ def test_walls_rejected_where_unsupported():
     with pytest.raises(lbd.LbdError) as e:
         lbd.Sim(64, 6, precision=lbd.LBD_FP64, flags=lbd.LBD_WALLS)
     assert e.value.code == lbd.LBD_EINVAL
-    with pytest.raises(lbd.LbdError) as e:
-        lbd.Batch([(128, 64)], [lbd.make_params(precision=lbd.LBD_FP32, flags=lbd.LBD_WALLS)])
-    assert e.value.code == lbd.LBD_EINVAL
