@@ -345,6 +345,36 @@ def time_3d(torch, stream, steps=100, n=256):
                 nonfinite=d["nonfinite"])
 
 
+def time_small(torch, lbd, autotune, stream, dev_name, steps=500):
+    """The small configurations, whose state sits in L2: the 128^2 single
+    droplet (FP64) and the 512x256 two-droplet case (FP32 and FP64), each in
+    the autotuner's launch shape, CUDA events on the launching stream.  These
+    steps are bound by the kernel's latency, not by HBM."""
+    from paper_1711_10984_gb300 import inputs
+    out = {}
+    for name, w, precs in (("single_droplet_128", inputs.single_droplet(), (lbd.LBD_FP64,)),
+                           ("two_droplets_512x256", inputs.two_droplets(),
+                            (lbd.LBD_FP32, lbd.LBD_FP64))):
+        for prec in precs:
+            sim = lbd.Sim(w["nx"], w["ny"], precision=prec, sources=w["sources"],
+                          stream=stream.cuda_stream, **w["params"])
+            sim.set_fields(w["phi"], w["psi"])
+            tile = autotune.tune(sim, dev_name)
+            sim.step(20)
+            sim.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            us = e0.elapsed_time(e1) / steps * 1e3
+            sim.close()
+            out["%s_%s" % (name, "fp32" if prec == lbd.LBD_FP32 else "fp64")] = dict(
+                sites=w["nx"] * w["ny"], us_per_step=round(us, 2),
+                mlups=round(w["nx"] * w["ny"] / us, 1), tile=list(tile))
+    return out
+
+
 def cpu_baseline(w, budget_s=12.0):
     """The FP64 oracle as it stands on the host cores, on the same 2048^2
     workload, for as many whole steps as fit in about budget_s seconds."""
@@ -403,6 +433,7 @@ def run_ours(args):
                         dev_name, barrier)
     trk = time_tracking(lbd, w) if rank == 0 else None
     r3 = time_3d(torch, stream, steps=min(args.steps, 100))
+    small = time_small(torch, lbd, autotune, stream, dev_name, steps=min(args.steps, 500))
 
     maxr = lambda v: max_over_ranks(v, dist, "cuda")
 
@@ -450,6 +481,7 @@ def run_ours(args):
         "fp32_drift": r32["drift"],
         "adjoint_forward_cost": adj,
         "tracking": trk,
+        "small_configs": dict(small, note="state in L2; latency-bound steps, no roofline"),
         "three_d": {"workload": "D3Q19 coupled step, periodic 256^3 box, 64 seeded spherical "
                                 "droplets R=16 with a source ball each, sink on, FP32",
                     "value": round(world * r3["mlups"], 1), "unit": "MLUPS",
