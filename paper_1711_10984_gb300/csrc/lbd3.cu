@@ -1,9 +1,9 @@
 // lbd3.cu -- the coupled step of arXiv 1711.10984 (Section 2) on the D3Q19
 // lattice, and the C ABI of include/lbd3.h.
 //
-// One step is five kernels, one thread per site; each CTA walks a run of z
-// planes of a 32 x 8 tile, the differentiated fields staged in a ring of
-// shared-memory halo planes:
+// One step is five kernels; each CTA walks a run of z planes of a 32 x 8 tile
+// (32 x 16 for the advection, two rows per thread), the differentiated fields
+// staged in a ring of shared-memory halo planes:
 //   k_chem    mu_phi (Eq. 3), m (Eq. 5) at t^n                       -> mu, m
 //   k_lb      F (Eq. 14), pull f_i, u (Eq. 11), BGK + Guo collision
 //             (Eqs. 10, 12, 13), u for the advection                 -> f, u
@@ -62,11 +62,12 @@ struct Arg3 {
 };
 
 // ------------------------------------------------------ z-marching kernels
-// Each CTA owns a TX x TY tile of the xy plane and a run of zl planes, and
-// walks the run in z.  The fields it differentiates pass through a ring of
-// SLOTS shared-memory planes, each the tile with a one-site periodic halo, so
-// that a value is loaded from global memory about HP / NT + 2 / zl times per
-// step instead of once per neighbour (nine xy rows per value with one thread
+// Each CTA of NT = TX x TY threads owns a TX x (TY RY) tile of the xy plane (RY
+// rows per thread) and a run of zl planes, and walks the run in z.  The fields
+// it differentiates pass through a ring of SLOTS shared-memory planes, each the
+// tile with a one-site periodic halo, so that a value is loaded from global
+// memory about HP / (TX TY RY) + 2 / zl times per step instead of once per
+// neighbour (nine xy rows per value with one thread
 // per site).  The planes arrive by cp.async, AHEAD planes ahead of the ones
 // being read.  One barrier per plane: at plane k, after each thread has waited
 // for its own copies of plane k + 1, the barrier makes every copy of plane
