@@ -40,8 +40,11 @@ def tune(sim, device, reps=20, path=CACHE, refresh=False):
     cache = load_cache(path)
     if key in cache and not refresh:
         tile = tuple(cache[key])
-        sim.set_tile(*tile)
-        return tile
-    tile = sim.autotune(reps)
+        try:
+            sim.set_tile(*tile)
+            return tile
+        except RuntimeError:  # a shape the library no longer accepts here: search again
+            pass
+    tile = tuple(sim.autotune(reps))
     store(key, tile, path)
     return tile
