@@ -370,3 +370,31 @@ def test_droplet_fields_profile():
     assert phi[32, 32] == pytest.approx(1.0, abs=1e-3) and phi[0, 0] == pytest.approx(-1.0, abs=1e-12)
     inside = phi > 0
     assert np.abs(psi[inside] - 0.1).max() <= 0.01 and np.all(psi[~inside] == 0.1)
+
+
+@pytest.mark.parametrize("cx,cy,refx,refy", [(0.0, 0.0, 5.0, 3.0), (39.5, 0.5, 35.25, 2.0),
+                                             (20.0, 29.5, 18.0, 27.75), (0.5, 0.0, 3.0, 28.0)])
+def test_centroid_minimum_image_across_the_seam(cx, cy, refx, refy):
+    """The centre of mass of the phi >= 0 region (Section 4) on a periodic
+    lattice: a disk centred on or next to the periodic seam, split between the
+    lattice edges, has the set of sites {(x, y): |x - c|^2 <= R^2} symmetric
+    under the point reflection through its centre c, so its phi-weighted
+    centroid is c exactly (modulo the lattice), whatever the reference point,
+    as long as every site of the disk lies within half a lattice of it."""
+    nx, ny, R = 40, 30, 6.3
+    x = np.arange(nx)[None, :]
+    y = np.arange(ny)[:, None]
+    dx = (x - cx + nx / 2) % nx - nx / 2
+    dy = (y - cy + ny / 2) % ny - ny / 2
+    inside = dx ** 2 + dy ** 2 <= R ** 2
+    # phi symmetric under the reflection too (a function of the distance only)
+    phi = np.where(inside, 1.0 - 0.5 * (dx ** 2 + dy ** 2) / R ** 2, -1.0)
+    psi = np.full((ny, nx), 0.1)
+    s = oracle.State(oracle.Params(nx, ny), phi, psi)
+    d = s.diagnostics(refx, refy)
+    got_x = (d["cm_x"] - cx + nx / 2) % nx - nx / 2
+    got_y = (d["cm_y"] - cy + ny / 2) % ny - ny / 2
+    assert abs(got_x) < 1e-12 and abs(got_y) < 1e-12
+    assert d["mass_pos"] == pytest.approx(phi[inside].sum(), rel=1e-14)
+    # the disk really straddles a seam in at least one direction
+    assert inside[:, 0].any() and inside[:, -1].any() or inside[0].any() and inside[-1].any()
