@@ -12,9 +12,23 @@ CACHE = os.environ.get("LBD_TUNE_CACHE",
                        os.path.join(os.path.dirname(os.path.abspath(__file__)), "_tune_cache.json"))
 
 
+def kernels_tag():
+    """Short hash of the CUDA sources the library is built from: a winner
+    measured on other kernels is not reused."""
+    import hashlib
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:12]
+
+
 def _key(device, nx, ny, precision, flags=0):
     walls = "|walls" if flags & 16 else ""
-    return "%s|%dx%d|%s%s" % (device, nx, ny, "fp64" if precision == 0 else "fp32", walls)
+    return "%s|%s|%dx%d|%s%s" % (kernels_tag(), device, nx, ny,
+                                 "fp64" if precision == 0 else "fp32", walls)
 
 
 def load_cache(path=CACHE):

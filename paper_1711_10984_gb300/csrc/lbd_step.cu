@@ -411,7 +411,7 @@ cudaError_t launch_tile(const StepArgs<T> &a, int mode, cudaStream_t s) {
 
 constexpr Tile kTiles[] = {{32, 8},   {32, 16},  {64, 8},    {32, 32},  {64, 16},
                            {118, 16}, {118, 32}, {118, 64}, {118, 128}, {246, 32},
-                           {246, 64}, {240, 32}, {240, 64}, {240, 128}};
+                           {246, 64}, {116, 32},  {116, 64}, {116, 128}};
 
 }  // namespace
 
@@ -430,7 +430,6 @@ Tile tile_at(int k) { return kTiles[k]; }
 
 template <typename T>
 size_t step_smem_bytes(Tile t) {
-    if (t.bx == 240) return pair_smem_bytes();
     if (t.bx >= 118) return stripe_smem_bytes<T>(t.bx + 10);
     if (t.bx == 32 && t.by == 8) return smem_for<T, 32, 8>();
     if (t.bx == 32 && t.by == 16) return smem_for<T, 32, 16>();
@@ -445,24 +444,27 @@ bool tile_valid(Tile t, bool fp32, int nx, long long plane) {
     for (const Tile &k : kTiles) known |= (k.bx == t.bx && k.by == t.by);
     if (!known) return false;
     if (t.bx >= 118 && 9.0 * (double)plane * (fp32 ? 4.0 : 8.0) >= 4294967295.0) return false;
-    if (t.bx == 240) return fp32 && pair_supported(nx);
+    if (t.bx == 116) return fp32 && vstripe_supported(nx, plane);
     return true;
 }
 
 template <typename T>
-cudaError_t launch_pair_if_float(const StepArgs<T> &, int, cudaStream_t) {
+cudaError_t launch_vstripe_if_float(const StepArgs<T> &, int, cudaStream_t) {
     return cudaErrorInvalidValue;
 }
 template <>
-cudaError_t launch_pair_if_float<float>(const StepArgs<float> &a, int seg, cudaStream_t s) {
-    return launch_pair(a, seg, s);
+cudaError_t launch_vstripe_if_float<float>(const StepArgs<float> &a, int seg, cudaStream_t s) {
+    return launch_vstripe(a, seg, s);
 }
 
 template <typename T>
 cudaError_t launch_step(const StepArgs<T> &a, int mode, Tile t, cudaStream_t s) {
+    if (t.bx == 116) {
+        if (mode == MODE_STEP) return launch_vstripe_if_float<T>(a, t.by, s);
+        t = Tile{32, 16};  // the fields evaluation always uses the tiled kernel
+    }
     if (t.bx >= 118) {
         if (mode == MODE_STEP) {
-            if (t.bx == 240) return launch_pair_if_float<T>(a, t.by, s);
             return launch_stripe<T>(a, t.bx + 10, t.by, s);
         }
         t = Tile{32, 16};  // the fields evaluation always uses the tiled kernel

@@ -67,7 +67,7 @@ def test_create_rejects_bad_grid(lib):
 def test_strerror_names_codes(lib):
     for code in (0, -1, -2, -3, -4, -5, -6):
         assert lib.lbd_strerror(code).startswith(b"LBD_")
-    assert (32, 8) in lbd.tiles() and (240, 64) in lbd.tiles()
+    assert (32, 8) in lbd.tiles() and (116, 64) in lbd.tiles() and (118, 64) in lbd.tiles()
 
 
 HEADER3 = os.path.join(ROOT, "include", "lbd3.h")
@@ -105,3 +105,15 @@ def test_3d_create_rejects_bad_input(lib, grid, bad):
     g = lbd3.lbd3_grid(*grid)
     h = ctypes.c_void_p()
     assert lib.lbd3_create(ctypes.byref(g), ctypes.byref(p), None, ctypes.byref(h)) == lbd.LBD_EINVAL
+
+
+@pytest.mark.parametrize("nx,ny,pitch", [((1 << 20) + 1, 8, (1 << 20) + 1), (0, 8, 8),
+                                         (16, 8, 15), (16, 8, (1 << 40) + 1),
+                                         (1 << 20, 1 << 20, 1 << 40)])
+def test_static_diagnostics_rejects_bad_shape(lib, nx, ny, pitch):
+    """lbd_diagnostics_static refuses lattices beyond its scratch limits and
+    pitches whose plane offsets would overflow, before any CUDA call."""
+    out = lbd.lbd_diag()
+    rc = lib.lbd_diagnostics_static(nx, ny, pitch, lbd.LBD_FP64, 1, 1, 1, 0.006, -0.05, 0.0, 0.0,
+                                    None, ctypes.byref(out))
+    assert rc == lbd.LBD_EINVAL

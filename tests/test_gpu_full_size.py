@@ -64,7 +64,7 @@ def test_fp64_full_size(work, tile):
     assert np.abs(g[1]).max() > 1e-8  # the flow has developed: every term is exercised
 
 
-@pytest.mark.parametrize("tile", ["bench", (118, 64), (246, 64)], ids=str)
+@pytest.mark.parametrize("tile", ["bench", (118, 64), (246, 64), (116, 64), (116, 32)], ids=str)
 def test_fp32_full_size(work, tile):
     g, _, r, _, used = advance_both(work, lbd.LBD_FP32, tile)
     for k in (1, 2, 3, 4):  # ux, uy, phi, psi

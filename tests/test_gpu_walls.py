@@ -146,8 +146,8 @@ def test_conservation_with_walls_on_gpu(prec):
 
 def test_walls_rejected_where_unsupported():
     sim = lbd.Sim(264, 64, precision=lbd.LBD_FP32, flags=lbd.LBD_WALLS)
-    with pytest.raises(lbd.LbdError) as e:  # the column-pair kernel has no walls
-        sim.set_tile(240, 64)
+    with pytest.raises(lbd.LbdError) as e:  # the 16-byte staged stripe kernel has no walls
+        sim.set_tile(116, 64)
     assert e.value.code == lbd.LBD_EINVAL
     sim.set_tile(32, 16)
     with pytest.raises(lbd.LbdError) as e:
