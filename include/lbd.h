@@ -50,7 +50,8 @@ extern "C" {
 #define LBD_ENONFINITE (-4)  /* a NaN or Inf in the fields                        */
 #define LBD_EUNSTABLE (-5)   /* B(psi) <= 0 or psi <= 0 somewhere (Section 4 notes
                                 that the droplet breaks up when B(c) <= 0)        */
-#define LBD_ETIMEOUT (-6)    /* a bounded device-side wait gave up               */
+#define LBD_ETIMEOUT (-6)    /* reserved: no kernel of the library waits on a
+                                flag or a peer, so no call returns it           */
 
 #define LBD_FP64 0           /* populations, phi, psi in double                   */
 #define LBD_FP32 1           /* populations stored as float deviations f_i - w_i,
@@ -132,8 +133,22 @@ int lbd_set_params(lbd_ctx *ctx, const lbd_params *params);
 int lbd_set_fields(lbd_ctx *ctx, const double *rho, const double *ux, const double *uy,
                    const double *phi, const double *psi);
 
-/* Advance nsteps >= 0 coupled time steps (asynchronous on the stream). */
+/* Advance nsteps >= 0 coupled time steps (asynchronous on the stream).  With
+ * run-time checks on (lbd_set_check), returns LBD_ENONFINITE or LBD_EUNSTABLE
+ * once a check has found the state broken (message in lbd_last_error); the
+ * verdict stays until the state is replaced (lbd_set_fields,
+ * lbd_set_populations, lbd_init_droplets), and steps are refused meanwhile. */
 int lbd_step(lbd_ctx *ctx, int64_t nsteps);
+
+/* Run-time checks (Section 4: the droplet breaks up when B(c) <= 0).  With
+ * every > 0, lbd_step queues the diagnostics reduction after each step whose
+ * count t is a multiple of every, on the context's stream and without a host
+ * synchronisation (up to 4 checks in flight; a fifth waits for the oldest).
+ * A check fails when a site holds a non-finite value (LBD_ENONFINITE) or when
+ * min B(psi) <= 0 or min psi <= 0 (LBD_EUNSTABLE).  Verdicts are read as the
+ * checks complete: at the next lbd_step and, waiting for all of them, at
+ * lbd_synchronize.  every = 0 (the default) turns the checks off. */
+int lbd_set_check(lbd_ctx *ctx, int64_t every);
 
 /* Copy the fields at the current time to host arrays of nx*ny doubles (any may
  * be NULL).  u is Eq. (11): (sum_i f_i e_i + F/2) / rho with the force of the
@@ -184,7 +199,12 @@ int lbd_set_populations(lbd_ctx *ctx, const double *f);
 
 /* Global diagnostics at the current time.  (ref_x, ref_y) in [0,nx) x [0,ny)
  * is the reference point for the minimum-image centre of mass (pass the
- * previous centre to follow a moving droplet).  Synchronises. */
+ * previous centre to follow a moving droplet).  *out is filled in every case;
+ * the return value is LBD_ENONFINITE if a site holds a non-finite value,
+ * LBD_EUNSTABLE if min B(psi) <= 0 or min psi <= 0, LBD_OK otherwise (these two
+ * verdicts are not sticky).  The FP64 form sums in double; the FP32 form
+ * accumulates each thread's sites in float with compensated (Neumaier)
+ * summation and combines the threads in double.  Synchronises. */
 int lbd_diagnostics(lbd_ctx *ctx, double ref_x, double ref_y, lbd_diag *out);
 
 /* One droplet of the current state (Section 4). */
@@ -227,11 +247,10 @@ int lbd_squirmer(lbd_ctx *ctx, int32_t n, const lbd_droplet *drops, double *b1, 
 
 /* Select the launch shape of the step: bx output columns x by output rows per
  * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
- * column per thread, segments of by rows); bx 240: FP32 column-pair kernel
- * with packed FP32x2 arithmetic (needs nx % 4 == 0 and nx >= 264).  With
- * LBD_WALLS the column-pair shapes are not valid.  Shapes not
- * compiled in, or not valid for the context's precision and lattice, return
- * LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
+ * column per thread, segments of by rows); bx 116: FP32 stripe-marching kernel
+ * with 16-byte population staging (periodic lattices with nx % 4 == 0; not
+ * valid with LBD_WALLS).  Shapes not compiled in, or not valid for the
+ * context's precision and lattice, return LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
  * kernels agree to rounding. */
 int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
 
@@ -281,17 +300,24 @@ int lbd_adjoint(lbd_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double ref_x, 
  * offset i*pitch*ny elements, site (x, y) at y*pitch + x (the order of the
  * sites within a plane does not matter for the totals); phi, psi with the
  * same site layout; element type double (LBD_FP64) or float (LBD_FP32).
- * Output: *out, a host struct.  B0, B1: B(psi) = B0 + B1 psi for min_B.
- * Limits: 1 <= nx, ny <= 2^20 and pitch >= nx, ref in [0,nx) x [0,ny);
- * anything else returns LBD_EINVAL before any work.  Works on the current
- * CUDA device and the given stream (NULL = legacy default); synchronises it.
+ * Output: *out, a host struct, filled in whenever the reduction ran; the
+ * return value is then LBD_ENONFINITE, LBD_EUNSTABLE or LBD_OK as for
+ * lbd_diagnostics.  B0, B1: B(psi) = B0 + B1 psi for min_B.
+ * Limits: 1 <= nx, ny <= 2^20, nx <= pitch <= 2^40 with 9 pitch ny < 2^52,
+ * ref in [0,nx) x [0,ny), and g, phi, psi device memory of the current device
+ * (or managed memory); anything else (a host pointer, another GPU's buffer)
+ * returns LBD_EINVAL before any work.  Works on the current CUDA device and
+ * the given stream (NULL = legacy default); synchronises it.
  *
- * The first call on each device looks up the device address of the scratch
- * array (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (different streams or host threads) race on it and must
- * be serialised by the caller.  Every scratch slot is overwritten on each call,
- * so nothing needs clearing. */
+ * Every call looks up the device address of the scratch array
+ * (cudaGetSymbolAddress with the caller's device current; the lookup
+ * allocates nothing), so the address stays right after cudaDeviceReset and
+ * under a non-primary context.  The first call on a device may load the
+ * library's device code there: make that first call before any stream
+ * capture.  All calls share the one array: calls that overlap on the GPU
+ * (different streams or host threads) race on it and must be serialised by
+ * the caller.  Every scratch slot is overwritten on each call, so nothing
+ * needs clearing. */
 int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precision,
                            const void *g, const void *phi, const void *psi, double B0, double B1,
                            double ref_x, double ref_y, void *stream, lbd_diag *out);
@@ -336,8 +362,26 @@ int lbd_get_time(const lbd_ctx *ctx, int64_t *t);
 /* Set the step count t (used by the activity schedule). */
 int lbd_set_time(lbd_ctx *ctx, int64_t t);
 
-/* Block until the context's queued work is done; reports any CUDA error. */
+/* Block until the context's queued work is done; reports any CUDA error, then
+ * the verdict of the run-time checks (LBD_ENONFINITE, LBD_EUNSTABLE). */
 int lbd_synchronize(lbd_ctx *ctx);
+
+/* Measurement support (the paper has no counterpart): the FP64 FMA rate of the
+ * current device in flop/s, timed with CUDA events over one launch of
+ * iters rounds of 8 independent FMA chains in each of 256 threads x 8 blocks
+ * per SM (2 flops per FMA), after an untimed warm-up launch; the FP64 form of
+ * the coupled step is bound by this rate.  Allocates and frees a small output
+ * buffer; runs on a stream of its own and synchronises it.  LBD_EINVAL for
+ * iters < 1 or a NULL output. */
+int lbd_fp64_peak(int32_t iters, double *flops_per_s);
+
+/* Test hook: the nth device or pinned-host allocation the library makes from
+ * now on (counted over all contexts and threads) fails as if the memory were
+ * exhausted; nth = 0 clears the hook.  The call that meets the failure returns
+ * LBD_ENOMEM and leaves its context as it was (lbd_create returns no context).
+ * LBD_EINVAL for nth < 0.  The paper has no counterpart: it exists so that the
+ * out-of-memory paths can be tested without exhausting a GPU. */
+int lbd_debug_fail_alloc(int32_t nth);
 
 /* Release all device memory of ctx (NULL is allowed). */
 void lbd_destroy(lbd_ctx *ctx);

@@ -22,6 +22,11 @@
 
 #include "lbd3.h"
 
+namespace lbd {
+// device and pinned-host allocation through the library-wide failure hook (lbd_api.cu)
+cudaError_t dev_malloc(void **p, size_t bytes);
+}  // namespace lbd
+
 namespace {
 
 constexpr int Q = 19;
@@ -896,7 +901,7 @@ cudaError_t ring_limits() {
 int ensure_staging3(lbd3_ctx *c) {
     if (c->staging) return LBD_OK;
     // six fields of doubles, then the first-invalid-site word of an upload
-    if (cudaMalloc(&c->staging, sizeof(double) * (6 * c->N + 1)) != cudaSuccess) {
+    if (lbd::dev_malloc((void **)&c->staging, sizeof(double) * (6 * c->N + 1)) != cudaSuccess) {
         cudaGetLastError();
         c->staging = nullptr;
         return fail3(c, LBD_ENOMEM, "staging allocation failed");
@@ -965,13 +970,13 @@ int lbd3_create(const lbd3_grid *grid, const lbd3_params *params, void *stream, 
     const size_t words = (size_t)((grid->nx + 31) / 32) * grid->ny * grid->nz;
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
-        ok &= cudaMalloc(&c->g[k], (size_t)Q * fb) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->phi[k], fb) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->psi[k], fb) == cudaSuccess;
+        ok &= lbd::dev_malloc((void **)&c->g[k], (size_t)Q * fb) == cudaSuccess;
+        ok &= ok && lbd::dev_malloc((void **)&c->phi[k], fb) == cudaSuccess;
+        ok &= ok && lbd::dev_malloc((void **)&c->psi[k], fb) == cudaSuccess;
     }
-    ok &= ok && cudaMalloc(&c->work, 9 * fb) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->theta, 4 * words) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->red, sizeof(double) * NRED3 * (RED3_BLOCKS + 1)) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->work, 9 * fb) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->theta, 4 * words) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->red, sizeof(double) * NRED3 * (RED3_BLOCKS + 1)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbd3_destroy(c);
@@ -1091,7 +1096,7 @@ int lbd3_get_populations(lbd3_ctx *c, double *f) {
     if (!c || !f) return LBD_EINVAL;
     if (c->sticky) return c->sticky;
     CK3(c, cudaSetDevice(c->dev));
-    if (!c->pop_staging && cudaMalloc(&c->pop_staging, sizeof(double) * Q * c->N) != cudaSuccess) {
+    if (!c->pop_staging && lbd::dev_malloc((void **)&c->pop_staging, sizeof(double) * Q * c->N) != cudaSuccess) {
         cudaGetLastError();
         c->pop_staging = nullptr;
         return fail3(c, LBD_ENOMEM, "population staging allocation failed");

@@ -499,7 +499,7 @@ int adjoint_run(const AdjointJob<T> &job) {
     std::vector<void *> allocs;
     auto dalloc = [&](size_t bytes) -> void * {
         void *ptr = nullptr;
-        if (cudaMalloc(&ptr, bytes ? bytes : 16) != cudaSuccess) {
+        if (lbd::dev_malloc((void **)&ptr, bytes ? bytes : 16) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }

@@ -4,8 +4,8 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <algorithm>
+#include <atomic>
 #include <new>
 #include <string>
 #include <vector>
@@ -44,6 +44,21 @@ struct lbd_ctx {
     Tile tile{118, 64};
     int sticky = 0;
     std::string msg;
+    // Run-time checks (lbd_set_check): every `check_every` steps lbd_step queues
+    // the diagnostics reduction into one of NCHECK result slots (device result,
+    // pinned host copy, completion event) without a host synchronisation; the
+    // verdicts are read as the slots complete.  `flagged` holds the first
+    // failure found (LBD_ENONFINITE or LBD_EUNSTABLE) until the state is reset.
+    static constexpr int NCHECK = 4;
+    int64_t check_every = 0;
+    struct CheckSlot {
+        double *d = nullptr, *h = nullptr;
+        cudaEvent_t ev = nullptr;
+        int64_t t = 0;
+        bool pending = false;
+    } chk[NCHECK];
+    int chk_next = 0;
+    int flagged = 0;
 };
 
 
@@ -359,6 +374,116 @@ __global__ void reduce_partial(int nx, int ny, long long pitch, long long plane,
         for (int k = 0; k < NRED; ++k) partial[k * gridDim.x + blockIdx.x] = v[k];
 }
 
+// Compensated FP32 running sum (Neumaier): s + c carries the sum of the added
+// terms to within about one FP32 rounding of the largest partial sum.
+struct Neu {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// The FP32 form of reduce_partial, with the same slots and the same results up
+// to rounding: each thread walks 4-site row chunks and accumulates the six sums
+// in FP32 with Neumaier compensation (the per-thread totals, over a few dozen
+// sites, are then combined in FP64 per block); min and max psi are kept in
+// FP32 and turned into min B = B0 + B1 psi (monotone in psi) once per thread,
+// in FP64; the minimum-image displacements are integers (x - floor(ref)),
+// wrapped with integer thresholds that reproduce the FP64 test
+// d = x - ref >= nx/2 (d -= nx), d < -nx/2 (d += nx), and the fractional part
+// of ref is taken off in FP64 after the block sums (slots 3-4 then hold the
+// same quantity as in FP64).  A site whose eleven values do not add up to a
+// finite number is re-examined value by value, so that the count is that of
+// sites holding a non-finite value.
+__global__ void reduce_partial_f32(int nx, int ny, long long pitch, long long plane,
+                                   const float *g, const float *phi, const float *psi, double B0,
+                                   double B1, double refx, double refy, int vec, double *partial) {
+    __shared__ double smem[NRED * 32];
+    const double fx = floor(refx), fy = floor(refy), frx = refx - fx, fry = refy - fy;
+    const int ix = (int)fx, iy = (int)fy;
+    // integer wrap thresholds: d = k - frac wraps down when k >= hi, up when k < lo
+    const int hix = (int)ceil(0.5 * nx + frx), lox = (int)ceil(frx - 0.5 * nx);
+    const int hiy = (int)ceil(0.5 * ny + fry), loy = (int)ceil(fry - 0.5 * ny);
+    Neu sg, sp, sc, sdx, sdy, spp;
+    float pmin = INFINITY, pmax = -INFINITY;
+    double bad = 0.0;
+    const int nq = (nx + 3) >> 2;
+    const long long nchunks = (long long)nq * ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nchunks;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(q / nq), x0 = (int)(q - (long long)y * nq) * 4;
+        int ky = y - iy;
+        if (ky >= hiy) ky -= ny; else if (ky < loy) ky += ny;
+        const long long o = (long long)y * pitch + x0;
+        const int cnt = nx - x0 < 4 ? nx - x0 : 4;
+        float gv[4] = {0.f, 0.f, 0.f, 0.f}, pv[4] = {0.f, 0.f, 0.f, 0.f}, cv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (vec && cnt == 4) {  // 16-byte loads: rows and planes 16-byte aligned
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float4 v = *reinterpret_cast<const float4 *>(g + i * plane + o);
+                gv[0] += v.x; gv[1] += v.y; gv[2] += v.z; gv[3] += v.w;
+            }
+            const float4 a = *reinterpret_cast<const float4 *>(phi + o);
+            const float4 b = *reinterpret_cast<const float4 *>(psi + o);
+            pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+            cv[0] = b.x; cv[1] = b.y; cv[2] = b.z; cv[3] = b.w;
+        } else {
+            for (int k = 0; k < cnt; ++k) {
+                for (int i = 0; i < 9; ++i) gv[k] += g[i * plane + o + k];
+                pv[k] = phi[o + k];
+                cv[k] = psi[o + k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k >= cnt) break;
+            const float ph = pv[k], c = cv[k];
+            if (!isfinite(gv[k] + ph + c)) {
+                // slow path: which of the eleven values is not finite
+                bool nf = !isfinite(ph) || !isfinite(c);
+                for (int i = 0; i < 9; ++i) nf |= !isfinite(g[i * plane + o + k]);
+                bad += nf ? 1.0 : 0.0;
+            }
+            sg.add(gv[k]);
+            sp.add(ph);
+            sc.add(c);
+            if (ph >= 0.f) {
+                int kx = x0 + k - ix;
+                if (kx >= hix) kx -= nx; else if (kx < lox) kx += nx;
+                sdx.add(ph * (float)kx);
+                sdy.add(ph * (float)ky);
+                spp.add(ph);
+            }
+            pmin = fminf(pmin, c);
+            pmax = fmaxf(pmax, c);
+        }
+    }
+    double v[NRED];
+    v[0] = sg.value();
+    v[1] = sp.value();
+    v[2] = sc.value();
+    v[3] = sdx.value();
+    v[4] = sdy.value();
+    v[5] = spp.value();
+    // B0 + B1 psi is monotone in psi: its minimum over the sites sits at the
+    // extreme psi (no site: +inf, as in the FP64 form)
+    const float pext = B1 < 0.0 ? pmax : pmin;
+    v[6] = isinf(pext) ? INFINITY : B0 + B1 * (double)pext;
+    v[7] = pmin;
+    v[8] = bad;
+    block_reduce(v, smem);
+    if (threadIdx.x == 0) {
+        // slots 3-4 relative to ref: subtract the fractional part of ref times
+        // the mass over phi >= 0
+        v[3] -= frx * v[5];
+        v[4] -= fry * v[5];
+        for (int k = 0; k < NRED; ++k) partial[k * gridDim.x + blockIdx.x] = v[k];
+    }
+}
+
 __global__ void reduce_final(int nb, const double *partial, double *out) {
     __shared__ double smem[NRED * 32];
     double v[NRED] = {0, 0, 0, 0, 0, 0, INFINITY, INFINITY, 0};
@@ -372,6 +497,26 @@ __global__ void reduce_final(int nb, const double *partial, double *out) {
         for (int k = 0; k < NRED; ++k) out[k] = v[k];
 }
 
+// The partial reduction of the state in (g, phi, psi) on stream st: the FP32
+// form takes the compensated FP32 kernel (16-byte loads where rows and planes
+// are 16-byte aligned), the FP64 form the FP64 kernel.
+cudaError_t launch_reduce_partial(int prec, int nx, int ny, long long pitch, long long plane,
+                                  const void *g, const void *phi, const void *psi, double B0,
+                                  double B1, double refx, double refy, double *partial,
+                                  cudaStream_t st) {
+    if (prec == LBD_FP64) {
+        reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, st>>>(
+            nx, ny, pitch, plane, (const double *)g, (const double *)phi, (const double *)psi, B0,
+            B1, refx, refy, partial);
+    } else {
+        const int vec = pitch % 4 == 0 && ((uintptr_t)g | (uintptr_t)phi | (uintptr_t)psi) % 16 == 0;
+        reduce_partial_f32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(
+            nx, ny, pitch, plane, (const float *)g, (const float *)phi, (const float *)psi, B0, B1,
+            refx, refy, vec, partial);
+    }
+    return cudaGetLastError();
+}
+
 // -------------------------------------------- scratch of lbd_diagnostics_static
 // Partial sums of the RED_BLOCKS reduction blocks plus the NRED results:
 // 5481 doubles = 43,848 bytes.  Every GPU that loads this library holds the
@@ -381,27 +526,49 @@ __global__ void reduce_final(int nb, const double *partial, double *out) {
 constexpr int kStaticScratchDoubles = NRED * RED_BLOCKS + NRED;
 static __device__ __align__(256) double g_diag_static_scratch[kStaticScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-double *g_static_ptr[kMaxDevices] = {};
-
-// Device address of the static scratch on the current device.  Host code only
-// sees a host-side stand-in under the array's name, so the address is looked up
-// once per device with that device current and cached.
+// Device address of the static scratch on the current device and context.  In
+// host code the array's name is only a host-side stand-in, so the address is
+// looked up with cudaGetSymbolAddress on every call: the lookup allocates
+// nothing and does not synchronise, and it cannot go stale (a cached address
+// would be wrong after cudaDeviceReset, which reloads the module in a new
+// primary context, or under a caller's own non-primary context).  The first
+// lookup on a device loads the library's device code there if lazy module
+// loading has not done so yet.
 cudaError_t static_scratch(double **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_diag_static_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_diag_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_static_ptr[dev];
+    *out = static_cast<double *>(p);
     return cudaSuccess;
+}
+
+// Whether p is memory that kernels on the current device can read: device
+// memory of that device, or managed memory.
+bool on_current_device(const void *p) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// ------------------------------------------------ allocation failure hook
+// Allocations still to go before the one that fails (0: none fails).
+std::atomic<int> g_fail_countdown{0};
+
+bool fail_this_allocation() {
+    int n = g_fail_countdown.load();
+    while (n > 0) {
+        if (g_fail_countdown.compare_exchange_weak(n, n - 1)) return n == 1;
+    }
+    return false;
 }
 
 // ---------------------------------------------------------------- helpers
@@ -473,6 +640,77 @@ StepArgs<T> make_args(const lbd_ctx *c, int cur = -1) {
 }
 
 
+// The verdict of a completed check: the first failure is kept in c->flagged.
+void judge_check(lbd_ctx *c, const double *r, int64_t t) {
+    if (c->flagged) return;
+    if (r[8] > 0) {
+        c->flagged = LBD_ENONFINITE;
+        c->msg = "run-time check: " + std::to_string((long long)r[8]) +
+                 " sites hold a non-finite value at step " + std::to_string((long long)t);
+    } else if (!(r[6] > 0) || !(r[7] > 0)) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "run-time check: min B(psi) = %g, min psi = %g at step %lld",
+                 r[6], r[7], (long long)t);
+        c->flagged = LBD_EUNSTABLE;
+        c->msg = buf;
+    }
+}
+
+// Read the verdicts of the completed checks, in the order they were queued;
+// with wait, wait for all of them.  Returns an LBD code for a CUDA failure.
+int poll_checks(lbd_ctx *c, bool wait) {
+    for (int k = 0; k < lbd_ctx::NCHECK; ++k) {
+        lbd_ctx::CheckSlot &s = c->chk[(c->chk_next + k) % lbd_ctx::NCHECK];
+        if (!s.pending) continue;
+        cudaError_t e = wait ? cudaEventSynchronize(s.ev) : cudaEventQuery(s.ev);
+        if (e == cudaErrorNotReady) break;  // later slots completed no earlier
+        if (e != cudaSuccess) return fail(c, LBD_ECUDA, "check: %s", cudaGetErrorString(e));
+        s.pending = false;
+        judge_check(c, s.h, s.t);
+    }
+    return LBD_OK;
+}
+
+// Queue one check of the current state (after the step that reached c->t).
+int queue_check(lbd_ctx *c) {
+    lbd::NvtxRange range("lbd check reduction");
+    lbd_ctx::CheckSlot &s = c->chk[c->chk_next];
+    if (!s.d) {
+        if (lbd::dev_malloc((void **)&s.d, NRED * sizeof(double)) != cudaSuccess ||
+            lbd::host_malloc((void **)&s.h, NRED * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s.d);
+            s.d = nullptr;
+            return fail(c, LBD_ENOMEM, "check slot allocation failed");
+        }
+        CK(c, cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+    }
+    if (s.pending) {  // every slot in flight: wait for the oldest
+        CK(c, cudaEventSynchronize(s.ev));
+        s.pending = false;
+        judge_check(c, s.h, s.t);
+    }
+    const lbd_params &p = c->params;
+    CK(c, launch_reduce_partial(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane,
+                                c->g[c->cur], c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, 0.0,
+                                0.0, c->red_partial, c->stream));
+    reduce_final<<<1, RED_THREADS, 0, c->stream>>>(RED_BLOCKS, c->red_partial, s.d);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(s.h, s.d, NRED * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaEventRecord(s.ev, c->stream));
+    s.t = c->t;
+    s.pending = true;
+    c->chk_next = (c->chk_next + 1) % lbd_ctx::NCHECK;
+    return LBD_OK;
+}
+
+// Forget queued checks and a flagged failure (the state was replaced).
+int reset_checks(lbd_ctx *c) {
+    int rc = poll_checks(c, true);
+    c->flagged = 0;
+    return rc;
+}
+
 template <typename T>
 int run_steps(lbd_ctx *c, int64_t n) {
     for (int64_t k = 0; k < n; ++k) {
@@ -484,6 +722,10 @@ int run_steps(lbd_ctx *c, int64_t n) {
         CK(c, lbd::launch_step<T>(a, lbd::MODE_STEP, c->tile, c->stream));
         c->cur = 1 - c->cur;
         c->t += 1;
+        if (c->check_every > 0 && c->t % c->check_every == 0) {
+            const int rc = queue_check(c);
+            if (rc != LBD_OK) return rc;
+        }
     }
     return LBD_OK;
 }
@@ -509,13 +751,14 @@ int update_theta(lbd_ctx *c) {
 // its precision and lattice, and a stripe shape when the lattice has walls.
 bool tile_ok(const lbd_ctx *c, Tile t) {
     if (!lbd::tile_valid(t, c->params.precision == LBD_FP32, c->grid.nx, c->plane)) return false;
-    return !(c->params.flags & LBD_WALLS) || t.bx != 240;  // no walls in the column-pair kernel
+    // no walls in the 16-byte staged stripe kernel
+    return !(c->params.flags & LBD_WALLS) || t.bx != 116;
 }
 
 int ensure_staging(lbd_ctx *c) {
     if (c->staging) return LBD_OK;
     // five fields of doubles, then the first-invalid-site word of an upload
-    if (cudaMalloc(&c->staging, (5 * c->N + 1) * sizeof(double)) != cudaSuccess) {
+    if (lbd::dev_malloc((void **)&c->staging, (5 * c->N + 1) * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->staging = nullptr;
         return fail(c, LBD_ENOMEM, "staging allocation of %zu bytes failed",
@@ -530,6 +773,23 @@ int grid_for(size_t n) {
 }
 
 }  // namespace
+
+namespace lbd {
+cudaError_t dev_malloc(void **p, size_t bytes) {
+    if (fail_this_allocation()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+cudaError_t host_malloc(void **p, size_t bytes) {
+    if (fail_this_allocation()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
+}
+}  // namespace lbd
 
 namespace {
 
@@ -587,7 +847,7 @@ int batch_build(lbd_batch *b) {
     const size_t bytes = sizeof(StepArgs<T>) * (size_t)b->n;
     std::vector<StepArgs<T>> host(b->n);
     for (int p = 0; p < 2; ++p) {
-        if (!b->args_dev[p]) BCK(b, cudaMalloc(&b->args_dev[p], bytes));
+        if (!b->args_dev[p]) BCK(b, lbd::dev_malloc((void **)&b->args_dev[p], bytes));
         for (int k = 0; k < b->n; ++k) host[k] = make_args<T>(b->ctx[k], p);
         BCK(b, cudaMemcpyAsync(b->args_dev[p], host.data(), bytes, cudaMemcpyHostToDevice, b->stream));
         BCK(b, cudaStreamSynchronize(b->stream));
@@ -609,7 +869,7 @@ int batch_build(lbd_batch *b) {
     });
     if (b->items_dev) cudaFree(b->items_dev);
     b->items_dev = nullptr;
-    BCK(b, cudaMalloc(&b->items_dev, sizeof(lbd::BatchItem) * items.size()));
+    BCK(b, lbd::dev_malloc((void **)&b->items_dev, sizeof(lbd::BatchItem) * items.size()));
     BCK(b, cudaMemcpyAsync(b->items_dev, items.data(), sizeof(lbd::BatchItem) * items.size(),
                            cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
@@ -716,6 +976,11 @@ void lbd_destroy(lbd_ctx *c) {
     cudaFree(c->red_out);
     cudaFree(c->theta);
     cudaFreeHost(c->h_red);
+    for (auto &k : c->chk) {
+        cudaFree(k.d);
+        cudaFreeHost(k.h);
+        if (k.ev) cudaEventDestroy(k.ev);
+    }
     cudaSetDevice(prev);
     delete c;
 }
@@ -748,14 +1013,14 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
     const size_t fbytes = (size_t)c->plane * c->esz;
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
-        ok &= cudaMalloc(&c->g[k], 9 * fbytes) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->phi[k], fbytes) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->psi[k], fbytes) == cudaSuccess;
+        ok &= lbd::dev_malloc((void **)&c->g[k], 9 * fbytes) == cudaSuccess;
+        ok &= ok && lbd::dev_malloc((void **)&c->phi[k], fbytes) == cudaSuccess;
+        ok &= ok && lbd::dev_malloc((void **)&c->psi[k], fbytes) == cudaSuccess;
     }
-    ok &= ok && cudaMalloc(&c->red_partial, NRED * RED_BLOCKS * sizeof(double)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->red_out, NRED * sizeof(double)) == cudaSuccess;
-    ok &= ok && cudaMallocHost(&c->h_red, NRED * sizeof(double)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->theta, (size_t)((grid->nx + 31) / 32) * grid->ny * 4) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->red_partial, NRED * RED_BLOCKS * sizeof(double)) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->red_out, NRED * sizeof(double)) == cudaSuccess;
+    ok &= ok && lbd::host_malloc((void **)&c->h_red, NRED * sizeof(double)) == cudaSuccess;
+    ok &= ok && lbd::dev_malloc((void **)&c->theta, (size_t)((grid->nx + 31) / 32) * grid->ny * 4) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         lbd_destroy(c);
@@ -774,14 +1039,18 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
     // Default launch shape: the stripe kernel (fastest measured on large
     // lattices) unless it would leave most SMs idle, then the tiled kernel with
     // its smallest tiles; lbd_autotune refines the choice.
-    c->tile = Tile{118, 64};
+    // FP32 on periodic lattices of width 4k: the stripe kernel with 16-byte
+    // population staging; otherwise the plain stripe kernel.
+    c->tile = Tile{116, 64};
+    if (!tile_ok(c, c->tile)) c->tile = Tile{118, 64};
     {
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess) {
             cudaGetLastError();
             sms = 1;
         }
-        const long long stripe_ctas = (long long)((grid->nx + 117) / 118) * ((grid->ny + 63) / 64);
+        const int w = c->tile.bx;
+        const long long stripe_ctas = (long long)((grid->nx + w - 1) / w) * ((grid->ny + 63) / 64);
         if (stripe_ctas < 2LL * sms || !tile_ok(c, c->tile)) c->tile = Tile{32, 8};
     }
     if (update_theta(c) != LBD_OK) {
@@ -800,7 +1069,7 @@ int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
         return fail(c, LBD_EINVAL, "precision cannot change after creation");
     const lbd_params keep = c->params;
     c->params = *p;
-    if ((p->flags & LBD_WALLS) && !tile_ok(c, c->tile)) {  // the column-pair shape
+    if ((p->flags & LBD_WALLS) && !tile_ok(c, c->tile)) {  // a shape without walls
         c->tile = Tile{118, 64};
         if (!tile_ok(c, c->tile)) c->tile = Tile{32, 8};
         if (!tile_ok(c, c->tile)) {
@@ -858,6 +1127,10 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     unsigned long long first = 0;
     CK(c, cudaMemcpyAsync(&first, bad, sizeof first, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (first == ~0ull) {  // the state was replaced: earlier check verdicts no longer apply
+        rc = reset_checks(c);
+        if (rc != LBD_OK) return rc;
+    }
     if (first != ~0ull) {
         const size_t site = (size_t)(first >> 2);
         switch ((int)(first & 3ull)) {
@@ -872,9 +1145,23 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
 int lbd_step(lbd_ctx *c, int64_t n) {
     if (!c || n < 0) return LBD_EINVAL;
     if (c->sticky) return c->sticky;
-    if (n == 0) return LBD_OK;
     CK(c, cudaSetDevice(c->dev));
-    return c->params.precision == LBD_FP64 ? run_steps<double>(c, n) : run_steps<float>(c, n);
+    int rc = poll_checks(c, false);
+    if (rc != LBD_OK) return rc;
+    if (c->flagged) return c->flagged;
+    if (n == 0) return LBD_OK;
+    lbd::NvtxRange range("lbd_step");
+    rc = c->params.precision == LBD_FP64 ? run_steps<double>(c, n) : run_steps<float>(c, n);
+    if (rc != LBD_OK) return rc;
+    rc = poll_checks(c, false);
+    if (rc != LBD_OK) return rc;
+    return c->flagged;
+}
+
+int lbd_set_check(lbd_ctx *c, int64_t every) {
+    if (!c || every < 0) return LBD_EINVAL;
+    c->check_every = every;
+    return LBD_OK;
 }
 
 }  // extern "C"
@@ -908,9 +1195,9 @@ int droplet_sums(lbd_ctx *c, int n, const double *ref, int stride, bool squirm) 
     if (rc != LBD_OK) return rc;
     const size_t m = (size_t)LBD_MAX_DROPLETS * lbd::DROP_SUMS;
     if (!c->drop_dev) {
-        if (cudaMalloc(&c->drop_dev, sizeof(double) * (m * (RED_BLOCKS + 1) + 4 * LBD_MAX_DROPLETS)) !=
+        if (lbd::dev_malloc((void **)&c->drop_dev, sizeof(double) * (m * (RED_BLOCKS + 1) + 4 * LBD_MAX_DROPLETS)) !=
                 cudaSuccess ||
-            cudaMallocHost(&c->h_drop, sizeof(double) * (m + 4 * LBD_MAX_DROPLETS)) != cudaSuccess) {
+            lbd::host_malloc((void **)&c->h_drop, sizeof(double) * (m + 4 * LBD_MAX_DROPLETS)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(c->drop_dev);
             c->drop_dev = nullptr;
@@ -993,7 +1280,7 @@ int lbd_init_droplets(lbd_ctx *c, int32_t n, const lbd_droplet_init *d, double p
             (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
-    return LBD_OK;
+    return reset_checks(c);
 }
 
 int lbd_get_fields_device(lbd_ctx *c, void *rho, void *ux, void *uy, void *phi, void *psi) {
@@ -1025,7 +1312,7 @@ int lbd_set_populations(lbd_ctx *c, const double *f) {
         if (!std::isfinite(f[k])) return fail(c, LBD_ENONFINITE, "non-finite population %zu", k);
     CK(c, cudaSetDevice(c->dev));
     if (!c->pop_staging) {
-        if (cudaMalloc(&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
+        if (lbd::dev_malloc((void **)&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             c->pop_staging = nullptr;
             return fail(c, LBD_ENOMEM, "population staging allocation failed");
@@ -1043,7 +1330,7 @@ int lbd_set_populations(lbd_ctx *c, const double *f) {
             c->grid.nx, c->grid.ny, c->pitch, c->plane, walls, c->pop_staging, (float *)c->g[c->cur]);
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
-    return LBD_OK;
+    return reset_checks(c);
 }
 
 int lbd_get_populations(lbd_ctx *c, double *f) {
@@ -1051,7 +1338,7 @@ int lbd_get_populations(lbd_ctx *c, double *f) {
     if (c->sticky) return c->sticky;
     CK(c, cudaSetDevice(c->dev));
     if (!c->pop_staging) {
-        if (cudaMalloc(&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
+        if (lbd::dev_malloc((void **)&c->pop_staging, 9 * c->N * sizeof(double)) != cudaSuccess) {
             cudaGetLastError();
             c->pop_staging = nullptr;
             return fail(c, LBD_ENOMEM, "population staging allocation failed");
@@ -1078,19 +1365,12 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
     if (c->sticky) return c->sticky;
     if (!(refx >= 0 && refx < c->grid.nx && refy >= 0 && refy < c->grid.ny))
         return fail(c, LBD_EINVAL, "reference point outside the lattice");
+    lbd::NvtxRange range("lbd_diagnostics");
     CK(c, cudaSetDevice(c->dev));
     const lbd_params &p = c->params;
-    if (p.precision == LBD_FP64)
-        reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
-            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const double *)c->g[c->cur],
-            (const double *)c->phi[c->cur], (const double *)c->psi[c->cur], p.B0, p.B1, refx, refy,
-            c->red_partial);
-    else
-        reduce_partial<float><<<RED_BLOCKS, RED_THREADS, 0, c->stream>>>(
-            c->grid.nx, c->grid.ny, c->pitch, c->plane, (const float *)c->g[c->cur],
-            (const float *)c->phi[c->cur], (const float *)c->psi[c->cur], p.B0, p.B1, refx, refy,
-            c->red_partial);
-    CK(c, cudaGetLastError());
+    CK(c, launch_reduce_partial(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane,
+                                c->g[c->cur], c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, refx,
+                                refy, c->red_partial, c->stream));
     reduce_final<<<1, RED_THREADS, 0, c->stream>>>(RED_BLOCKS, c->red_partial, c->red_out);
     CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(c->h_red, c->red_out, NRED * sizeof(double), cudaMemcpyDeviceToHost,
@@ -1106,6 +1386,11 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
     out->min_B = r[6];
     out->min_psi = r[7];
     out->nonfinite = (int64_t)r[8];
+    if (out->nonfinite > 0)
+        return fail(c, LBD_ENONFINITE, "%lld sites hold a non-finite value",
+                    (long long)out->nonfinite);
+    if (!(out->min_B > 0) || !(out->min_psi > 0))
+        return fail(c, LBD_EUNSTABLE, "min B(psi) = %g, min psi = %g", out->min_B, out->min_psi);
     return LBD_OK;
 }
 
@@ -1252,8 +1537,13 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
                            double ref_x, double ref_y, void *stream, lbd_diag *out) {
     if (!g || !phi || !psi || !out) return LBD_EINVAL;
     if (nx < 1 || ny < 1 || nx > (1 << 20) || ny > (1 << 20) || pitch < nx) return LBD_EINVAL;
+    // the nine planes span 9 * pitch * ny elements: keep every index in range
+    if (pitch > (int64_t(1) << 40) || 9.0 * (double)pitch * (double)ny >= 0x1p52) return LBD_EINVAL;
     if (precision != LBD_FP64 && precision != LBD_FP32) return LBD_EINVAL;
     if (!(ref_x >= 0 && ref_x < nx && ref_y >= 0 && ref_y < ny)) return LBD_EINVAL;
+    // a host pointer or another GPU's buffer would fault the kernel: refuse it
+    if (!on_current_device(g) || !on_current_device(phi) || !on_current_device(psi))
+        return LBD_EINVAL;
     double *scratch = nullptr;
     if (static_scratch(&scratch) != cudaSuccess) {
         cudaGetLastError();
@@ -1262,15 +1552,9 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
     double *partial = scratch, *res = scratch + NRED * RED_BLOCKS;
     cudaStream_t s = (cudaStream_t)stream;
     const long long plane = (long long)pitch * ny;
-    if (precision == LBD_FP64)
-        reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
-            nx, ny, pitch, plane, (const double *)g, (const double *)phi, (const double *)psi, B0,
-            B1, ref_x, ref_y, partial);
-    else
-        reduce_partial<float><<<RED_BLOCKS, RED_THREADS, 0, s>>>(
-            nx, ny, pitch, plane, (const float *)g, (const float *)phi, (const float *)psi, B0, B1,
-            ref_x, ref_y, partial);
-    if (cudaGetLastError() != cudaSuccess) return LBD_ECUDA;
+    if (launch_reduce_partial(precision, nx, ny, pitch, plane, g, phi, psi, B0, B1, ref_x, ref_y,
+                              partial, s) != cudaSuccess)
+        return LBD_ECUDA;
     reduce_final<<<1, RED_THREADS, 0, s>>>(RED_BLOCKS, partial, res);
     if (cudaGetLastError() != cudaSuccess) return LBD_ECUDA;
     double r[NRED];
@@ -1288,11 +1572,14 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
     out->min_B = r[6];
     out->min_psi = r[7];
     out->nonfinite = (int64_t)r[8];
+    if (out->nonfinite > 0) return LBD_ENONFINITE;
+    if (!(out->min_B > 0) || !(out->min_psi > 0)) return LBD_EUNSTABLE;
     return LBD_OK;
 }
 
 int lbd_adjoint(lbd_ctx *c, int64_t nsteps, int32_t ckpt_every, double ref_x, double *loss,
                 double *dL_dpsi0, double *dL_dB1) {
+    lbd::NvtxRange range("lbd_adjoint");
     if (!c || !loss || !dL_dB1) return LBD_EINVAL;
     if (c->sticky) return c->sticky;
     if (nsteps < 1 || ckpt_every < 1) return fail(c, LBD_EINVAL, "nsteps and ckpt_every must be >= 1");
@@ -1355,7 +1642,7 @@ int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params,
             lbd_batch_destroy(b);
             return LBD_EINVAL;
         }
-    if (cudaMalloc(&b->t_dev, sizeof(long long)) != cudaSuccess) {
+    if (lbd::dev_malloc((void **)&b->t_dev, sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         lbd_batch_destroy(b);
         return LBD_ENOMEM;
@@ -1487,6 +1774,14 @@ int lbd_synchronize(lbd_ctx *c) {
     CK(c, cudaSetDevice(c->dev));
     CK(c, cudaStreamSynchronize(c->stream));
     CK(c, cudaGetLastError());
+    const int rc = poll_checks(c, true);
+    if (rc != LBD_OK) return rc;
+    return c->flagged;
+}
+
+int lbd_debug_fail_alloc(int32_t nth) {
+    if (nth < 0) return LBD_EINVAL;
+    g_fail_countdown.store(nth);
     return LBD_OK;
 }
 

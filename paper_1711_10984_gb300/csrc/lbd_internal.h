@@ -6,10 +6,20 @@
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lbd.h"
 
 namespace lbd {
+
+// NVTX range over a host scope (header-only NVTX v3: free when no tool is
+// attached); names the library's phases in Nsight timelines.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Arguments of the fused coupled-step kernel.  Arrays are pitched: site (x, y)
 // at y*pitch + x, population i at offset i*plane with plane = pitch*ny.
@@ -54,8 +64,9 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 //   bx in {32, 64}:   tiled kernel (lbd_step.cu), bx x by tiles;
 //   bx in {118, 246}: stripe-marching kernel (lbd_stripe.cu), bx + 10 threads,
 //                     segments of by rows;
-//   bx == 240:        FP32 column-pair kernel (lbd_stripe2.cu), 128 threads,
-//                     segments of by rows (nx % 4 == 0 and nx >= 264 only).
+//   bx == 116:        FP32 stripe kernel with 16-byte population staging
+//                     (lbd_vstripe.cu), 128 threads, segments of by rows
+//                     (periodic lattices with nx % 4 == 0 only).
 struct Tile {
     int bx, by;
 };
@@ -94,10 +105,12 @@ int stripe_batch_ctas_per_sm(int nt);
 cudaError_t launch_time_advance(long long *t_dev, long long add, cudaStream_t s);
 cudaError_t launch_time_set(long long *t_dev, long long value, cudaStream_t s);
 
-// FP32 column-pair stripe kernel.
-cudaError_t launch_pair(const StepArgs<float> &a, int seg, cudaStream_t s);
-bool pair_supported(int nx);
-size_t pair_smem_bytes();
+// FP32 stripe kernel with 16-byte population row staging (lbd_vstripe.cu):
+// periodic lattices with nx % 4 == 0 whose nine planes fit 32-bit byte offsets.
+bool vstripe_supported(int nx, long long plane);
+size_t vstripe_smem_bytes();
+cudaError_t launch_vstripe(const StepArgs<float> &a, int seg, cudaStream_t s);
+
 
 // Per-droplet sums (lbd_droplets.cu) on the dense fields of the fields
 // evaluation (5 arrays of nx*ny doubles: rho, ux, uy, phi, psi).  Tracking
@@ -156,6 +169,12 @@ int adjoint_run(const AdjointJob<T> &job);
 // Shared memory bytes the fused kernel needs for a tile shape.
 template <typename T>
 size_t step_smem_bytes(Tile tile);
+
+// Every device and pinned-host allocation of the library goes through these,
+// so that the test hook lbd_debug_fail_alloc can make the n-th one fail as if
+// the memory were exhausted (cudaErrorMemoryAllocation, nothing allocated).
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t host_malloc(void **p, size_t bytes);
 
 // Tile shapes compiled into the library.
 int n_tiles();

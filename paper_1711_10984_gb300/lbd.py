@@ -111,6 +111,9 @@ SIGNATURES = {
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_set_time": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_synchronize": (ctypes.c_int, [_P]),
+    "lbd_set_check": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "lbd_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
+    "lbd_fp64_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "lbd_destroy": (None, [_P]),
 }
 
@@ -243,10 +246,20 @@ class Sim:
         self._check(load().lbd_get_populations(self._h, f.ctypes.data_as(_dp)))
         return f.reshape(9, self.ny, self.nx)
 
-    def diagnostics(self, refx, refy):
+    def diagnostics(self, refx, refy, check=False):
+        """lbd_diagnostics as a dict; its verdict (LBD_OK, LBD_ENONFINITE or
+        LBD_EUNSTABLE) is under "status", and check=True raises on a bad one."""
         d = lbd_diag()
-        self._check(load().lbd_diagnostics(self._h, float(refx), float(refy), ctypes.byref(d)))
-        return {k: getattr(d, k) for k, _ in lbd_diag._fields_}
+        rc = load().lbd_diagnostics(self._h, float(refx), float(refy), ctypes.byref(d))
+        if rc not in (LBD_OK, LBD_ENONFINITE, LBD_EUNSTABLE) or (check and rc != LBD_OK):
+            self._check(rc)
+        out = {k: getattr(d, k) for k, _ in lbd_diag._fields_}
+        out["status"] = rc
+        return out
+
+    def set_check(self, every):
+        """lbd_set_check: run-time checks every `every` steps (0 = off)."""
+        self._check(load().lbd_set_check(self._h, int(every)))
 
     def droplets(self, refs):
         """Per-droplet centre, mass, mean velocity and site count (lbd_droplets)
@@ -345,9 +358,13 @@ class Batch:
 
     def diagnostics(self, k, refx, refy):
         d = lbd_diag()
-        self._check(load().lbd_batch_diagnostics(self._h, int(k), float(refx), float(refy),
-                                                 ctypes.byref(d)))
-        return {kk: getattr(d, kk) for kk, _ in lbd_diag._fields_}
+        rc = load().lbd_batch_diagnostics(self._h, int(k), float(refx), float(refy),
+                                          ctypes.byref(d))
+        if rc not in (LBD_OK, LBD_ENONFINITE, LBD_EUNSTABLE):
+            self._check(rc)
+        out = {kk: getattr(d, kk) for kk, _ in lbd_diag._fields_}
+        out["status"] = rc
+        return out
 
     def step(self, n=1):
         self._check(load().lbd_batch_step(self._h, int(n)))

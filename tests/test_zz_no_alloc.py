@@ -31,47 +31,100 @@ def built():
     lbd.load()
 
 
-@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
-def test_static_scratch_diagnostics_match(prec):
-    torch = pytest.importorskip("torch")
-    nx, ny = 200, 150
-    d = dict(x=90.5, y=70.0, R=30.0, psi_mean=0.1, noise=0.01, gx=0.005)
-    phi, psi = inputs.droplet_fields(nx, ny, [d], seed=21)
+def _state(prec, nx, ny, seed, steps, R):
+    d = dict(x=nx * 0.45 + 0.5, y=ny * 0.47, R=R, psi_mean=0.1, noise=0.01, gx=0.005)
+    phi, psi = inputs.droplet_fields(nx, ny, [d], seed=seed)
     kw = dict(M=0.5, tau=0.8, gamma=1.5e-3, c0=0.09, A0=1e-6, A_max=1e-4, t_on=0)
-    src = [inputs.default_source(d, nx, ny)]
-    sim = lbd.Sim(nx, ny, precision=prec, sources=src, **kw)
+    sim = lbd.Sim(nx, ny, precision=prec, sources=[inputs.default_source(d, nx, ny)], **kw)
     sim.set_fields(phi, psi)
-    sim.step(120)
+    sim.step(steps)
+    return sim, d
 
-    # the same state, copied into device buffers that the test owns
+
+def _device_copy(torch, sim, prec, pad):
+    """The state of sim in device buffers owned by the test, rows padded by pad
+    elements (pitch = nx + pad); returns the three buffers and the pitch."""
     f = sim.populations()
     _, _, _, ph, ps = sim.fields()
     dt = torch.float64 if prec == lbd.LBD_FP64 else torch.float32
-    g_dev = torch.tensor(f - W[:, None, None], dtype=dt, device="cuda").contiguous()
-    phi_dev = torch.tensor(ph, dtype=dt, device="cuda").contiguous()
-    psi_dev = torch.tensor(ps, dtype=dt, device="cuda").contiguous()
-    torch.cuda.synchronize()
+    ny, nx = ph.shape
+    pitch = nx + pad
+    g = torch.full((9, ny, pitch), float("nan"), dtype=dt, device="cuda")
+    p1 = torch.full((ny, pitch), float("nan"), dtype=dt, device="cuda")
+    p2 = torch.full((ny, pitch), float("nan"), dtype=dt, device="cuda")
+    g[:, :, :nx] = torch.tensor(f - W[:, None, None], dtype=dt)
+    p1[:, :nx] = torch.tensor(ph, dtype=dt)
+    p2[:, :nx] = torch.tensor(ps, dtype=dt)
+    return (g, p1, p2), pitch
 
+
+def _call(L, nx, ny, pitch, prec, bufs, refx, refy, stream):
+    out = lbd.lbd_diag()
+    rc = L.lbd_diagnostics_static(nx, ny, pitch, prec, bufs[0].data_ptr(), bufs[1].data_ptr(),
+                                  bufs[2].data_ptr(), 0.006, -0.05, refx, refy, stream,
+                                  ctypes.byref(out))
+    assert rc == lbd.LBD_OK, rc
+    return {k: getattr(out, k) for k, _ in lbd.lbd_diag._fields_}
+
+
+def _agree(got, want, prec, what):
+    tol = 1e-12 if prec == lbd.LBD_FP64 else 1e-7
+    for k in ("sum_rho", "sum_phi", "sum_psi", "mass_pos"):
+        assert abs(got[k] - want[k]) <= tol * max(abs(want[k]), 1.0), (what, k)
+    ctol = 1e-10 if prec == lbd.LBD_FP64 else 1e-5
+    assert abs(got["cm_x"] - want["cm_x"]) <= ctol, what
+    assert abs(got["cm_y"] - want["cm_y"]) <= ctol, what
+    assert got["min_B"] == want["min_B"] and got["min_psi"] == want["min_psi"], what
+    assert got["nonfinite"] == want["nonfinite"] == 0, what
+
+
+@pytest.mark.parametrize("pad", [0, 24], ids=["pitch=nx", "pitch=nx+24"])
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
+def test_static_scratch_diagnostics_match(prec, pad):
+    """Two calls in a row on the same state agree with lbd_diagnostics, also with
+    a call on a different (smaller) lattice between them, whose own results
+    must not leak into the next call's; on the legacy stream and on a
+    caller-given stream; with unpadded and padded rows (the padding is NaN, so
+    a read of it would show)."""
+    torch = pytest.importorskip("torch")
+    nx, ny = 200, 150
+    sim, d = _state(prec, nx, ny, seed=21, steps=120, R=30.0)
+    other, od = _state(prec, 72, 40, seed=5, steps=30, R=12.0)
+    bufs, pitch = _device_copy(torch, sim, prec, pad)
+    obufs, opitch = _device_copy(torch, other, prec, 8)
+    torch.cuda.synchronize()
     L = lbd.load()
-    for refx, refy in [(d["x"], d["y"]), (5.0, 140.0)]:
-        want = sim.diagnostics(refx, refy)
-        for call in range(2):
-            out = lbd.lbd_diag()
-            rc = L.lbd_diagnostics_static(nx, ny, nx, prec, g_dev.data_ptr(), phi_dev.data_ptr(),
-                                          psi_dev.data_ptr(), kw.get("B0", 0.006),
-                                          kw.get("B1", -0.05), refx, refy, None,
-                                          ctypes.byref(out))
-            assert rc == lbd.LBD_OK, (call, rc)
-            got = {k: getattr(out, k) for k, _ in lbd.lbd_diag._fields_}
-            tol = 1e-12 if prec == lbd.LBD_FP64 else 1e-7
-            for k in ("sum_rho", "sum_phi", "sum_psi", "mass_pos"):
-                assert abs(got[k] - want[k]) <= tol * max(abs(want[k]), 1.0), (call, k)
-            ctol = 1e-10 if prec == lbd.LBD_FP64 else 1e-5
-            assert abs(got["cm_x"] - want["cm_x"]) <= ctol, call
-            assert abs(got["cm_y"] - want["cm_y"]) <= ctol, call
-            assert got["min_B"] == want["min_B"] and got["min_psi"] == want["min_psi"]
-            assert got["nonfinite"] == want["nonfinite"] == 0
+    side = torch.cuda.Stream()
+    for stream in (None, side.cuda_stream):
+        for refx, refy in [(d["x"], d["y"]), (5.0, 140.0)]:
+            want = sim.diagnostics(refx, refy)
+            got1 = _call(L, nx, ny, pitch, prec, bufs, refx, refy, stream)
+            _agree(got1, want, prec, "first call")
+            owant = other.diagnostics(od["x"], od["y"])
+            ogot = _call(L, 72, 40, opitch, prec, obufs, od["x"], od["y"], stream)
+            _agree(ogot, owant, prec, "other lattice")
+            got2 = _call(L, nx, ny, pitch, prec, bufs, refx, refy, stream)
+            _agree(got2, want, prec, "second call")
     sim.close()
+    other.close()
+
+
+def test_static_scratch_rejects_host_pointer():
+    """A host buffer handed in where device memory belongs is refused
+    (LBD_EINVAL) instead of reaching the kernel."""
+    torch = pytest.importorskip("torch")
+    nx, ny = 16, 8
+    host = np.zeros(9 * nx * ny)
+    dev = torch.zeros(9 * nx * ny, dtype=torch.float64, device="cuda")
+    L = lbd.load()
+    out = lbd.lbd_diag()
+    hp = host.ctypes.data
+    for g, phi, psi in ((hp, dev.data_ptr(), dev.data_ptr()),
+                        (dev.data_ptr(), hp, dev.data_ptr()),
+                        (dev.data_ptr(), dev.data_ptr(), hp)):
+        rc = L.lbd_diagnostics_static(nx, ny, nx, lbd.LBD_FP64, g, phi, psi, 0.006, -0.05, 1.0,
+                                      1.0, None, ctypes.byref(out))
+        assert rc == lbd.LBD_EINVAL
 
 
 def test_static_scratch_rejects_oversized_lattice():
