@@ -8,8 +8,9 @@ Workload (one GPU): the dilute emulsion, a periodic 2048 x 2048 lattice with 64
 seeded droplets of radius 25, seeded surfactant asymmetries and one source disk
 per droplet, source and sink active.  A "step" is one coupled time step of the
 whole lattice (force, LB collide-and-stream, advection, diffusion, source and
-sink); every 100 steps the FP64 diagnostics reduction (totals, centroid, minima)
-runs as well.  The FP32 state is 369 MB, larger than the 129 MB L2, so no L2
+sink); every min(100, K) steps of the step count the diagnostics reduction
+(totals, centroid sums, minima, non-finite count: FP64 results) runs as well,
+queued on the stream without a host synchronisation (lbd_set_check).  The FP32 state is 369 MB, larger than the 129 MB L2, so no L2
 flush is needed between steps.
 
 With --gpus N under torchrun every rank runs its own replica (different seed):
@@ -150,18 +151,34 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ ours
-def kernel_source_hash():
-    """Hash of the sources of the profiled step kernel (stripe_kernel)."""
+# Sources of each kernel family, by the launch shape's column count.
+KERNEL_SOURCES = {116: ("lbd_vstripe.cu", "lbd_internal.h"),
+                  118: ("lbd_stripe.cu", "lbd_internal.h"),
+                  246: ("lbd_stripe.cu", "lbd_internal.h")}
+
+
+def kernel_name(tile, prec):
+    t = "float" if prec == 1 else "double"
+    if tile[0] == 116:
+        return "vstripe_kernel (FP32, 116-column stripes, segments of %d rows)" % tile[1]
+    if tile[0] in (118, 246):
+        return "stripe_kernel<%s,%d> (segments of %d rows)" % (t, tile[0] + 10, tile[1])
+    return "step_kernel<%s,%d,%d>" % (t, tile[0], tile[1])
+
+
+def kernel_source_hash(tile):
+    """Hash of the sources of the kernel that runs launch shape `tile`."""
     h = hashlib.sha256()
-    for name in ("lbd_stripe.cu", "lbd_internal.h"):
+    for name in KERNEL_SOURCES.get(tile[0], ("lbd_step.cu", "lbd_internal.h")):
         with open(os.path.join(ROOT, "paper_1711_10984_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(precision):
+def ncu_traffic(precision, tile):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+    if it was taken on the current source of the kernel that runs `tile`;
+    else None."""
     name = "step_kernel_%s_emulsion2048.txt" % ("fp32" if precision == 1 else "fp64")
     path = os.path.join(ROOT, "profiles", name)
     try:
@@ -170,54 +187,76 @@ def ncu_traffic(precision):
         return None
     m = re.search(r"source_hash:\s*(\w+)", text)
     t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
-    if not m or not t or m.group(1) != kernel_source_hash():
+    k = re.search(r"launch_shape:\s*(\d+)x(\d+)", text)
+    if not m or not t or m.group(1) != kernel_source_hash(tile):
+        return None
+    if k and int(k.group(1)) != tile[0]:
         return None
     return float(t.group(1))
 
 
 def time_precision(torch, lbd, autotune, w, prec, steps, warmup, stream, dev_name, barrier):
+    """K timed steps of the whole path: the coupled step every step and the S8
+    reduction (lbd_set_check: totals, centroid sums, minima, non-finite count,
+    queued on the stream with its result copied to pinned host memory, no host
+    synchronisation) every min(100, K) steps of the step count.  Then, outside
+    the timed region, K more launches of the step kernel alone, timed with CUDA
+    events on the same stream, for the kernel's roofline."""
     sim = lbd.Sim(w["nx"], w["ny"], precision=prec, sources=w["sources"], stream=stream.cuda_stream,
                   **w["params"])
     sim.set_fields(w["phi"], w["psi"])
     tile = autotune.tune(sim, dev_name)
+    every = min(DIAG_EVERY, steps)
+    sim.set_check(every)
     sim.step(warmup)
     sim.synchronize()
     ref = (w["droplets"][0]["x"], w["droplets"][0]["y"])
     d0 = sim.diagnostics(*ref)
+    t0 = sim.t
     ev = lambda: torch.cuda.Event(enable_timing=True)
     barrier()
     e0, e1 = ev(), ev()
-    chunks = []
     e0.record(stream)
-    done = 0
-    launches = 0
-    while done < steps:
-        c = min(DIAG_EVERY, steps - done)
-        k0, k1 = ev(), ev()
-        k0.record(stream)
-        sim.step(c)
-        k1.record(stream)
-        chunks.append((k0, k1, c))
-        done += c
-        launches += c
-        if done % DIAG_EVERY == 0 or done == steps:
-            sim.diagnostics(*ref)   # S8 reduction: two launches, synchronises
-            launches += 2
+    sim.step(steps)
     e1.record(stream)
     e1.synchronize()
     barrier()
     total_ms = e0.elapsed_time(e1)
-    kernel_ms = sum(a.elapsed_time(b) for a, b, _ in chunks)
+    sim.synchronize()  # the checks' verdicts: raises if one found the state broken
+    checks = (t0 + steps) // every - t0 // every
+    sim.set_check(0)
+    k0, k1 = ev(), ev()
+    k0.record(stream)
+    sim.step(steps)
+    k1.record(stream)
+    k1.synchronize()
+    kernel_ms = k0.elapsed_time(k1)
     d1 = sim.diagnostics(*ref)
     drift = {k: (d1[k] - d0[k]) / abs(d0[k]) for k in ("sum_rho", "sum_phi")}
     sim.close()
-    return dict(total_ms=total_ms, kernel_ms=kernel_ms, tile=list(tile), launches=launches,
+    return dict(total_ms=total_ms, kernel_ms=kernel_ms, tile=list(tile),
+                launches=steps + 2 * checks, checks=checks, every=every,
                 drift=drift, nonfinite=d1["nonfinite"])
 
 
-def time_e2e(torch, lbd, w, steps, stream):
-    """The same FP32 job through the public API from pinned host memory: upload
-    phi, psi (H2D), run the steps, read all five fields back (D2H)."""
+def fp64_peak_measured(lbd):
+    """The device's FP64 FMA rate in flop/s (lbd_fp64_peak), best of three; None
+    if the measurement fails."""
+    import ctypes
+    best = None
+    for _ in range(3):
+        v = ctypes.c_double()
+        if lbd.load().lbd_fp64_peak(4000, ctypes.byref(v)) == lbd.LBD_OK:
+            best = v.value if best is None else max(best, v.value)
+    return best
+
+
+def time_e2e(torch, lbd, autotune, w, steps, stream, dev_name):
+    """The same FP32 job through the public API from pinned host memory, in the
+    headline's launch shape and diagnostics cadence: upload phi, psi (H2D,
+    lbd_set_fields), K steps with the S8 reduction every min(100, K) steps (its
+    9 doubles copied D2H each time), then all five fields read back (D2H,
+    lbd_get_fields)."""
     n = w["nx"]
     N = n * n
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
@@ -225,13 +264,17 @@ def time_e2e(torch, lbd, w, steps, stream):
     outs = [torch.empty(N, dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
     sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=w["sources"], stream=stream.cuda_stream,
                   **w["params"])
+    autotune.tune(sim, dev_name)
+    every = min(DIAG_EVERY, steps)
     sim.set_fields(phi_h, psi_h)  # untimed first call (allocates the staging area)
+    sim.set_check(every)
     sim.step(2)
     sim.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record(stream)
     sim.set_fields(phi_h, psi_h)
+    t_start = sim.t
     sim.step(steps)
     import ctypes
     dp = ctypes.POINTER(ctypes.c_double)
@@ -240,9 +283,11 @@ def time_e2e(torch, lbd, w, steps, stream):
     e1.synchronize()
     wall = time.perf_counter() - t0
     sim._check(rc)
+    sim.synchronize()
+    checks = (t_start + steps) // every - t_start // every
     sim.close()
     ms = max(e0.elapsed_time(e1), wall * 1e3)
-    return dict(ms=ms, h2d=2 * 8 * N, d2h=5 * 8 * N)
+    return dict(ms=ms, h2d=2 * 8 * N, d2h=5 * 8 * N + 9 * 8 * checks, every=every)
 
 
 def time_batch(torch, lbd, steps, warmup, count=256):
@@ -445,9 +490,11 @@ def run_ours(args):
     r64 = time_precision(torch, lbd, autotune, w, lbd.LBD_FP64, args.steps, args.warmup, stream,
                          dev_name, barrier)
     clk = clocks.stop()
-    e2e = time_e2e(torch, lbd, w, args.steps, stream)
+    fp64_rate = fp64_peak_measured(lbd)
+    e2e = time_e2e(torch, lbd, autotune, w, args.steps, stream, dev_name)
     batch = time_batch(torch, lbd, min(args.steps, 500), args.warmup)
-    adj = time_adjoint(lbd, steps=min(4000, 4 * args.steps)) if rank == 0 else None
+    # the adjoint workload at its own size, whatever --steps is
+    adj = time_adjoint(lbd, steps=4000, ckpt=100) if rank == 0 else None
     # walls (bounce-back plates): the same emulsion between plates, and the
     # channel of Section 4 (512 x 256, one droplet R = 32, tau = 0.6)
     from paper_1711_10984_gb300 import inputs
@@ -479,7 +526,12 @@ def run_ours(args):
     ach64_gbs = BYTES_PER_SITE[0] * N / (k64 / args.steps * 1e-3) / 1e9
     flops64 = FLOPS_PER_SITE * N / (k64 / args.steps * 1e-3) / 1e12
     mhz = clk.get("sm_mhz") or SM_MAX_MHZ
-    fp64_peak = FP64_NOMINAL_TFLOPS * mhz / SM_MAX_MHZ
+    if fp64_rate:
+        fp64_peak, fp64_src = fp64_rate / 1e12, (
+            "measured: lbd_fp64_peak (independent FP64 FMAs on every SM, CUDA events)")
+    else:
+        fp64_peak, fp64_src = FP64_NOMINAL_TFLOPS * mhz / SM_MAX_MHZ, (
+            "nominal 1.25 TFLOP/s at 2070 MHz x median SM clock (measurement failed)")
     out = {
         "metric": METRIC, "value": round(mlups32, 1), "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t32 / args.steps,
@@ -488,21 +540,25 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "sites_per_gpu": N, "precision": "FP32 shifted populations",
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state 369 MB > 129 MB L2, no flush", "tile": r32["tile"],
-                   "diagnostics_every": DIAG_EVERY},
+                   "diagnostics_every": r32["every"], "diagnostics_in_timed_region": r32["checks"]},
         "roofline": {"bound": "hbm", "achieved": round(ach32, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(ach32 / hbm, 4), "traffic": ncu_traffic(1),
-                     "peak_source": src, "kernel": "step_kernel<float>",
+                     "frac": round(ach32 / hbm, 4), "traffic": ncu_traffic(1, r32["tile"]),
+                     "peak_source": src, "kernel": kernel_name(r32["tile"], 1),
+                     "timing": "CUDA events around %d back-to-back launches on the launching "
+                               "stream" % args.steps,
                      "bytes_per_site": BYTES_PER_SITE[1]},
         "fp64": {"value": round(mlups64, 1), "unit": "MLUPS", "ms_per_step": t64 / args.steps,
                  "dtype": "f64", "tile": r64["tile"],
                  "roofline": {"bound": "alu", "achieved": round(flops64, 4),
                               "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                               "frac": round(flops64 / fp64_peak, 4),
-                              "peak_source": "nominal 1.25 TFLOP/s at 2070 MHz x median SM clock",
+                              "peak_source": fp64_src,
                               "flops_per_site": FLOPS_PER_SITE,
                               "hbm_gbs_achieved": round(ach64_gbs, 1),
                               "hbm_frac": round(ach64_gbs / hbm, 4),
-                              "traffic": ncu_traffic(0)},
+                              "traffic": ncu_traffic(0, r64["tile"]),
+                              "kernel": kernel_name(r64["tile"], 0),
+                              "nominal_tflops": FP64_NOMINAL_TFLOPS},
                  "drift": r64["drift"]},
         "fp32_over_fp64_speedup": round(t64 / t32, 2),
         "fp32_drift": r32["drift"],
@@ -539,8 +595,10 @@ def run_ours(args):
         "e2e": {"value": round(world * N * args.steps / te / 1e3, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps,
-                "what": "lbd_set_fields from pinned host phi/psi, lbd_step(K), "
-                        "lbd_get_fields of rho, u, phi, psi to pinned host"},
+                "what": "one job of K=%d steps through the C ABI: lbd_set_fields from pinned "
+                        "host phi/psi, lbd_step(K) with the S8 reduction every %d steps (its 9 "
+                        "doubles copied to pinned host memory), lbd_get_fields of rho, u, phi, "
+                        "psi to pinned host" % (args.steps, e2e["every"])},
         "clocks": clk,
         "gpu_launches": r32["launches"],
     }

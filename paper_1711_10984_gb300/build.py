@@ -13,9 +13,9 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "liblbd.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["lbd_step.cu", "lbd_stripe.cu", "lbd_stripe2.cu", "lbd_adjoint.cu", "lbd_droplets.cu",
+SOURCES = ["lbd_step.cu", "lbd_stripe.cu", "lbd_vstripe.cu", "lbd_adjoint.cu", "lbd_droplets.cu",
            "lbd3.cu",
-           "lbd_api.cu"]
+           "lbd_peak.cu", "lbd_api.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
