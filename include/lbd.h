@@ -254,6 +254,9 @@ int lbd_squirmer(lbd_ctx *ctx, int32_t n, const lbd_droplet *drops, double *b1, 
  * kernels agree to rounding. */
 int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);
 
+/* The context's current launch shape (either pointer may be NULL). */
+int lbd_get_tile(const lbd_ctx *ctx, int32_t *bx, int32_t *by);
+
 /* Tile shapes compiled into the library: writes up to cap pairs into bx[], by[]
  * and returns how many shapes exist. */
 int lbd_tiles(int32_t *bx, int32_t *by, int32_t cap);
@@ -291,9 +294,9 @@ int lbd_adjoint(lbd_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double ref_x, 
  * synchronisation a cudaMalloc or cudaFree can cause.  It computes the same
  * quantities as lbd_diagnostics (the paper has no counterpart of this entry
  * point) and allocates nothing: its reduction scratch is a fixed array of
- * 43,848 bytes (608 blocks x 9 partial sums + 9 results) compiled into the
- * library, which every GPU that loads the library holds until the process
- * exits.
+ * 43,856 bytes (608 blocks x 9 partial sums, a completion counter, 9 results)
+ * compiled into the library, which every GPU that loads the library holds
+ * until the process exits.
  *
  * Inputs (device pointers, caller-owned, read only): g = the 9 population
  * planes stored as deviations f_i - w_i from the rest weights, plane i at
@@ -316,8 +319,9 @@ int lbd_adjoint(lbd_ctx *ctx, int64_t nsteps, int32_t ckpt_every, double ref_x, 
  * library's device code there: make that first call before any stream
  * capture.  All calls share the one array: calls that overlap on the GPU
  * (different streams or host threads) race on it and must be serialised by
- * the caller.  Every scratch slot is overwritten on each call, so nothing
- * needs clearing. */
+ * the caller.  Every scratch slot a call reads is written earlier in the same
+ * call, except the completion counter of the FP32 reduction, which starts at
+ * zero when the device code loads and which every call leaves at zero. */
 int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precision,
                            const void *g, const void *phi, const void *psi, double B0, double B1,
                            double ref_x, double ref_y, void *stream, lbd_diag *out);
@@ -347,12 +351,17 @@ int lbd_batch_get_fields(lbd_batch *b, int32_t k, double *rho, double *ux, doubl
 int lbd_batch_diagnostics(lbd_batch *b, int32_t k, double ref_x, double ref_y, lbd_diag *out);
 /* Advance every instance by nsteps (asynchronous on the batch stream). */
 int lbd_batch_step(lbd_batch *b, int64_t nsteps);
-/* Launch shape of the batched kernel: bx 118 or 246, by 32, 64 or 128. */
+/* Launch shape of the batched kernel: bx 116 (FP32 16-byte staged stripe kernel
+ * for the periodic instances, which must then be 4k wide; instances with plates
+ * take 118-column stripes of the stripe kernel), 118 or 246, by 32, 64 or 128.
+ * FP32 batches start at 116 x 64 where it is valid, the others at 118 x 64. */
 int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by);
 /* Time the batched launch for each shape (reps launches each, no state change)
  * and keep the fastest; returns it in *bx, *by (may be NULL). */
 int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by);
 int lbd_batch_synchronize(lbd_batch *b);
+/* The batch's current launch shape (either pointer may be NULL). */
+int lbd_batch_get_tile(const lbd_batch *b, int32_t *bx, int32_t *by);
 int lbd_batch_get_time(const lbd_batch *b, int64_t *t);
 void lbd_batch_destroy(lbd_batch *b);
 

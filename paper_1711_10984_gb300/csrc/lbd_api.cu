@@ -20,6 +20,7 @@ namespace {
 constexpr int NRED = 9;      // reduction slots, see reduce_partial
 constexpr int RED_BLOCKS = 608;  // 4 x 152 SMs
 constexpr int RED_THREADS = 256;
+constexpr int RED32_BLOCKS = 456;  // FP32 reduction: 3 resident blocks on each of 152 SMs
 
 }  // namespace
 
@@ -374,60 +375,86 @@ __global__ void reduce_partial(int nx, int ny, long long pitch, long long plane,
         for (int k = 0; k < NRED; ++k) partial[k * gridDim.x + blockIdx.x] = v[k];
 }
 
-// Compensated FP32 running sum (Neumaier): s + c carries the sum of the added
-// terms to within about one FP32 rounding of the largest partial sum.
-struct Neu {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = s + x;
-        c += fabsf(s) >= fabsf(x) ? (s - t) + x : (x - t) + s;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+// Exact sum of two floats: s + e == a + b (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Reference point of the minimum image, split on the host into its integer
+// part and fraction, with the integer thresholds that reproduce the FP64 test
+// d = x - ref >= n/2 (d -= n), d < -n/2 (d += n) for d = k - frac, k = x - floor(ref):
+// k >= hi wraps down, k < lo wraps up.
+struct RefImage {
+    int ix, iy, hix, lox, hiy, loy;
+    double frx, fry;
 };
 
-// The FP32 form of reduce_partial, with the same slots and the same results up
-// to rounding: each thread walks 4-site row chunks and accumulates the six sums
-// in FP32 with Neumaier compensation (the per-thread totals, over a few dozen
-// sites, are then combined in FP64 per block); min and max psi are kept in
-// FP32 and turned into min B = B0 + B1 psi (monotone in psi) once per thread,
-// in FP64; the minimum-image displacements are integers (x - floor(ref)),
-// wrapped with integer thresholds that reproduce the FP64 test
-// d = x - ref >= nx/2 (d -= nx), d < -nx/2 (d += nx), and the fractional part
-// of ref is taken off in FP64 after the block sums (slots 3-4 then hold the
-// same quantity as in FP64).  A site whose eleven values do not add up to a
-// finite number is re-examined value by value, so that the count is that of
-// sites holding a non-finite value.
-__global__ void reduce_partial_f32(int nx, int ny, long long pitch, long long plane,
-                                   const float *g, const float *phi, const float *psi, double B0,
-                                   double B1, double refx, double refy, int vec, double *partial) {
-    __shared__ double smem[NRED * 32];
-    const double fx = floor(refx), fy = floor(refy), frx = refx - fx, fry = refy - fy;
-    const int ix = (int)fx, iy = (int)fy;
-    // integer wrap thresholds: d = k - frac wraps down when k >= hi, up when k < lo
-    const int hix = (int)ceil(0.5 * nx + frx), lox = (int)ceil(frx - 0.5 * nx);
-    const int hiy = (int)ceil(0.5 * ny + fry), loy = (int)ceil(fry - 0.5 * ny);
-    Neu sg, sp, sc, sdx, sdy, spp;
-    float pmin = INFINITY, pmax = -INFINITY;
-    double bad = 0.0;
+RefImage ref_image(int nx, int ny, double refx, double refy) {
+    RefImage r;
+    const double fx = std::floor(refx), fy = std::floor(refy);
+    r.ix = (int)fx;
+    r.iy = (int)fy;
+    r.frx = refx - fx;
+    r.fry = refy - fy;
+    r.hix = (int)std::ceil(0.5 * nx + r.frx);
+    r.lox = (int)std::ceil(r.frx - 0.5 * nx);
+    r.hiy = (int)std::ceil(0.5 * ny + r.fry);
+    r.loy = (int)std::ceil(r.fry - 0.5 * ny);
+    return r;
+}
+
+// The FP32 form of the diagnostics reduction, with the results of the FP64
+// form up to rounding, in one launch of RED32_BLOCKS (<= RED_BLOCKS) blocks:
+//  * each thread walks 4-site row chunks (16-byte loads where rows and planes
+//    are 16-byte aligned) and accumulates the six sums in FP32 with Neumaier
+//    compensation; the warps merge the (sum, compensation) pairs by TwoSum
+//    over shuffles; each warp's totals are combined in FP64 per block in a
+//    fixed order, into partial[k * gridDim.x + block];
+//  * min and max psi stay in FP32: min B = B0 + B1 psi is monotone in psi, so
+//    it is evaluated once, at the extreme psi (max for B1 < 0);
+//  * the minimum-image displacements are integers (RefImage); slots 3-4 are
+//    shifted by the fraction of ref times the phi >= 0 mass in FP64;
+//  * a site whose eleven values do not add up to a finite number is
+//    re-examined value by value, so the count is that of sites holding a
+//    non-finite value;
+//  * the block that finishes last (a counter at partial[NRED * RED_BLOCKS],
+//    zero between calls) combines the block partials in a fixed order and
+//    writes the NRED results to out, so the results do not depend on which
+//    block finishes last.
+__global__ void __launch_bounds__(RED_THREADS, 3) reduce_f32(
+    int nx, int ny, long long pitch, long long plane, const float *g, const float *phi,
+    const float *psi, double B0, double B1, RefImage ri, int vec, double *partial, double *out) {
+    constexpr int NW = RED_THREADS / 32;
+    __shared__ double wsum[6][NW];
+    __shared__ float wext[3][NW];  // min psi, max psi, bad count
+    __shared__ bool last;
+    float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cmp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    auto add = [&](int k, float x) {
+        const float t = s[k] + x;
+        cmp[k] += fabsf(s[k]) >= fabsf(x) ? (s[k] - t) + x : (x - t) + s[k];
+        s[k] = t;
+    };
+    float pmin = INFINITY, pmax = -INFINITY, bad = 0.f;
     const int nq = (nx + 3) >> 2;
     const long long nchunks = (long long)nq * ny;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nchunks;
          q += (long long)gridDim.x * blockDim.x) {
         const int y = (int)(q / nq), x0 = (int)(q - (long long)y * nq) * 4;
-        int ky = y - iy;
-        if (ky >= hiy) ky -= ny; else if (ky < loy) ky += ny;
+        int ky = y - ri.iy;
+        if (ky >= ri.hiy) ky -= ny; else if (ky < ri.loy) ky += ny;
         const long long o = (long long)y * pitch + x0;
         const int cnt = nx - x0 < 4 ? nx - x0 : 4;
         float gv[4] = {0.f, 0.f, 0.f, 0.f}, pv[4] = {0.f, 0.f, 0.f, 0.f}, cv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (vec && cnt == 4) {  // 16-byte loads: rows and planes 16-byte aligned
+        if (vec && cnt == 4) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float4 v = *reinterpret_cast<const float4 *>(g + i * plane + o);
+                const float4 v = __ldcs(reinterpret_cast<const float4 *>(g + i * plane + o));
                 gv[0] += v.x; gv[1] += v.y; gv[2] += v.z; gv[3] += v.w;
             }
-            const float4 a = *reinterpret_cast<const float4 *>(phi + o);
-            const float4 b = *reinterpret_cast<const float4 *>(psi + o);
+            const float4 a = __ldcs(reinterpret_cast<const float4 *>(phi + o));
+            const float4 b = __ldcs(reinterpret_cast<const float4 *>(psi + o));
             pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
             cv[0] = b.x; cv[1] = b.y; cv[2] = b.z; cv[3] = b.w;
         } else {
@@ -442,45 +469,107 @@ __global__ void reduce_partial_f32(int nx, int ny, long long pitch, long long pl
             if (k >= cnt) break;
             const float ph = pv[k], c = cv[k];
             if (!isfinite(gv[k] + ph + c)) {
-                // slow path: which of the eleven values is not finite
                 bool nf = !isfinite(ph) || !isfinite(c);
                 for (int i = 0; i < 9; ++i) nf |= !isfinite(g[i * plane + o + k]);
-                bad += nf ? 1.0 : 0.0;
+                bad += nf ? 1.f : 0.f;
             }
-            sg.add(gv[k]);
-            sp.add(ph);
-            sc.add(c);
+            add(0, gv[k]);
+            add(1, ph);
+            add(2, c);
             if (ph >= 0.f) {
-                int kx = x0 + k - ix;
-                if (kx >= hix) kx -= nx; else if (kx < lox) kx += nx;
-                sdx.add(ph * (float)kx);
-                sdy.add(ph * (float)ky);
-                spp.add(ph);
+                int kx = x0 + k - ri.ix;
+                if (kx >= ri.hix) kx -= nx; else if (kx < ri.lox) kx += nx;
+                add(3, ph * (float)kx);
+                add(4, ph * (float)ky);
+                add(5, ph);
             }
             pmin = fminf(pmin, c);
             pmax = fmaxf(pmax, c);
         }
     }
-    double v[NRED];
-    v[0] = sg.value();
-    v[1] = sp.value();
-    v[2] = sc.value();
-    v[3] = sdx.value();
-    v[4] = sdy.value();
-    v[5] = spp.value();
-    // B0 + B1 psi is monotone in psi: its minimum over the sites sits at the
-    // extreme psi (no site: +inf, as in the FP64 form)
-    const float pext = B1 < 0.0 ? pmax : pmin;
-    v[6] = isinf(pext) ? INFINITY : B0 + B1 * (double)pext;
-    v[7] = pmin;
-    v[8] = bad;
-    block_reduce(v, smem);
+    // warp: merge the compensated pairs (TwoSum of the sums, compensations added)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float s2 = __shfl_down_sync(0xffffffffu, s[k], o);
+            const float c2 = __shfl_down_sync(0xffffffffu, cmp[k], o);
+            float t, e;
+            two_sum(s[k], s2, t, e);
+            s[k] = t;
+            cmp[k] = (cmp[k] + c2) + e;
+        }
+        pmin = fminf(pmin, __shfl_down_sync(0xffffffffu, pmin, o));
+        pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+        bad += __shfl_down_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        for (int k = 0; k < 6; ++k) wsum[k][warp] = (double)s[k] + (double)cmp[k];
+        wext[0][warp] = pmin;
+        wext[1][warp] = pmax;
+        wext[2][warp] = bad;
+    }
+    __syncthreads();
+    const int nb = gridDim.x;
+    // the completion counter sits after the RED_BLOCKS partials of either form
+    unsigned long long *counter =
+        reinterpret_cast<unsigned long long *>(partial + NRED * RED_BLOCKS);
     if (threadIdx.x == 0) {
-        // slots 3-4 relative to ref: subtract the fractional part of ref times
-        // the mass over phi >= 0
-        v[3] -= frx * v[5];
-        v[4] -= fry * v[5];
-        for (int k = 0; k < NRED; ++k) partial[k * gridDim.x + blockIdx.x] = v[k];
+        double v[6] = {0, 0, 0, 0, 0, 0};
+        float mn = INFINITY, mx = -INFINITY, bd = 0.f;
+        for (int w = 0; w < NW; ++w) {
+            for (int k = 0; k < 6; ++k) v[k] += wsum[k][w];
+            mn = fminf(mn, wext[0][w]);
+            mx = fmaxf(mx, wext[1][w]);
+            bd += wext[2][w];
+        }
+        v[3] -= ri.frx * v[5];
+        v[4] -= ri.fry * v[5];
+        for (int k = 0; k < 6; ++k) partial[k * nb + blockIdx.x] = v[k];
+        partial[6 * nb + blockIdx.x] = mn;
+        partial[7 * nb + blockIdx.x] = mx;
+        partial[8 * nb + blockIdx.x] = bd;
+        __threadfence();
+        last = atomicAdd(counter, 1ull) == (unsigned long long)(nb - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last block: thread t combines the partials of blocks t, t + 256, ...
+    // (sums in double, extremes), then a fixed tree over the threads; the
+    // order does not depend on which block finished last
+    __threadfence();
+    double v[NRED];
+    for (int k = 0; k < NRED; ++k) v[k] = k == 6 ? INFINITY : (k == 7 ? -INFINITY : 0.0);
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+        for (int k = 0; k < NRED; ++k) {
+            const double x = __ldcg(partial + k * nb + b);
+            v[k] = k == 6 ? fmin(v[k], x) : (k == 7 ? fmax(v[k], x) : v[k] + x);
+        }
+    __shared__ double tree[NRED][NW];
+    for (int k = 0; k < NRED; ++k) {
+        double x = v[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, o);
+            x = k == 6 ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+        }
+        if (lane == 0) tree[k][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[NRED];
+        for (int k = 0; k < NRED; ++k) {
+            r[k] = tree[k][0];
+            for (int w = 1; w < NW; ++w)
+                r[k] = k == 6 ? fmin(r[k], tree[k][w]) : (k == 7 ? fmax(r[k], tree[k][w]) : r[k] + tree[k][w]);
+        }
+        for (int k = 0; k < 6; ++k) out[k] = r[k];
+        // min B = B0 + B1 psi at the extreme psi; +inf without any site
+        const double ext = B1 < 0.0 ? r[7] : r[6];
+        out[6] = isinf(ext) ? INFINITY : (B1 == 0.0 ? B0 : B0 + B1 * ext);
+        out[7] = r[6];
+        out[8] = r[8];
+        *counter = 0ull;
     }
 }
 
@@ -497,33 +586,39 @@ __global__ void reduce_final(int nb, const double *partial, double *out) {
         for (int k = 0; k < NRED; ++k) out[k] = v[k];
 }
 
-// The partial reduction of the state in (g, phi, psi) on stream st: the FP32
-// form takes the compensated FP32 kernel (16-byte loads where rows and planes
-// are 16-byte aligned), the FP64 form the FP64 kernel.
-cudaError_t launch_reduce_partial(int prec, int nx, int ny, long long pitch, long long plane,
-                                  const void *g, const void *phi, const void *psi, double B0,
-                                  double B1, double refx, double refy, double *partial,
-                                  cudaStream_t st) {
+// The diagnostics reduction of the state in (g, phi, psi) on stream st into
+// out[NRED]: the FP64 form takes the FP64 block kernel and reduce_final, the
+// FP32 form the compensated FP32 kernel, which finishes in its last block.
+// partial holds NRED * RED_BLOCKS + 1 doubles (the last one a counter that is
+// zero between calls).
+cudaError_t launch_reduce(int prec, int nx, int ny, long long pitch, long long plane, const void *g,
+                          const void *phi, const void *psi, double B0, double B1, double refx,
+                          double refy, double *partial, double *out, cudaStream_t st) {
     if (prec == LBD_FP64) {
         reduce_partial<double><<<RED_BLOCKS, RED_THREADS, 0, st>>>(
             nx, ny, pitch, plane, (const double *)g, (const double *)phi, (const double *)psi, B0,
             B1, refx, refy, partial);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        reduce_final<<<1, RED_THREADS, 0, st>>>(RED_BLOCKS, partial, out);
     } else {
         const int vec = pitch % 4 == 0 && ((uintptr_t)g | (uintptr_t)phi | (uintptr_t)psi) % 16 == 0;
-        reduce_partial_f32<<<RED_BLOCKS, RED_THREADS, 0, st>>>(
+        reduce_f32<<<RED32_BLOCKS, RED_THREADS, 0, st>>>(
             nx, ny, pitch, plane, (const float *)g, (const float *)phi, (const float *)psi, B0, B1,
-            refx, refy, vec, partial);
+            ref_image(nx, ny, refx, refy), vec, partial, out);
     }
     return cudaGetLastError();
 }
 
 // -------------------------------------------- scratch of lbd_diagnostics_static
-// Partial sums of the RED_BLOCKS reduction blocks plus the NRED results:
-// 5481 doubles = 43,848 bytes.  Every GPU that loads this library holds the
-// array until the process exits.  Each call overwrites every slot it reads
-// (each block writes all of its partials, the final kernel writes all results),
-// so nothing has to be cleared between calls.
-constexpr int kStaticScratchDoubles = NRED * RED_BLOCKS + NRED;
+// Partial sums of the RED_BLOCKS reduction blocks, the FP32 form's completion
+// counter, then the NRED results: 5482 doubles = 43,856 bytes.  Every GPU that
+// loads this library holds the array until the process exits.  Each call
+// overwrites every slot it reads (each block writes all of its partials, the
+// final step writes all results); the counter starts at zero (the array is
+// zero-initialised when the library's device code loads) and every FP32 call
+// leaves it at zero.
+constexpr int kStaticScratchDoubles = NRED * RED_BLOCKS + 1 + NRED;
 static __device__ __align__(256) double g_diag_static_scratch[kStaticScratchDoubles];
 
 // Device address of the static scratch on the current device and context.  In
@@ -691,11 +786,9 @@ int queue_check(lbd_ctx *c) {
         judge_check(c, s.h, s.t);
     }
     const lbd_params &p = c->params;
-    CK(c, launch_reduce_partial(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane,
-                                c->g[c->cur], c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, 0.0,
-                                0.0, c->red_partial, c->stream));
-    reduce_final<<<1, RED_THREADS, 0, c->stream>>>(RED_BLOCKS, c->red_partial, s.d);
-    CK(c, cudaGetLastError());
+    CK(c, launch_reduce(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane, c->g[c->cur],
+                        c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, 0.0, 0.0, c->red_partial, s.d,
+                        c->stream));
     CK(c, cudaMemcpyAsync(s.h, s.d, NRED * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaEventRecord(s.ev, c->stream));
     s.t = c->t;
@@ -852,10 +945,15 @@ int batch_build(lbd_batch *b) {
         BCK(b, cudaMemcpyAsync(b->args_dev[p], host.data(), bytes, cudaMemcpyHostToDevice, b->stream));
         BCK(b, cudaStreamSynchronize(b->stream));
     }
-    const int bxo = b->tile.bx, seg = b->tile.by;
+    // Periodic instances take stripes of the launch shape's width; with the
+    // 16-byte staged kernel (bx 116) the instances with plates take the stripe
+    // kernel's 118-column stripes.
+    const int seg = b->tile.by;
+    const int w_plain = b->tile.bx, w_walls = b->tile.bx == 116 ? 118 : b->tile.bx;
     std::vector<lbd::BatchItem> items;
     for (int k = 0; k < b->n; ++k) {
         const int nx = b->ctx[k]->grid.nx, ny = b->ctx[k]->grid.ny;
+        const int bxo = (b->ctx[k]->params.flags & LBD_WALLS) ? w_walls : w_plain;
         for (int y0 = 0; y0 < ny; y0 += seg)
             for (int x0 = 0; x0 < nx; x0 += bxo)
                 items.push_back(lbd::BatchItem{k, x0, y0, seg});
@@ -877,23 +975,44 @@ int batch_build(lbd_batch *b) {
     b->n_plain = (int)std::count_if(items.begin(), items.end(), [&](const lbd::BatchItem &u) { return !walls(u); });
     int sms = 0;
     BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
-    const int per_sm = lbd::stripe_batch_ctas_per_sm<T>(bxo + 10);
-    b->ctas = std::min(b->n_plain, sms * per_sm);
-    b->ctas_walls = std::min(b->n_items - b->n_plain, sms * per_sm);
+    const int per_sm_plain = w_plain == 116 ? lbd::vstripe_batch_ctas_per_sm()
+                                            : lbd::stripe_batch_ctas_per_sm<T>(w_plain + 10);
+    const int per_sm_walls = lbd::stripe_batch_ctas_per_sm<T>(w_walls + 10);
+    b->ctas = std::min(b->n_plain, sms * per_sm_plain);
+    b->ctas_walls = std::min(b->n_items - b->n_plain, sms * per_sm_walls);
     batch_drop_graphs(b);
     return LBD_OK;
+}
+
+template <typename T>
+cudaError_t launch_vstripe_batch_if_float(const StepArgs<T> *, const lbd::BatchItem *, int, int,
+                                         const long long *, int, cudaStream_t) {
+    return cudaErrorInvalidValue;
+}
+template <>
+cudaError_t launch_vstripe_batch_if_float<float>(const StepArgs<float> *args,
+                                                 const lbd::BatchItem *items, int n, int ctas,
+                                                 const long long *t_dev, int t_off,
+                                                 cudaStream_t s) {
+    return lbd::launch_vstripe_batch(args, items, n, ctas, t_dev, t_off, s);
 }
 
 template <typename T>
 cudaError_t batch_launch(lbd_batch *b, int parity, int t_off) {
     const StepArgs<T> *args = (const StepArgs<T> *)b->args_dev[parity];
     cudaError_t e = cudaSuccess;
-    if (b->n_plain > 0)
-        e = lbd::launch_stripe_batch<T>(args, b->items_dev, b->n_plain, b->tile.bx + 10, false,
-                                        b->ctas, b->t_dev, t_off, b->stream);
+    const int w_walls = b->tile.bx == 116 ? 118 : b->tile.bx;
+    if (b->n_plain > 0) {
+        if (b->tile.bx == 116)
+            e = launch_vstripe_batch_if_float<T>(args, b->items_dev, b->n_plain, b->ctas, b->t_dev,
+                                                 t_off, b->stream);
+        else
+            e = lbd::launch_stripe_batch<T>(args, b->items_dev, b->n_plain, b->tile.bx + 10,
+                                            false, b->ctas, b->t_dev, t_off, b->stream);
+    }
     if (e == cudaSuccess && b->n_items > b->n_plain)
         e = lbd::launch_stripe_batch<T>(args, b->items_dev + b->n_plain, b->n_items - b->n_plain,
-                                        b->tile.bx + 10, true, b->ctas_walls, b->t_dev, t_off,
+                                        w_walls + 10, true, b->ctas_walls, b->t_dev, t_off,
                                         b->stream);
     return e;
 }
@@ -1017,7 +1136,8 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
         ok &= ok && lbd::dev_malloc((void **)&c->phi[k], fbytes) == cudaSuccess;
         ok &= ok && lbd::dev_malloc((void **)&c->psi[k], fbytes) == cudaSuccess;
     }
-    ok &= ok && lbd::dev_malloc((void **)&c->red_partial, NRED * RED_BLOCKS * sizeof(double)) == cudaSuccess;
+    // block partials plus the FP32 reduction's completion counter (zeroed below)
+    ok &= ok && lbd::dev_malloc((void **)&c->red_partial, (NRED * RED_BLOCKS + 1) * sizeof(double)) == cudaSuccess;
     ok &= ok && lbd::dev_malloc((void **)&c->red_out, NRED * sizeof(double)) == cudaSuccess;
     ok &= ok && lbd::host_malloc((void **)&c->h_red, NRED * sizeof(double)) == cudaSuccess;
     ok &= ok && lbd::dev_malloc((void **)&c->theta, (size_t)((grid->nx + 31) / 32) * grid->ny * 4) == cudaSuccess;
@@ -1025,6 +1145,13 @@ int lbd_create(const lbd_grid *grid, const lbd_params *params, void *stream, lbd
         cudaGetLastError();
         lbd_destroy(c);
         return LBD_ENOMEM;
+    }
+    // the reduction's completion counter starts at zero
+    if (cudaMemsetAsync(c->red_partial + NRED * RED_BLOCKS, 0, sizeof(double), c->stream) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        lbd_destroy(c);
+        return LBD_ECUDA;
     }
     // rest state: g = 0 (f = w_i, rho = 1, u = 0), phi = psi = 0
     for (int k = 0; k < 2; ++k) {
@@ -1368,11 +1495,9 @@ int lbd_diagnostics(lbd_ctx *c, double refx, double refy, lbd_diag *out) {
     lbd::NvtxRange range("lbd_diagnostics");
     CK(c, cudaSetDevice(c->dev));
     const lbd_params &p = c->params;
-    CK(c, launch_reduce_partial(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane,
-                                c->g[c->cur], c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, refx,
-                                refy, c->red_partial, c->stream));
-    reduce_final<<<1, RED_THREADS, 0, c->stream>>>(RED_BLOCKS, c->red_partial, c->red_out);
-    CK(c, cudaGetLastError());
+    CK(c, launch_reduce(p.precision, c->grid.nx, c->grid.ny, c->pitch, c->plane, c->g[c->cur],
+                        c->phi[c->cur], c->psi[c->cur], p.B0, p.B1, refx, refy, c->red_partial,
+                        c->red_out, c->stream));
     CK(c, cudaMemcpyAsync(c->h_red, c->red_out, NRED * sizeof(double), cudaMemcpyDeviceToHost,
                           c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -1549,14 +1674,12 @@ int lbd_diagnostics_static(int32_t nx, int32_t ny, int64_t pitch, int32_t precis
         cudaGetLastError();
         return LBD_ECUDA;
     }
-    double *partial = scratch, *res = scratch + NRED * RED_BLOCKS;
+    double *partial = scratch, *res = scratch + NRED * RED_BLOCKS + 1;
     cudaStream_t s = (cudaStream_t)stream;
     const long long plane = (long long)pitch * ny;
-    if (launch_reduce_partial(precision, nx, ny, pitch, plane, g, phi, psi, B0, B1, ref_x, ref_y,
-                              partial, s) != cudaSuccess)
+    if (launch_reduce(precision, nx, ny, pitch, plane, g, phi, psi, B0, B1, ref_x, ref_y, partial,
+                      res, s) != cudaSuccess)
         return LBD_ECUDA;
-    reduce_final<<<1, RED_THREADS, 0, s>>>(RED_BLOCKS, partial, res);
-    if (cudaGetLastError() != cudaSuccess) return LBD_ECUDA;
     double r[NRED];
     if (cudaMemcpyAsync(r, res, sizeof r, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
@@ -1642,6 +1765,15 @@ int lbd_batch_create(int32_t n, const lbd_grid *grids, const lbd_params *params,
             lbd_batch_destroy(b);
             return LBD_EINVAL;
         }
+    // FP32 batches whose periodic instances are all 4k wide start on the 16-byte
+    // staged stripe kernel (lbd_batch_autotune refines the choice)
+    if (b->prec == LBD_FP32) {
+        bool all = true;
+        for (lbd_ctx *c : b->ctx)
+            if (!(c->params.flags & LBD_WALLS))
+                all &= lbd::tile_valid(Tile{116, 64}, true, c->grid.nx, c->plane);
+        if (all) b->tile = Tile{116, 64};
+    }
     if (lbd::dev_malloc((void **)&b->t_dev, sizeof(long long)) != cudaSuccess) {
         cudaGetLastError();
         lbd_batch_destroy(b);
@@ -1687,11 +1819,16 @@ int lbd_batch_step(lbd_batch *b, int64_t nsteps) {
 
 int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by) {
     if (!b) return LBD_EINVAL;
-    if (!((bx == 118 || bx == 246) && (by == 32 || by == 64 || by == 128)))
-        return bfail(b, LBD_EINVAL, "batched steps use the stripe kernel: bx 118 or 246, by 32, 64 or 128");
-    for (lbd_ctx *c : b->ctx)
-        if (!lbd::tile_valid(Tile{bx, by}, b->prec == LBD_FP32, c->grid.nx, c->plane))
-            return bfail(b, LBD_EINVAL, "an instance is too large for the batched stripe kernel");
+    if (!((bx == 118 || bx == 246 || bx == 116) && (by == 32 || by == 64 || by == 128)))
+        return bfail(b, LBD_EINVAL,
+                     "batched steps use a stripe kernel: bx 116, 118 or 246, by 32, 64 or 128");
+    for (lbd_ctx *c : b->ctx) {
+        // instances with plates run the 118-column stripe kernel under bx 116
+        const bool walls = (c->params.flags & LBD_WALLS) != 0;
+        const Tile t{bx == 116 && walls ? 118 : bx, by};
+        if (!lbd::tile_valid(t, b->prec == LBD_FP32, c->grid.nx, c->plane))
+            return bfail(b, LBD_EINVAL, "launch shape %dx%d is not valid for an instance", bx, by);
+    }
     BCK(b, cudaStreamSynchronize(b->stream));
     b->tile = Tile{bx, by};
     return b->prec == LBD_FP64 ? batch_build<double>(b) : batch_build<float>(b);
@@ -1700,7 +1837,8 @@ int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by) {
 int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by) {
     if (!b || reps < 1) return LBD_EINVAL;
     if (b->sticky) return b->sticky;
-    const Tile cand[] = {{118, 32}, {118, 64}, {118, 128}, {246, 32}, {246, 64}};
+    const Tile cand[] = {{118, 32}, {118, 64}, {118, 128}, {246, 32},
+                         {246, 64}, {116, 32}, {116, 64}, {116, 128}};
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
@@ -1709,6 +1847,10 @@ int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by) {
     int rc = LBD_OK;
     for (const Tile &t : cand) {
         rc = lbd_batch_set_tile(b, t.bx, t.by);
+        if (rc == LBD_EINVAL) {  // not valid for these instances (e.g. 116 with FP64)
+            rc = LBD_OK;
+            continue;
+        }
         if (rc != LBD_OK) break;
         // trial launches read the current buffers and write the others: no state change
         const int parity = b->ctx[0]->cur;
@@ -1741,6 +1883,20 @@ int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by) {
     if (bx) *bx = keep.bx;
     if (by) *by = keep.by;
     return rc;
+}
+
+int lbd_batch_get_tile(const lbd_batch *b, int32_t *bx, int32_t *by) {
+    if (!b) return LBD_EINVAL;
+    if (bx) *bx = b->tile.bx;
+    if (by) *by = b->tile.by;
+    return LBD_OK;
+}
+
+int lbd_get_tile(const lbd_ctx *c, int32_t *bx, int32_t *by) {
+    if (!c) return LBD_EINVAL;
+    if (bx) *bx = c->tile.bx;
+    if (by) *by = c->tile.by;
+    return LBD_OK;
 }
 
 int lbd_batch_synchronize(lbd_batch *b) {

@@ -110,6 +110,11 @@ cudaError_t launch_time_set(long long *t_dev, long long value, cudaStream_t s);
 bool vstripe_supported(int nx, long long plane);
 size_t vstripe_smem_bytes();
 cudaError_t launch_vstripe(const StepArgs<float> &a, int seg, cudaStream_t s);
+// The batched form (periodic FP32 instances; items 116 columns wide) and its
+// resident CTAs per SM.
+cudaError_t launch_vstripe_batch(const StepArgs<float> *args, const BatchItem *items, int n_items,
+                                 int ctas, const long long *t_dev, int t_off, cudaStream_t s);
+int vstripe_batch_ctas_per_sm();
 
 
 // Per-droplet sums (lbd_droplets.cu) on the dense fields of the fields

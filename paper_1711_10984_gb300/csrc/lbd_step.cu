@@ -411,7 +411,7 @@ cudaError_t launch_tile(const StepArgs<T> &a, int mode, cudaStream_t s) {
 
 constexpr Tile kTiles[] = {{32, 8},   {32, 16},  {64, 8},    {32, 32},  {64, 16},
                            {118, 16}, {118, 32}, {118, 64}, {118, 128}, {246, 32},
-                           {246, 64}, {116, 32},  {116, 64}, {116, 128}};
+                           {246, 64}, {116, 32},  {116, 64}, {116, 96},  {116, 128}};
 
 }  // namespace
 

@@ -415,6 +415,35 @@ __global__ void __launch_bounds__(NT, 4) vstripe_kernel(const StepArgs<float> p,
     vstripe_body(p, x0, y0, seg, smem_raw);
 }
 
+// Batched step: a persistent grid walks the work items of periodic FP32
+// instances; the arguments of the item's instance are staged in shared memory
+// with the activity of this step, evaluated from the device step count, so
+// that the launch can be replayed from a CUDA graph.
+__global__ void __launch_bounds__(NT, 4)
+    vstripe_batch_kernel(const StepArgs<float> *args, const BatchItem *items, const int n_items,
+                         const long long *t_dev, const int t_off) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ StepArgs<float> sp;
+    const long long t = *t_dev + t_off;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const BatchItem item = items[it];
+        if (threadIdx.x == 0) {
+            sp = args[item.k];
+            double A = 0.0, g = 0.0;
+            if (t >= sp.t_on) {
+                A = sp.A0 * (double)(t - sp.t_on);
+                A = A < sp.A_max ? A : sp.A_max;
+                g = sp.gamma_on;
+            }
+            sp.A = (float)A;
+            sp.gamma = (float)g;
+        }
+        __syncthreads();
+        vstripe_body(sp, item.x0, item.y0, item.rows, smem_raw);
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 bool vstripe_supported(int nx, long long plane) {
@@ -440,6 +469,38 @@ cudaError_t launch_vstripe(const StepArgs<float> &a, int seg, cudaStream_t s) {
     dim3 grid((a.nx + W - 1) / W, (a.ny + seg - 1) / seg);
     vstripe_kernel<<<grid, NT, smem, s>>>(a, seg);
     return cudaGetLastError();
+}
+
+}  // namespace lbd
+
+namespace lbd {
+
+cudaError_t launch_vstripe_batch(const StepArgs<float> *args, const BatchItem *items, int n_items,
+                                 int ctas, const long long *t_dev, int t_off, cudaStream_t s) {
+    const size_t smem = vstripe_smem_bytes();
+    static unsigned long long configured = 0;  // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(configured & bit)) {
+        e = cudaFuncSetAttribute(vstripe_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        configured |= bit;
+    }
+    vstripe_batch_kernel<<<ctas, NT, smem, s>>>(args, items, n_items, t_dev, t_off);
+    return cudaGetLastError();
+}
+
+int vstripe_batch_ctas_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, vstripe_batch_kernel, NT,
+                                                      vstripe_smem_bytes()) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    return n > 0 ? n : 1;
 }
 
 }  // namespace lbd

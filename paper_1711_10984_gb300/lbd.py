@@ -106,6 +106,10 @@ SIGNATURES = {
     "lbd_batch_autotune": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_int32)]),
     "lbd_batch_synchronize": (ctypes.c_int, [_P]),
+    "lbd_batch_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_int32)]),
+    "lbd_get_tile": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.POINTER(ctypes.c_int32)]),
     "lbd_batch_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "lbd_batch_destroy": (None, [_P]),
     "lbd_get_time": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
@@ -314,6 +318,13 @@ class Sim:
     def synchronize(self):
         self._check(load().lbd_synchronize(self._h))
 
+    @property
+    def tile(self):
+        """The current launch shape (bx, by)."""
+        bx, by = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().lbd_get_tile(self._h, ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
+
     def close(self):
         if self._h:
             load().lbd_destroy(self._h)
@@ -380,6 +391,13 @@ class Batch:
 
     def synchronize(self):
         self._check(load().lbd_batch_synchronize(self._h))
+
+    @property
+    def tile(self):
+        """The current launch shape (bx, by)."""
+        bx, by = ctypes.c_int32(), ctypes.c_int32()
+        self._check(load().lbd_batch_get_tile(self._h, ctypes.byref(bx), ctypes.byref(by)))
+        return bx.value, by.value
 
     @property
     def t(self):

@@ -1,7 +1,7 @@
 """Run one of the seeded droplet workloads from the command line.
 
     python -m paper_1711_10984_gb300.run_case --workload emulsion --n 2048 \
-        --precision fp32 --steps 10 [--tile 32x16]
+        --precision fp32 --steps 10 [--tile 32x16] [--check-every 20]
     python -m paper_1711_10984_gb300.run_case --workload emulsion3 --n 128 \
         --droplets 8 --radius 12 --steps 7          (the 3D step on an n^3 box)
     python -m paper_1711_10984_gb300.run_case --workload adjoint --n 256 \
@@ -37,6 +37,8 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--tile", default=None)
     ap.add_argument("--ckpt", type=int, default=100, help="adjoint: checkpoint interval")
+    ap.add_argument("--check-every", type=int, default=0,
+                    help="run-time checks (the S8 reduction) every k steps (lbd_set_check)")
     a = ap.parse_args(argv)
     prec = lbd.LBD_FP32 if a.precision == "fp32" else lbd.LBD_FP64
     if a.workload == "emulsion3":
@@ -67,7 +69,9 @@ def main(argv=None):
     if a.tile:
         sim.set_tile(*[int(v) for v in a.tile.split("x")])
     sim.set_fields(w["phi"], w["psi"])
+    sim.set_check(a.check_every)
     sim.step(a.steps)
+    sim.synchronize()
     d = sim.diagnostics(w["droplets"][0]["x"] % w["nx"], w["droplets"][0]["y"] % w["ny"])
     print(json.dumps(d))
     sim.close()

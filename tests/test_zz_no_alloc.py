@@ -82,16 +82,18 @@ def _agree(got, want, prec, what):
 @pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
 def test_static_scratch_diagnostics_match(prec, pad):
     """Two calls in a row on the same state agree with lbd_diagnostics, also with
-    a call on a different (smaller) lattice between them, whose own results
-    must not leak into the next call's; on the legacy stream and on a
-    caller-given stream; with unpadded and padded rows (the padding is NaN, so
-    a read of it would show)."""
+    a call on a different (smaller) lattice in the other precision between
+    them, whose own results must not leak into the next call's (both forms
+    share the one scratch array); on the legacy stream and on a caller-given
+    stream; with unpadded and padded rows (the padding is NaN, so a read of it
+    would show)."""
     torch = pytest.importorskip("torch")
     nx, ny = 200, 150
+    oprec = lbd.LBD_FP32 if prec == lbd.LBD_FP64 else lbd.LBD_FP64
     sim, d = _state(prec, nx, ny, seed=21, steps=120, R=30.0)
-    other, od = _state(prec, 72, 40, seed=5, steps=30, R=12.0)
+    other, od = _state(oprec, 72, 40, seed=5, steps=30, R=12.0)
     bufs, pitch = _device_copy(torch, sim, prec, pad)
-    obufs, opitch = _device_copy(torch, other, prec, 8)
+    obufs, opitch = _device_copy(torch, other, oprec, 8)
     torch.cuda.synchronize()
     L = lbd.load()
     side = torch.cuda.Stream()
@@ -101,8 +103,8 @@ def test_static_scratch_diagnostics_match(prec, pad):
             got1 = _call(L, nx, ny, pitch, prec, bufs, refx, refy, stream)
             _agree(got1, want, prec, "first call")
             owant = other.diagnostics(od["x"], od["y"])
-            ogot = _call(L, 72, 40, opitch, prec, obufs, od["x"], od["y"], stream)
-            _agree(ogot, owant, prec, "other lattice")
+            ogot = _call(L, 72, 40, opitch, oprec, obufs, od["x"], od["y"], stream)
+            _agree(ogot, owant, oprec, "other lattice")
             got2 = _call(L, nx, ny, pitch, prec, bufs, refx, refy, stream)
             _agree(got2, want, prec, "second call")
     sim.close()
