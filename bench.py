@@ -256,32 +256,33 @@ def fp64_peak_measured(lbd):
 
 def time_e2e(torch, lbd, autotune, w, steps, stream, dev_name):
     """The same FP32 job through the public API from pinned host memory, in the
-    headline's launch shape and diagnostics cadence: upload phi, psi (H2D,
-    lbd_set_fields), K steps with the S8 reduction every min(100, K) steps (its
-    9 doubles copied D2H each time), then all five fields read back (D2H,
-    lbd_get_fields)."""
+    headline's launch shape and diagnostics cadence: upload phi, psi as floats
+    (H2D, lbd_set_fields_f32), K steps with the S8 reduction every min(100, K)
+    steps (its 9 doubles copied D2H each time), then all five fields read back
+    as floats (D2H, lbd_get_fields_f32)."""
     n = w["nx"]
     N = n * n
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-    phi_h, psi_h = pin(w["phi"]), pin(w["psi"])
-    outs = [torch.empty(N, dtype=torch.float64).pin_memory().numpy() for _ in range(5)]
+    phi_h = pin(np.asarray(w["phi"], dtype=np.float32))
+    psi_h = pin(np.asarray(w["psi"], dtype=np.float32))
+    outs = [torch.empty(N, dtype=torch.float32).pin_memory().numpy() for _ in range(5)]
     sim = lbd.Sim(n, n, precision=lbd.LBD_FP32, sources=w["sources"], stream=stream.cuda_stream,
                   **w["params"])
     autotune.tune(sim, dev_name)
     every = min(DIAG_EVERY, steps)
-    sim.set_fields(phi_h, psi_h)  # untimed first call (allocates the staging area)
+    sim.set_fields_f32(phi_h, psi_h)  # untimed first call (allocates the staging areas)
     sim.set_check(every)
     sim.step(2)
     sim.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record(stream)
-    sim.set_fields(phi_h, psi_h)
+    sim.set_fields_f32(phi_h, psi_h)
     t_start = sim.t
     sim.step(steps)
     import ctypes
-    dp = ctypes.POINTER(ctypes.c_double)
-    rc = lbd.load().lbd_get_fields(sim._h, *[o.ctypes.data_as(dp) for o in outs])
+    fp = ctypes.POINTER(ctypes.c_float)
+    rc = lbd.load().lbd_get_fields_f32(sim._h, *[o.ctypes.data_as(fp) for o in outs])
     e1.record(stream)
     e1.synchronize()
     wall = time.perf_counter() - t0
@@ -290,7 +291,7 @@ def time_e2e(torch, lbd, autotune, w, steps, stream, dev_name):
     checks = (t_start + steps) // every - t_start // every
     sim.close()
     ms = max(e0.elapsed_time(e1), wall * 1e3)
-    return dict(ms=ms, h2d=2 * 8 * N, d2h=5 * 8 * N + 9 * 8 * checks, every=every)
+    return dict(ms=ms, h2d=2 * 4 * N, d2h=5 * 4 * N + 9 * 8 * checks, every=every)
 
 
 def time_batch(torch, lbd, steps, warmup, count=256):
@@ -598,10 +599,10 @@ def run_ours(args):
         "e2e": {"value": round(world * N * args.steps / te / 1e3, 1), "unit": "MLUPS",
                 "h2d_bytes_per_step": e2e["h2d"] / args.steps,
                 "d2h_bytes_per_step": e2e["d2h"] / args.steps,
-                "what": "one job of K=%d steps through the C ABI: lbd_set_fields from pinned "
-                        "host phi/psi, lbd_step(K) with the S8 reduction every %d steps (its 9 "
-                        "doubles copied to pinned host memory), lbd_get_fields of rho, u, phi, "
-                        "psi to pinned host" % (args.steps, e2e["every"])},
+                "what": "one job of K=%d steps through the C ABI: lbd_set_fields_f32 from "
+                        "pinned host float phi/psi, lbd_step(K) with the S8 reduction every %d "
+                        "steps (its 9 doubles copied to pinned host memory), lbd_get_fields_f32 "
+                        "of rho, u, phi, psi to pinned host floats" % (args.steps, e2e["every"])},
         "clocks": clk,
         "gpu_launches": r32["launches"],
     }

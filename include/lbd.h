@@ -133,6 +133,14 @@ int lbd_set_params(lbd_ctx *ctx, const lbd_params *params);
 int lbd_set_fields(lbd_ctx *ctx, const double *rho, const double *ux, const double *uy,
                    const double *phi, const double *psi);
 
+/* lbd_set_fields with host arrays of nx*ny floats: the values are widened to
+ * double on the device (exactly), then everything is as for lbd_set_fields.
+ * Half the host-to-device bytes; meant for FP32 contexts, whose state holds no
+ * more than float precision anyway.  Allocates a float staging area of 5*nx*ny
+ * floats on first use (LBD_ENOMEM if that fails).  Synchronises. */
+int lbd_set_fields_f32(lbd_ctx *ctx, const float *rho, const float *ux, const float *uy,
+                       const float *phi, const float *psi);
+
 /* Advance nsteps >= 0 coupled time steps (asynchronous on the stream).  With
  * run-time checks on (lbd_set_check), returns LBD_ENONFINITE or LBD_EUNSTABLE
  * once a check has found the state broken (message in lbd_last_error); the
@@ -154,6 +162,13 @@ int lbd_set_check(lbd_ctx *ctx, int64_t every);
  * be NULL).  u is Eq. (11): (sum_i f_i e_i + F/2) / rho with the force of the
  * current phi, psi.  Synchronises the stream. */
 int lbd_get_fields(lbd_ctx *ctx, double *rho, double *ux, double *uy, double *phi, double *psi);
+
+/* lbd_get_fields into host arrays of nx*ny floats (the values of lbd_get_fields
+ * rounded to float; for an FP32 context rho and u are computed in float and phi,
+ * psi are stored in float, so nothing is lost).  Half the device-to-host bytes.
+ * Allocates the float staging area of lbd_set_fields_f32 on first use.  NULL
+ * skips a field.  Synchronises. */
+int lbd_get_fields_f32(lbd_ctx *ctx, float *rho, float *ux, float *uy, float *phi, float *psi);
 
 /* One droplet of a seeded initial state (lbd_init_droplets). */
 typedef struct {

@@ -8,6 +8,7 @@
 #include <atomic>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbd_internal.h"
@@ -36,6 +37,7 @@ struct lbd_ctx {
     void *psi[2] = {nullptr, nullptr};
     int cur = 0;
     double *staging = nullptr;   // dense doubles, 5*N
+    float *staging32 = nullptr;  // dense floats, 5*N (FP32 host I/O, on demand)
     double *pop_staging = nullptr;  // dense doubles, 9*N (on demand)
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
     uint32_t *theta = nullptr;      // source indicator, one bit per site
@@ -192,6 +194,27 @@ __global__ void init_kernel(int nx, int ny, long long pitch, long long plane, co
     }
 }
 
+// The rest state rho = 1, u = 0 with the uploaded phi, psi: f_i^eq(1, 0) = w_i, so
+// every deviation g_i is exactly +0 (the value init_kernel's formula gives for
+// rho = 1, u = 0, bit for bit), plates or not.  Nothing is written unless *bad
+// holds no invalid site.
+template <typename T>
+__global__ void init_rest_kernel(int nx, int ny, long long pitch, long long plane, const double *phi,
+                                 const double *psi, const unsigned long long *bad, T *g, T *phi_o,
+                                 T *psi_o) {
+    if (*bad != ~0ull) return;
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(s / nx), x = (int)(s - (long long)y * nx);
+        const long long o = (long long)y * pitch + x;
+        phi_o[o] = (T)phi[s];
+        psi_o[o] = (T)psi[s];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i * plane + o] = T(0);
+    }
+}
+
 struct DropInits {
     lbd_droplet_init d[LBD_MAX_DROPLETS];
 };
@@ -236,6 +259,12 @@ __global__ void init_droplets_kernel(int nx, int ny, long long pitch, int n, Dro
         }
         psi[o] = (T)c;
     }
+}
+
+__global__ void to_double_kernel(long long n, const float *a, double *b) {
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
+         s += (long long)gridDim.x * blockDim.x)
+        b[s] = (double)a[s];
 }
 
 __global__ void to_float_kernel(long long n, const double *a, float *b) {
@@ -860,6 +889,17 @@ int ensure_staging(lbd_ctx *c) {
     return LBD_OK;
 }
 
+int ensure_staging32(lbd_ctx *c) {
+    if (c->staging32) return LBD_OK;
+    if (lbd::dev_malloc((void **)&c->staging32, 5 * c->N * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        c->staging32 = nullptr;
+        return fail(c, LBD_ENOMEM, "float staging allocation of %zu bytes failed",
+                    5 * c->N * sizeof(float));
+    }
+    return LBD_OK;
+}
+
 int grid_for(size_t n) {
     size_t b = (n + 255) / 256;
     return (int)(b < 4096 ? (b ? b : 1) : 4096);
@@ -1088,6 +1128,7 @@ void lbd_destroy(lbd_ctx *c) {
         cudaFree(c->psi[k]);
     }
     cudaFree(c->staging);
+    cudaFree(c->staging32);
     cudaFree(c->pop_staging);
     cudaFree(c->drop_dev);
     cudaFreeHost(c->h_drop);
@@ -1208,8 +1249,16 @@ int lbd_set_params(lbd_ctx *c, const lbd_params *p) {
     return update_theta(c);
 }
 
-int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double *uy,
-                   const double *phi, const double *psi) {
+}  // extern "C"
+
+namespace {
+// Upload the host fields (element type In: double or float) into the dense
+// double staging area, validate them there and build the state only if every
+// site is valid (the state is left as it was otherwise).  Float input is
+// copied as is and widened on the device (exact).
+template <typename In>
+int set_fields_impl(lbd_ctx *c, const In *rho, const In *ux, const In *uy, const In *phi,
+                    const In *psi) {
     if (!c) return LBD_EINVAL;
     if (c->sticky) return c->sticky;
     if (!phi || !psi) return fail(c, LBD_EINVAL, "phi and psi are required");
@@ -1217,30 +1266,57 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
     const lbd_params &p = c->params;
     int rc = ensure_staging(c);
     if (rc != LBD_OK) return rc;
+    constexpr bool F32 = std::is_same<In, float>::value;
+    if (F32) {
+        rc = ensure_staging32(c);
+        if (rc != LBD_OK) return rc;
+    }
     CK(c, cudaSetDevice(c->dev));
-    // upload into the staging area, validate there, and build the state only if
-    // every site is valid (the state is left as it was otherwise)
     double *d = c->staging;
     unsigned long long *bad = reinterpret_cast<unsigned long long *>(d + 5 * N);
     const size_t B = N * sizeof(double);
     const int nb = grid_for(N);
+    // without rho and u the populations are the rest state: no equilibrium to evaluate
+    const bool rest = !rho && !ux && !uy;
+    auto upload = [&](const In *h, int k) -> int {
+        if (F32) {
+            float *t = c->staging32 + k * N;
+            CK(c, cudaMemcpyAsync(t, h, N * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+            to_double_kernel<<<nb, 256, 0, c->stream>>>((long long)N, t, d + k * N);
+            CK(c, cudaGetLastError());
+        } else {
+            CK(c, cudaMemcpyAsync(d + k * N, h, B, cudaMemcpyHostToDevice, c->stream));
+        }
+        return LBD_OK;
+    };
     CK(c, cudaMemsetAsync(bad, 0xFF, sizeof *bad, c->stream));
-    if (rho) CK(c, cudaMemcpyAsync(d, rho, B, cudaMemcpyHostToDevice, c->stream));
-    else {
+    if (rho) {
+        if ((rc = upload(rho, 0)) != LBD_OK) return rc;
+    } else if (!rest) {
         fill_kernel<<<nb, 256, 0, c->stream>>>(d, (long long)N, 1.0);
         CK(c, cudaGetLastError());
     }
-    if (ux) CK(c, cudaMemcpyAsync(d + N, ux, B, cudaMemcpyHostToDevice, c->stream));
-    else CK(c, cudaMemsetAsync(d + N, 0, B, c->stream));
-    if (uy) CK(c, cudaMemcpyAsync(d + 2 * N, uy, B, cudaMemcpyHostToDevice, c->stream));
-    else CK(c, cudaMemsetAsync(d + 2 * N, 0, B, c->stream));
-    CK(c, cudaMemcpyAsync(d + 3 * N, phi, B, cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaMemcpyAsync(d + 4 * N, psi, B, cudaMemcpyHostToDevice, c->stream));
+    if (ux) {
+        if ((rc = upload(ux, 1)) != LBD_OK) return rc;
+    } else if (!rest) CK(c, cudaMemsetAsync(d + N, 0, B, c->stream));
+    if (uy) {
+        if ((rc = upload(uy, 2)) != LBD_OK) return rc;
+    } else if (!rest) CK(c, cudaMemsetAsync(d + 2 * N, 0, B, c->stream));
+    if ((rc = upload(phi, 3)) != LBD_OK) return rc;
+    if ((rc = upload(psi, 4)) != LBD_OK) return rc;
     check_fields_kernel<<<nb, 256, 0, c->stream>>>((long long)N, d, d + N, d + 2 * N, d + 3 * N,
                                                    d + 4 * N, rho != nullptr, ux != nullptr,
                                                    uy != nullptr, p.B0, p.B1, bad);
     CK(c, cudaGetLastError());
-    if (p.precision == LBD_FP64)
+    if (rest && p.precision == LBD_FP64)
+        init_rest_kernel<double><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, d + 3 * N, d + 4 * N, bad,
+            (double *)c->g[c->cur], (double *)c->phi[c->cur], (double *)c->psi[c->cur]);
+    else if (rest)
+        init_rest_kernel<float><<<nb, 256, 0, c->stream>>>(
+            c->grid.nx, c->grid.ny, c->pitch, c->plane, d + 3 * N, d + 4 * N, bad,
+            (float *)c->g[c->cur], (float *)c->phi[c->cur], (float *)c->psi[c->cur]);
+    else if (p.precision == LBD_FP64)
         init_kernel<double><<<nb, 256, 0, c->stream>>>(
             c->grid.nx, c->grid.ny, c->pitch, c->plane, d, d + N, d + 2 * N, d + 3 * N, d + 4 * N,
             (p.flags & LBD_WALLS) ? 1 : 0, bad, (double *)c->g[c->cur], (double *)c->phi[c->cur],
@@ -1267,6 +1343,19 @@ int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double
         }
     }
     return LBD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int lbd_set_fields(lbd_ctx *c, const double *rho, const double *ux, const double *uy,
+                   const double *phi, const double *psi) {
+    return set_fields_impl<double>(c, rho, ux, uy, phi, psi);
+}
+
+int lbd_set_fields_f32(lbd_ctx *c, const float *rho, const float *ux, const float *uy,
+                       const float *phi, const float *psi) {
+    return set_fields_impl<float>(c, rho, ux, uy, phi, psi);
 }
 
 int lbd_step(lbd_ctx *c, int64_t n) {
@@ -1360,6 +1449,26 @@ int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi,
         if (outs[k])
             CK(c, cudaMemcpyAsync(outs[k], d + k * N, N * sizeof(double), cudaMemcpyDeviceToHost,
                                   c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBD_OK;
+}
+
+int lbd_get_fields_f32(lbd_ctx *c, float *rho, float *ux, float *uy, float *phi, float *psi) {
+    if (!c) return LBD_EINVAL;
+    if (c->sticky) return c->sticky;
+    int rc = eval_fields(c);
+    if (rc == LBD_OK) rc = ensure_staging32(c);
+    if (rc != LBD_OK) return rc;
+    const size_t N = c->N;
+    float *outs[5] = {rho, ux, uy, phi, psi};
+    for (int k = 0; k < 5; ++k)
+        if (outs[k]) {
+            to_float_kernel<<<grid_for(N), 256, 0, c->stream>>>((long long)N, c->staging + k * N,
+                                                              c->staging32 + k * N);
+            CK(c, cudaGetLastError());
+            CK(c, cudaMemcpyAsync(outs[k], c->staging32 + k * N, N * sizeof(float),
+                                  cudaMemcpyDeviceToHost, c->stream));
+        }
     CK(c, cudaStreamSynchronize(c->stream));
     return LBD_OK;
 }

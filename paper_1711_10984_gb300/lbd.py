@@ -20,6 +20,7 @@ LBD_FROZEN_U, LBD_BODY_FORCE, LBD_WALLS = 1, 2, 16
 LBD_MAX_SOURCES = 64
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
 
 
 class lbd_grid(ctypes.Structure):
@@ -71,6 +72,8 @@ SIGNATURES = {
     "lbd_set_fields": (ctypes.c_int, [_P, _dp, _dp, _dp, _dp, _dp]),
     "lbd_step": (ctypes.c_int, [_P, ctypes.c_int64]),
     "lbd_get_fields": (ctypes.c_int, [_P, _dp, _dp, _dp, _dp, _dp]),
+    "lbd_set_fields_f32": (ctypes.c_int, [_P, _fp, _fp, _fp, _fp, _fp]),
+    "lbd_get_fields_f32": (ctypes.c_int, [_P, _fp, _fp, _fp, _fp, _fp]),
     "lbd_get_populations": (ctypes.c_int, [_P, _dp]),
     "lbd_diagnostics": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(lbd_diag)]),
@@ -214,6 +217,24 @@ class Sim:
     def step(self, n=1):
         self._check(load().lbd_step(self._h, int(n)))
         return self
+
+    def set_fields_f32(self, phi, psi, rho=None, ux=None, uy=None):
+        """lbd_set_fields_f32: the fields as float32 host arrays."""
+        def arr(a):
+            if a is None:
+                return None, None
+            a = np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+            if a.size != self.N:
+                raise ValueError("expected %d values" % self.N)
+            return a, a.ctypes.data_as(_fp)
+        arrs = [arr(a) for a in (rho, ux, uy, phi, psi)]
+        self._check(load().lbd_set_fields_f32(self._h, *[q for _, q in arrs]))
+
+    def fields_f32(self):
+        """lbd_get_fields_f32: (rho, ux, uy, phi, psi) as (ny, nx) float32 arrays."""
+        out = [np.empty(self.N, dtype=np.float32) for _ in range(5)]
+        self._check(load().lbd_get_fields_f32(self._h, *[o.ctypes.data_as(_fp) for o in out]))
+        return tuple(o.reshape(self.ny, self.nx) for o in out)
 
     def fields(self):
         """(rho, ux, uy, phi, psi) as (ny, nx) float64 arrays."""

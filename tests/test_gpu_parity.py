@@ -290,3 +290,84 @@ def test_error_paths():
     sim.set_fields(phi, psi)
     sim.step(3)
     assert sim.t == 3
+
+
+@pytest.mark.parametrize("flags", [0, lbd.LBD_WALLS], ids=["periodic", "plates"])
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
+def test_rest_state_upload_equals_explicit_rest(prec, flags):
+    """set_fields without rho and u builds the rest state directly (g = 0); it is
+    bit-identical to uploading rho = 1, u = 0 explicitly (the equilibrium
+    formula), before and after steps."""
+    nx, ny = 60, 44
+    d, phi, psi = droplet(nx, ny, seed=12)
+    sims = []
+    for explicit in (False, True):
+        sim = lbd.Sim(nx, ny, precision=prec, flags=flags, **dict(ACTIVE, t_on=0))
+        if explicit:
+            sim.set_fields(phi, psi, rho=np.ones((ny, nx)), ux=np.zeros((ny, nx)),
+                           uy=np.zeros((ny, nx)))
+        else:
+            sim.set_fields(phi, psi)
+        sims.append(sim)
+    assert np.array_equal(sims[0].populations(), sims[1].populations())
+    for s in sims:
+        s.step(30)
+    for a, b in zip(sims[0].fields(), sims[1].fields()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(sims[0].populations(), sims[1].populations())
+
+
+@pytest.mark.parametrize("prec", [lbd.LBD_FP64, lbd.LBD_FP32])
+def test_float_upload_and_readback(prec):
+    """lbd_set_fields_f32 of float values equals lbd_set_fields of the same values
+    held as doubles (the widening is exact), bit for bit, with and without rho
+    and u; lbd_get_fields_f32 returns lbd_get_fields rounded to float."""
+    nx, ny = 76, 50
+    d, phi, psi = droplet(nx, ny, seed=21)
+    rng = np.random.default_rng(5)
+    f32 = lambda a: np.asarray(a, dtype=np.float32)
+    phi32, psi32 = f32(phi), f32(psi)
+    rho32 = f32(1 + 0.01 * rng.standard_normal((ny, nx)))
+    u32 = [f32(0.01 * rng.standard_normal((ny, nx))) for _ in range(2)]
+    for with_u in (False, True):
+        sims = []
+        for use_f32 in (False, True):
+            sim = lbd.Sim(nx, ny, precision=prec, **dict(ACTIVE, t_on=0))
+            kw = dict(rho=rho32, ux=u32[0], uy=u32[1]) if with_u else {}
+            if use_f32:
+                sim.set_fields_f32(phi32, psi32, **kw)
+            else:
+                sim.set_fields(phi32.astype(np.float64), psi32.astype(np.float64),
+                               **{k: v.astype(np.float64) for k, v in kw.items()})
+            sims.append(sim)
+        assert np.array_equal(sims[0].populations(), sims[1].populations())
+        for s in sims:
+            s.step(25)
+        assert np.array_equal(sims[0].populations(), sims[1].populations())
+        got = sims[1].fields_f32()
+        for a, b in zip(got, sims[1].fields()):
+            assert a.dtype == np.float32
+            assert np.array_equal(a, b.astype(np.float32))
+        if prec == lbd.LBD_FP32:
+            # phi and psi are stored in float: the readback is exact
+            assert np.array_equal(got[3].astype(np.float64), sims[1].fields()[3])
+
+
+def test_float_io_rejects_bad_input():
+    nx, ny = 40, 24
+    sim = lbd.Sim(nx, ny, precision=lbd.LBD_FP32)
+    d, phi, psi = droplet(nx, ny)
+    sim.set_fields_f32(phi, psi)
+    before = sim.fields()
+    bad = np.asarray(phi, dtype=np.float32).copy()
+    bad[3, 5] = np.nan
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields_f32(bad, psi)
+    assert e.value.code == lbd.LBD_ENONFINITE
+    for a, b in zip(sim.fields(), before):
+        assert np.array_equal(a, b)
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields_f32(phi, psi, rho=-np.ones((ny, nx), dtype=np.float32))
+    assert e.value.code == lbd.LBD_EINVAL
+    r = sim.fields_f32()
+    assert np.array_equal(r[3], before[3].astype(np.float32))
