@@ -95,7 +95,7 @@ struct Tile {
 
 // rows per thread of the step kernels (k_lb keeps one: its 19 pulls per site
 // are held in registers across the barrier)
-constexpr int R_CHEM = 1, R_LB = 1, R_ADVECT = 2, R_CHEM2 = 1, R_UPDATE = 1;
+constexpr int R_LB = 1, R_ADVECT = 2;
 
 extern __shared__ __align__(16) unsigned char lbd3_smem[];
 
@@ -125,6 +125,10 @@ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
     return __ffma2_rn(b, make_float2(-1.f, -1.f), a);  // a - b, rounded once
 }
 __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) {
+    return make_double2(a.x + b.x, a.y + b.y);
+}
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) {
     return make_double2(a.x - b.x, a.y - b.y);
 }
@@ -269,6 +273,173 @@ __device__ __forceinline__ void march(const Arg3<T> &p, const T *const (&src)[2 
     cp_wait<0>();
 }
 
+// The z-window form of march for kernels that need the D3Q19 gradient or
+// Laplacian of ring fields (and nothing else of the neighbours).  The 19-point
+// stencil splits into per-plane sums over the in-plane 3 x 3 neighbourhood
+// (ZWin below), so each plane is read once, when it arrives, and a thread
+// keeps the sums of the two planes before it in registers: at the arrival of
+// plane k the output is plane k - 1.  The ring holds the arriving plane and
+// AHEAD planes in flight.  arrive(nb, out, x, y, z, s) receives the arriving
+// plane's neighbourhood (nb.pair(f, ex, ey), nb.one(f, ex, ey)); out says
+// whether plane z = k - 1 (element offset s) is one of the CTA's planes;
+// pre(x, y, z, s) runs for that plane before the wait.
+constexpr int ZSLOTS = 1 + AHEAD;
+
+template <int NP, int NS>
+constexpr size_t zring_bytes(size_t esz) {
+    return (size_t)(2 * NP + NS) * ZSLOTS * Tile<1>::HP * esz;
+}
+
+template <typename T>
+struct ZNb {
+    const V2<T> *pp;
+    const T *ps;
+    int o;
+    __device__ V2<T> pair(int f, int ex, int ey) const {
+        return pp[f * ZSLOTS * Tile<1>::HP + o + ey * HX + ex];
+    }
+    __device__ T one(int f, int ex, int ey) const {
+        return ps[f * ZSLOTS * Tile<1>::HP + o + ey * HX + ex];
+    }
+};
+
+template <typename T, int NP, int NS, class Pre, class Arrive>
+__device__ __forceinline__ void march_zw(const Arg3<T> &p, const T *const (&src)[2 * NP + NS],
+                                         Pre pre, Arrive arrive) {
+    constexpr int HP = Tile<1>::HP, LPT = Tile<1>::LPT;
+    constexpr int SINGLES = 2 * NP * ZSLOTS * HP;
+    const int nx = p.nx, ny = p.ny, nz = p.nz;
+    T *sm = reinterpret_cast<T *>(lbd3_smem);
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * p.zl;
+    const int z1 = min(nz, z0 + p.zl);
+    const int x = x0 + tid % TX, y = y0 + tid / TX;
+    const unsigned pitch = (unsigned)p.pitch, plane = (unsigned)p.plane;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(sm);
+    unsigned hxy[LPT];
+#pragma unroll
+    for (int j = 0; j < LPT; ++j) {
+        const int e = tid + j * NT;
+        int gx = (x0 + e % HX - 1) % nx, gy = (y0 + e / HX - 1) % ny;
+        gx += gx < 0 ? nx : 0;
+        gy += gy < 0 ? ny : 0;
+        hxy[j] = (unsigned)gy * pitch + (unsigned)gx;
+    }
+    // copy plane k (k in [z0 - 1, z1], periodic) into the slot at element offset o
+    auto issue = [&](int k, int o) {
+        if (k <= z1) {
+            const unsigned zo = (unsigned)(k < 0 ? k + nz : (k >= nz ? k - nz : k)) * plane;
+#pragma unroll
+            for (int j = 0; j < LPT; ++j) {
+                const int e = tid + j * NT;
+                if (e < HP) {
+#pragma unroll
+                    for (int f = 0; f < NP; ++f)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c)
+                            cp_async<sizeof(T)>(
+                                sbase + (unsigned)((2 * (f * ZSLOTS * HP + o + e) + c) * sizeof(T)),
+                                src[2 * f + c] + zo + hxy[j]);
+#pragma unroll
+                    for (int f = 0; f < NS; ++f)
+                        cp_async<sizeof(T)>(
+                            sbase + (unsigned)((SINGLES + f * ZSLOTS * HP + o + e) * sizeof(T)),
+                            src[2 * NP + f] + zo + hxy[j]);
+                }
+            }
+        }
+        cp_commit();
+    };
+    int o[ZSLOTS];  // slot offsets of planes k, k + 1, ..., k + AHEAD - 1, and the free slot
+#pragma unroll
+    for (int q = 0; q < ZSLOTS; ++q) o[q] = q * HP;
+#pragma unroll
+    for (int q = 0; q < ZSLOTS - 1; ++q) issue(z0 - 1 + q, o[q]);
+    const int c = (tid / TX + 1) * HX + tid % TX + 1;
+    const bool in = x < nx && y < ny;
+    for (int k = z0 - 1; k <= z1; ++k) {
+        const bool out = k > z0;
+        const unsigned s = (unsigned)(out ? k - 1 : 0) * plane + (unsigned)y * pitch + (unsigned)x;
+        if (in && out) pre(x, y, k - 1, s);
+        cp_wait<AHEAD - 1>();  // this thread's copies of plane k have landed
+        __syncthreads();       // ... and everyone's; plane k - 1 has been read
+        issue(k + AHEAD, o[ZSLOTS - 1]);
+        ZNb<T> nb;
+        nb.pp = reinterpret_cast<const V2<T> *>(sm) + c;
+        nb.ps = sm + SINGLES + c;
+        nb.o = o[0];
+        if (in) arrive(nb, out, x, y, k - 1, s);
+        const int freed = o[0];
+#pragma unroll
+        for (int q = 0; q < ZSLOTS - 1; ++q) o[q] = o[q + 1];
+        o[ZSLOTS - 1] = freed;
+    }
+    cp_wait<0>();
+}
+
+// Per-plane sums of a pair field for the isotropic D3Q19 gradient and Laplacian
+// (weights 1/18 for the 6 faces, 1/36 for the 12 edges).  For plane z, with C
+// the value at (x, y, z) and the in-plane neighbours x+-1, y+-1 and diagonals:
+//   T  = (x+1) + (x-1) + (y+1) + (y-1) - 4 C,    E  = (four diagonals) - 4 C,
+//   DX = (x+1) - (x-1),   DY = (y+1) - (y-1),
+//   EX = (x+1,y+1) + (x+1,y-1) - (x-1,y+1) - (x-1,y-1),   EY likewise in y.
+// With m, 0, p the planes z - 1, z, z + 1:
+//   d/dx = DX_0 / 6 + (EX_0 + DX_m + DX_p) / 12,   d/dy likewise,
+//   d/dz = (C_p - C_m) / 2 + (T_p - T_m) / 12,
+//   lap  = T_0 / 3 + (E_0 + T_m + T_p) / 6 + (C_p - C_0) - (C_0 - C_m),
+// which is 3 sum_i w_i e_i v_i and 6 sum_i w_i (v_i - v_0) term by term.
+template <typename V, bool GRAD, bool LAP>
+struct ZWin {
+    using S = typename Lane<V>::type;
+    V cm, tm, dxm, dym;                // plane z - 1
+    V c0, t0, dx0, dy0, e0, ex0, ey0;  // plane z
+    __device__ __forceinline__ void reset() {
+        cm = tm = dxm = dym = c0 = t0 = dx0 = dy0 = e0 = ex0 = ey0 = Lane<V>::splat(S(0));
+    }
+    // the arriving plane z + 1 (values from get(ex, ey)); with out, the
+    // gradient and Laplacian at plane z and its centre value
+    template <class Get>
+    __device__ __forceinline__ void arrive(Get get, bool out, V &gx, V &gy, V &gz, V &lap,
+                                           V &mid) {
+        const V c = get(0, 0);
+        const V xp = get(1, 0), xm = get(-1, 0), yp = get(0, 1), ym = get(0, -1);
+        const V pp = get(1, 1), pm = get(1, -1), mp = get(-1, 1), mn = get(-1, -1);
+        const V t = vfma(c, Lane<V>::splat(S(-4)), (xp + xm) + (yp + ym));
+        const V a = pp + pm, b = mp + mn;
+        V e = e0, dx = dx0, dy = dy0, ex = ex0, ey = ey0;
+        if (LAP) e = vfma(c, Lane<V>::splat(S(-4)), a + b);
+        if (GRAD) {
+            dx = xp - xm;
+            dy = yp - ym;
+            ex = a - b;
+            ey = (pp + mp) - (pm + mn);
+        }
+        if (out) {
+            if (GRAD) {
+                gx = vfma(dx0, Lane<V>::splat(S(1) / S(6)), (ex0 + (dxm + dx)) * Lane<V>::splat(S(1) / S(12)));
+                gy = vfma(dy0, Lane<V>::splat(S(1) / S(6)), (ey0 + (dym + dy)) * Lane<V>::splat(S(1) / S(12)));
+                gz = vfma(c - cm, Lane<V>::splat(S(0.5)), (t - tm) * Lane<V>::splat(S(1) / S(12)));
+            }
+            if (LAP)
+                lap = vfma(t0, Lane<V>::splat(S(1) / S(3)),
+                           vfma((e0 + tm) + t, Lane<V>::splat(S(1) / S(6)), (c - c0) - (c0 - cm)));
+            mid = c0;
+        }
+        cm = c0;
+        tm = t0;
+        dxm = dx0;
+        dym = dy0;
+        c0 = c;
+        t0 = t;
+        dx0 = dx;
+        dy0 = dy;
+        e0 = e;
+        ex0 = ex;
+        ey0 = ey;
+    }
+};
+
 // Offsets of the 27 sites around (x, y, z) (periodic), ox/oy/oz index -1, 0, 1;
 // 32-bit (the host keeps 19 * vol below 2^32).
 struct Nb {
@@ -360,19 +531,21 @@ __device__ inline void grad3(const V v[Q], V &gx, V &gy, V &gz) {
     grad_lap(v, gx, gy, gz, lap);
 }
 
-// mu_phi and m at t^n (Eqs. 3, 5); ring: the pair (phi, psi)
+// mu_phi and m at t^n (Eqs. 3, 5); ring: the pair (phi, psi), z-window form
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chem(const Arg3<T> p) {
-    constexpr int ROWS = R_CHEM;
     const T *const src[2] = {p.phi, p.psi};
-    march<T, 1, 0, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int, int, int, unsigned s, const auto &pl) {
-        V2<T> v[Q], gx, gy, gz, lap;
-        gather_pair(pl, 0, v);
-        grad_lap(v, gx, gy, gz, lap);
-        const T ph = v[0].x, c = v[0].y;
-        p.mu[s] = p.a * ph + p.b * (ph * ph * ph) - (p.B0 + p.B1 * c) * lap.x -
-                  p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
-        p.mm[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+    ZWin<V2<T>, true, true> w;
+    w.reset();
+    march_zw<T, 1, 0>(p, src, [](int, int, int, unsigned) {}, [&](const ZNb<T> &nb, bool out, int, int, int, unsigned s) {
+        V2<T> gx, gy, gz, lap, mid;
+        w.arrive([&](int ex, int ey) { return nb.pair(0, ex, ey); }, out, gx, gy, gz, lap, mid);
+        if (out) {
+            const T ph = mid.x, c = mid.y;
+            p.mu[s] = p.a * ph + p.b * (ph * ph * ph) - (p.B0 + p.B1 * c) * lap.x -
+                      p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
+            p.mm[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+        }
     });
 }
 
@@ -468,50 +641,60 @@ __global__ void __launch_bounds__(NT) k_advect(const Arg3<T> p) {
 }
 
 // mu*, m* from phi*, psi* (Eqs. 3, 5), the cubic from phi^n (Eq. 18); ring: the
-// pair (phi*, psi*)
+// pair (phi*, psi*), z-window form
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chem2(const Arg3<T> p) {
-    constexpr int ROWS = R_CHEM2;
     const T *const src[2] = {p.phs, p.pss};
-    march<T, 1, 0, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int, int, int, unsigned s, const auto &pl) {
-        V2<T> v[Q], gx, gy, gz, lap;
-        gather_pair(pl, 0, v);
-        grad_lap(v, gx, gy, gz, lap);
-        const T pn = p.phi[s];
-        p.mus[s] = p.a * v[0].x + p.b * (pn * pn * pn) - (p.B0 + p.B1 * v[0].y) * lap.x -
-                   p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
-        p.mms[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+    ZWin<V2<T>, true, true> w;
+    w.reset();
+    T pn = 0;
+    march_zw<T, 1, 0>(p, src, [&](int, int, int, unsigned s) { pn = p.phi[s]; },
+                      [&](const ZNb<T> &nb, bool out, int, int, int, unsigned s) {
+        V2<T> gx, gy, gz, lap, mid;
+        w.arrive([&](int ex, int ey) { return nb.pair(0, ex, ey); }, out, gx, gy, gz, lap, mid);
+        if (out) {
+            p.mus[s] = p.a * mid.x + p.b * (pn * pn * pn) - (p.B0 + p.B1 * mid.y) * lap.x -
+                       p.B1 * (gx.x * gx.y + gy.x * gy.y + gz.x * gz.y);
+            p.mms[s] = T(0.5) * p.B1 * (gx.x * gx.x + gy.x * gy.x + gz.x * gz.x);
+        }
     });
 }
 
 // phi^{n+1} = phi* + M lap mu* (Eq. 18); psi^{n+1} = psi* + D sum_j 6 w_j
-// [(psi*_j - psi*) + (psi* + psi*_j)(m*_j - m*)/2] - gamma (psi* - c0) + A Theta (Eq. 19)
-// Ring: the pair (psi*, m*) and mu*.
+// [(psi*_j - psi*) + (psi* + psi*_j)(m*_j - m*)/2] - gamma (psi* - c0) + A Theta
+// (Eq. 19).  With L the D3Q19 Laplacian and p* = psi* m*, the link sum is
+// L psi* + (psi* L m* + L p* - m* L psi*) / 2, so that every neighbour term is a
+// linear stencil: z-window form on the pairs (psi*, m*) and (mu*, p*), p* formed
+// from each neighbour's psi* and m*.  Ring: the pair (psi*, m*) and mu*.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_update(const Arg3<T> p) {
-    constexpr int ROWS = R_UPDATE;
     const T *const src[3] = {p.pss, p.mms, p.mus};
-    march<T, 1, 1, ROWS>(p, src, [](int, int, int, unsigned) {}, [=](int x, int y, int z, unsigned s, const auto &pl) {
-        {
-            T v[Q];
-            gather_one(pl, 0, v);
-            T sl = 0;
-#pragma unroll
-            for (int i = 1; i < Q; ++i) sl += (T)wq(i) * (v[i] - v[0]);
-            p.phi_o[s] = p.phs[s] + p.M * (T(6) * sl);
+    ZWin<V2<T>, false, true> wpm, wup;
+    wpm.reset();
+    wup.reset();
+    T phs = 0;
+    uint32_t word = 0;
+    const int words = (p.nx + 31) / 32;
+    march_zw<T, 1, 1>(p, src, [&](int x, int y, int z, unsigned s) {
+        phs = p.phs[s];
+        word = p.theta[((long long)z * p.ny + y) * words + (x >> 5)];
+    }, [&](const ZNb<T> &nb, bool out, int x, int, int, unsigned s) {
+        V2<T> g, lpm, lup, mpm, mup;
+        wpm.arrive([&](int ex, int ey) { return nb.pair(0, ex, ey); }, out, g, g, g, lpm, mpm);
+        wup.arrive([&](int ex, int ey) {
+            const V2<T> q = nb.pair(0, ex, ey);
+            V2<T> r;
+            r.x = nb.one(0, ex, ey);
+            r.y = q.x * q.y;
+            return r;
+        }, out, g, g, g, lup, mup);
+        if (out) {
+            p.phi_o[s] = phs + p.M * lup.x;
+            const T C0 = mpm.x, m0 = mpm.y;
+            const T div = lpm.x + T(0.5) * ((C0 * lpm.y + lup.y) - m0 * lpm.x);
+            const bool bit = (word >> (x & 31)) & 1u;
+            p.psi_o[s] = C0 + (p.D * div - p.gamma * (C0 - p.c0) + (bit ? p.A : T(0)));
         }
-        V2<T> cm[Q];
-        gather_pair(pl, 0, cm);
-        const T C0 = cm[0].x;
-        T div = 0;
-#pragma unroll
-        for (int i = 1; i < Q; ++i) {
-            const V2<T> d = cm[i] - cm[0];  // (psi*_j - psi*, m*_j - m*)
-            div += (T)wq(i) * (d.x + T(0.5) * (C0 + cm[i].x) * d.y);
-        }
-        const int words = (p.nx + 31) / 32;
-        const uint32_t bit = (p.theta[((long long)z * p.ny + y) * words + (x >> 5)] >> (x & 31)) & 1u;
-        p.psi_o[s] = C0 + (p.D * (T(6) * div) - p.gamma * (C0 - p.c0) + (bit ? p.A : T(0)));
     });
 }
 
@@ -864,11 +1047,11 @@ dim3 march_grid(const Arg3<T> &a) {
 template <typename T>
 cudaError_t launch_step3(const Arg3<T> &a, cudaStream_t s) {
     const size_t e = sizeof(T);
-    k_chem<T><<<march_grid<R_CHEM>(a), NT, ring_bytes<1, 0, R_CHEM>(e), s>>>(a);
+    k_chem<T><<<march_grid<1>(a), NT, zring_bytes<1, 0>(e), s>>>(a);
     k_lb<T, 0><<<march_grid<R_LB>(a), NT, ring_bytes<1, 1, R_LB>(e), s>>>(a, nullptr);
     k_advect<T><<<march_grid<R_ADVECT>(a), NT, ring_bytes<1, 3, R_ADVECT>(e), s>>>(a);
-    k_chem2<T><<<march_grid<R_CHEM2>(a), NT, ring_bytes<1, 0, R_CHEM2>(e), s>>>(a);
-    k_update<T><<<march_grid<R_UPDATE>(a), NT, ring_bytes<1, 1, R_UPDATE>(e), s>>>(a);
+    k_chem2<T><<<march_grid<1>(a), NT, zring_bytes<1, 0>(e), s>>>(a);
+    k_update<T><<<march_grid<1>(a), NT, zring_bytes<1, 1>(e), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -876,7 +1059,7 @@ template <typename T>
 cudaError_t launch_fields3(const Arg3<T> &a, const Geo3 &G, double *out, cudaStream_t s) {
     const size_t e = sizeof(T);
     const long long N = (long long)a.nx * a.ny * a.nz;
-    k_chem<T><<<march_grid<R_CHEM>(a), NT, ring_bytes<1, 0, R_CHEM>(e), s>>>(a);
+    k_chem<T><<<march_grid<1>(a), NT, zring_bytes<1, 0>(e), s>>>(a);
     k_lb<T, 1><<<march_grid<R_LB>(a), NT, ring_bytes<1, 1, R_LB>(e), s>>>(a, out);
     k_dense<T><<<1024, 256, 0, s>>>(G, a.phi, a.psi, out + 4 * N, out + 5 * N);
     return cudaGetLastError();
@@ -887,14 +1070,14 @@ template <typename T>
 cudaError_t ring_limits() {
     const size_t e = sizeof(T);
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t r = cudaFuncSetAttribute(k_chem<T>, A, (int)ring_bytes<1, 0, R_CHEM>(e));
+    cudaError_t r = cudaFuncSetAttribute(k_chem<T>, A, (int)zring_bytes<1, 0>(e));
     if (r == cudaSuccess) r = cudaFuncSetAttribute(k_lb<T, 0>, A, (int)ring_bytes<1, 1, R_LB>(e));
     if (r == cudaSuccess) r = cudaFuncSetAttribute(k_lb<T, 1>, A, (int)ring_bytes<1, 1, R_LB>(e));
     if (r == cudaSuccess)
         r = cudaFuncSetAttribute(k_advect<T>, A, (int)ring_bytes<1, 3, R_ADVECT>(e));
-    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_chem2<T>, A, (int)ring_bytes<1, 0, R_CHEM2>(e));
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_chem2<T>, A, (int)zring_bytes<1, 0>(e));
     if (r == cudaSuccess)
-        r = cudaFuncSetAttribute(k_update<T>, A, (int)ring_bytes<1, 1, R_UPDATE>(e));
+        r = cudaFuncSetAttribute(k_update<T>, A, (int)zring_bytes<1, 1>(e));
     return r;
 }
 

@@ -324,7 +324,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
                     const float jx = a13.x + ((g56.x - g56.y) + (g78.y - g78.x));
                     const float jy = a13.y + ((g56.x + g56.y) - (g78.x + g78.y));
                     const float n = 1.f + dn;
-                    const float inv = __frcp_rn(n);
+                    const float inv = __fdividef(1.f, n);  // fast reciprocal, <= 2 ulp
                     const float2 u = vfma(vsplat(0.5f), F, vmake(jx, jy)) * vsplat(inv);
                     ux = u.x;
                     uy = u.y;
