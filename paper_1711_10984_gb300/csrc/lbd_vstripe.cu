@@ -22,6 +22,10 @@
 //    (psi*, p*)) and the population stage are 3 rows deep and the steady loop
 //    is unrolled 3 times, so every slot is a compile-time constant and the
 //    three-row stencil windows in registers advance without register moves.
+//    The (phi^n, psi^n) ring has 12 slots and every row is copied into two,
+//    s and s + 12: the eight rows an iteration reads (y0 - 13 + i ..
+//    y0 - 6 + i) then sit at fixed offsets from one base slot, which advances
+//    by one slot per iteration, with no wrap to compute per read.
 #include <cstdint>
 #include <type_traits>
 
@@ -32,7 +36,7 @@ namespace {
 
 constexpr int NT = 128;       // threads per CTA
 constexpr int W = NT - 12;    // output columns per stripe
-constexpr int LD = 16;        // rows in the (phi^n, psi^n) ring
+constexpr int LD = 12;        // rows in the (phi^n, psi^n) ring (each row stored twice)
 constexpr int R3 = 3;         // rows in the small rings and the population stage
 constexpr int RS = NT + 2;    // ring row: one padding column on each side
 constexpr int PW = NT + 8;    // staged population row: columns x0 - 8 .. x0 + 127
@@ -41,7 +45,7 @@ constexpr int NCP = 3 * NCH;  // copying threads (three planes per source row)
 
 // (phi, psi) ring, four pair rings, the u_x ring, then the population stage on
 // a 128-byte boundary (the 16-byte copies need 16-byte aligned destinations)
-constexpr size_t RING_FLOATS = ((size_t)RS * (2 * LD + 2 * 4 * R3 + R3) + 31) / 32 * 32;
+constexpr size_t RING_FLOATS = ((size_t)RS * (4 * LD + 2 * 4 * R3 + R3) + 31) / 32 * 32;
 constexpr size_t SMEM_FLOATS = RING_FLOATS + (size_t)R3 * 9 * PW;
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -133,7 +137,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
                                              const int seg, unsigned char *smem_raw) {
     const int c = threadIdx.x;
     float2 *const r_ps = reinterpret_cast<float2 *>(smem_raw) + 1 + c;  // [LD] (phi^n, psi^n)
-    float2 *const r_mm = r_ps + LD * RS;                                 // [R3] (mu, m)       A -> B
+    float2 *const r_mm = r_ps + 2 * LD * RS;                                 // [R3] (mu, m)       A -> B
     float2 *const r_st = r_mm + R3 * RS;                                 // [R3] (phi*, psi*)  C -> D
     float2 *const r_ms = r_st + R3 * RS;                                 // [R3] (mu*, m*)     D -> E
     float2 *const r_pp = r_ms + R3 * RS;                                 // [R3] (psi*, p*)    D -> E
@@ -163,6 +167,9 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
         so1 = (unsigned)pB * plane_b + xb;
         so2 = (unsigned)pC * plane_b + xb;
     }
+    const char *const gp0 = reinterpret_cast<const char *>(p.g_in) + so0;
+    const char *const gp1 = reinterpret_cast<const char *>(p.g_in) + so1;
+    const char *const gp2 = reinterpret_cast<const char *>(p.g_in) + so2;
     const int xo = x0 + c - 6;  // output column of this thread
     const bool inE = c >= 6 && c < NT - 6 && xo < nx;
     const unsigned xo_b = (unsigned)xo * 4u;
@@ -184,24 +191,26 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
     // Asynchronous loads of iteration k into stage slot `slot`: (phi^n, psi^n)
     // of loader row y0 - 5 + k, and the populations pulled by stage-B row
     // y0 - 9 + k.
-    auto issue = [&](int k, int slot) {
+    auto issue = [&](int k, int slot, int ws) {
         const int rl = y0 - 5 + k;
         if (rl < yend + 5) {
-            const unsigned so = (unsigned)(((rl - y0) & (LD - 1)) * RS) * 8u;
-            cp4<0>(u_ps + so, phi_in + lo_b);
-            cp4<4>(u_ps + so, psi_in + lo_b);
+            const unsigned so = u_ps + (unsigned)(ws * RS) * 8u;
+            cp4<0>(so, phi_in + lo_b);
+            cp4<4>(so, psi_in + lo_b);
+            cp4<LD * RS * 8>(so, phi_in + lo_b);
+            cp4<LD * RS * 8 + 4>(so, psi_in + lo_b);
         }
         const int rb = y0 - 9 + k;
         if (copier && rb >= y0 - 3 && rb < yend + 3) {
             const unsigned d = u_chunk + (unsigned)(slot * 9 * PW) * 4u;
-            cp16<0 * 3 * PW * 4>(d, g_in + (so0 + rm_b));
-            cp16<1 * 3 * PW * 4>(d, g_in + (so1 + r0_b));
-            cp16<2 * 3 * PW * 4>(d, g_in + (so2 + rp_b));
+            cp16<0 * 3 * PW * 4>(d, gp0 + rm_b);
+            cp16<1 * 3 * PW * 4>(d, gp1 + r0_b);
+            cp16<2 * 3 * PW * 4>(d, gp2 + rp_b);
         }
         cp_commit();
         adv(lo_b);
-        adv(rm_b);
-        adv(r0_b);
+        rm_b = r0_b;
+        r0_b = rp_b;
         adv(rp_b);
     };
 
@@ -218,8 +227,10 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
     char *const phi_out = reinterpret_cast<char *>(p.phi_out);
     char *const psi_out = reinterpret_cast<char *>(p.psi_out);
     const float A_t = p.A, gamma_t = p.gamma;
-    issue(0, 0);
-    issue(1, 1);
+    issue(0, 0, 0);
+    issue(1, 1, 1);
+    // slot of ring row y0 - 13 + i (loader index i - 8) at iteration i
+    int bq = 4;
     const int iters = (yend - y0) + 15;
 
     // One pipeline iteration i (ph = i % 3); with GUARD false every stage is
@@ -228,7 +239,8 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
         constexpr bool GUARD = decltype(guard_tag)::value;
         cp_wait1();
         __syncthreads();
-        issue(i + 2, s3<2>(ph));
+        issue(i + 2, s3<2>(ph), bq < 2 ? bq + 10 : bq - 2);
+        const float2 *const Bp = r_ps + bq * RS;  // rows y0 - 13 + i .. y0 - 6 + i at Bp[j RS]
 
         // ---- E: phi^{n+1} (Eq. 18), psi^{n+1} (Eq. 19 + source, sink), row y0 - 15 + i
         {
@@ -264,7 +276,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
                 phs_e = wD.cm.x;
                 wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);
                 if (!GUARD || i >= 12) {
-                    const float pn = r_ps[((r - y0) & (LD - 1)) * RS].x;
+                    const float pn = Bp[0].x;
                     const float mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
                                       B1 * (gx.x * gx.y + gy.x * gy.y);
                     const float ms = 0.5f * B1 * (gx.x * gx.x + gy.x * gy.x);
@@ -278,9 +290,9 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
         {
             const int r = y0 - 11 + i;
             if (!GUARD || (i >= 9 && r < yend + 2)) {
-                const float2 *Q = r_ps + ((r - y0) & (LD - 1)) * RS;
-                const float2 QN = r_ps[((r + 1 - y0) & (LD - 1)) * RS];
-                const float2 QS = r_ps[((r - 1 - y0) & (LD - 1)) * RS];
+                const float2 *Q = Bp + 2 * RS;
+                const float2 QN = Bp[3 * RS];
+                const float2 QS = Bp[1 * RS];
                 const float *U = r_ux + s3<-11>(ph) * RS;
                 const float uxc = ux2;
                 const float ue = 0.5f * (uxc + U[1]);
@@ -304,7 +316,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
                 float2 gx, gy, mid;
                 wB.push_grad(M1[0], M1[-1], M1[1], gx, gy, mid);
                 if (!GUARD || i >= 6) {
-                    const float2 pp = r_ps[((r - y0) & (LD - 1)) * RS];
+                    const float2 pp = Bp[4 * RS];
                     float2 F = vmake(fmaf(-pp.x, gx.x, fmaf(-pp.y, gx.y, -gps2.x)),
                                      fmaf(-pp.x, gy.x, fmaf(-pp.y, gy.y, -gps2.y)));
                     F = F + vmake(p.fx, p.fy);
@@ -375,7 +387,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
             const int r = y0 - 7 + i;
             float2 gp = vsplat(0.f);
             if (!GUARD || (i >= 1 && r < yend + 4)) {
-                const float2 *F1 = r_ps + ((r + 1 - y0) & (LD - 1)) * RS;
+                const float2 *F1 = Bp + 7 * RS;
                 float2 gx, gy, lap, mid;
                 wA.push(F1[0], F1[-1], F1[1], gx, gy, lap, mid);
                 gp = vmake(gx.y, gy.y);
@@ -389,6 +401,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
             }
             gps2 = gps1; gps1 = gp;
         }
+        bq = bq == LD - 1 ? 0 : bq + 1;
     };
     const std::integral_constant<bool, true> guarded;
     const std::integral_constant<bool, false> steady;
