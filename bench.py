@@ -270,28 +270,34 @@ def time_e2e(torch, lbd, autotune, w, steps, stream, dev_name):
                   **w["params"])
     autotune.tune(sim, dev_name)
     every = min(DIAG_EVERY, steps)
-    sim.set_fields_f32(phi_h, psi_h)  # untimed first call (allocates the staging areas)
-    sim.set_check(every)
-    sim.step(2)
-    sim.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    e0.record(stream)
-    sim.set_fields_f32(phi_h, psi_h)
-    t_start = sim.t
-    sim.step(steps)
     import ctypes
     fp = ctypes.POINTER(ctypes.c_float)
-    rc = lbd.load().lbd_get_fields_f32(sim._h, *[o.ctypes.data_as(fp) for o in outs])
-    e1.record(stream)
-    e1.synchronize()
-    wall = time.perf_counter() - t0
-    sim._check(rc)
+    # one untimed job first: the calls allocate their staging areas on first use
+    sim.set_fields_f32(phi_h, psi_h)
+    sim.set_check(every)
+    sim.step(2)
+    sim._check(lbd.load().lbd_get_fields_f32(sim._h, *[o.ctypes.data_as(fp) for o in outs]))
     sim.synchronize()
-    checks = (t_start + steps) // every - t_start // every
+    times, checks = [], 0
+    for rep in range(3):  # three jobs; the median is reported
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        sim.set_fields_f32(phi_h, psi_h)
+        t_start = sim.t
+        sim.step(steps)
+        rc = lbd.load().lbd_get_fields_f32(sim._h, *[o.ctypes.data_as(fp) for o in outs])
+        e1.record(stream)
+        e1.synchronize()
+        wall = time.perf_counter() - t0
+        sim._check(rc)
+        sim.synchronize()
+        checks = (t_start + steps) // every - t_start // every
+        times.append(max(e0.elapsed_time(e1), wall * 1e3))
     sim.close()
-    ms = max(e0.elapsed_time(e1), wall * 1e3)
-    return dict(ms=ms, h2d=2 * 4 * N, d2h=5 * 4 * N + 9 * 8 * checks, every=every)
+    ms = sorted(times)[1]
+    return dict(ms=ms, h2d=2 * 4 * N, d2h=5 * 4 * N + 9 * 8 * checks, every=every,
+                jobs_ms=[round(t, 4) for t in times])
 
 
 def time_batch(torch, lbd, steps, warmup, count=256):
@@ -602,7 +608,9 @@ def run_ours(args):
                 "what": "one job of K=%d steps through the C ABI: lbd_set_fields_f32 from "
                         "pinned host float phi/psi, lbd_step(K) with the S8 reduction every %d "
                         "steps (its 9 doubles copied to pinned host memory), lbd_get_fields_f32 "
-                        "of rho, u, phi, psi to pinned host floats" % (args.steps, e2e["every"])},
+                        "of rho, u, phi, psi to pinned host floats; median of 3 such jobs, after "
+                        "one untimed job" % (args.steps, e2e["every"]),
+                "jobs_ms": e2e["jobs_ms"]},
         "clocks": clk,
         "gpu_launches": r32["launches"],
     }

@@ -38,6 +38,11 @@ struct lbd_ctx {
     int cur = 0;
     double *staging = nullptr;   // dense doubles, 5*N
     float *staging32 = nullptr;  // dense floats, 5*N (FP32 host I/O, on demand)
+    // a second stream and two events (on demand): lbd_get_fields_f32 reads phi
+    // and psi back on it while rho and u are evaluated on the context's stream
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_main = nullptr, ev_side = nullptr;
+    unsigned long long *word = nullptr;  // verdict of a float rest-state upload (on demand)
     double *pop_staging = nullptr;  // dense doubles, 9*N (on demand)
     double *red_partial = nullptr, *red_out = nullptr, *h_red = nullptr;
     uint32_t *theta = nullptr;      // source indicator, one bit per site
@@ -150,6 +155,27 @@ __global__ void check_fields_kernel(long long N, const double *rho, const double
             code = 2;
         else if (has_rho && !(rho[s] > 0.0))
             code = 3;
+        if (code) atomicMin(first, (unsigned long long)s * 4ull + code);
+    }
+}
+
+// The same test of phi and psi in place, for pitched FP32 planes (rest-state
+// upload of an FP32 context: rho = 1 and u = 0 are valid).  The values are
+// widened to double first, so the verdict is that of check_fields_kernel on the
+// same values.
+__global__ void check_state_kernel(int nx, int ny, long long pitch, const float *phi,
+                                   const float *psi, double B0, double B1,
+                                   unsigned long long *first) {
+    const long long N = (long long)nx * ny;
+    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long y = s / nx, o = y * pitch + (s - y * nx);
+        const double ph = (double)phi[o], ps = (double)psi[o];
+        unsigned code = 0;
+        if (!isfinite(ph) || !isfinite(ps))
+            code = 1;
+        else if (!(ps > 0.0) || !(__dadd_rn(B0, __dmul_rn(B1, ps)) > 0.0))
+            code = 2;
         if (code) atomicMin(first, (unsigned long long)s * 4ull + code);
     }
 }
@@ -900,6 +926,23 @@ int ensure_staging32(lbd_ctx *c) {
     return LBD_OK;
 }
 
+int ensure_side(lbd_ctx *c) {
+    if (c->side) return LBD_OK;
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_main, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_side, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->side) cudaStreamDestroy(c->side);
+        if (c->ev_main) cudaEventDestroy(c->ev_main);
+        if (c->ev_side) cudaEventDestroy(c->ev_side);
+    cudaFree(c->word);
+        c->side = nullptr;
+        c->ev_main = c->ev_side = nullptr;
+        return fail(c, LBD_ECUDA, "stream or event creation failed");
+    }
+    return LBD_OK;
+}
+
 int grid_for(size_t n) {
     size_t b = (n + 255) / 256;
     return (int)(b < 4096 ? (b ? b : 1) : 4096);
@@ -1129,6 +1172,13 @@ void lbd_destroy(lbd_ctx *c) {
     }
     cudaFree(c->staging);
     cudaFree(c->staging32);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_main) cudaEventDestroy(c->ev_main);
+    if (c->ev_side) cudaEventDestroy(c->ev_side);
+    cudaFree(c->word);
     cudaFree(c->pop_staging);
     cudaFree(c->drop_dev);
     cudaFreeHost(c->h_drop);
@@ -1264,9 +1314,44 @@ int set_fields_impl(lbd_ctx *c, const In *rho, const In *ux, const In *uy, const
     if (!phi || !psi) return fail(c, LBD_EINVAL, "phi and psi are required");
     const size_t N = c->N;
     const lbd_params &p = c->params;
+    constexpr bool F32 = std::is_same<In, float>::value;
+    if (F32 && !rho && !ux && !uy && p.precision == LBD_FP32) {
+        // Float phi and psi into an FP32 context's rest state: copied straight
+        // into the second buffer set (scratch between steps), checked there,
+        // and, if every site is valid, copied into the state with g = 0 (the
+        // buffer parity is kept).  Same state and verdicts as the staged path.
+        if (!c->word && lbd::dev_malloc((void **)&c->word, sizeof *c->word) != cudaSuccess) {
+            cudaGetLastError();
+            c->word = nullptr;
+            return fail(c, LBD_ENOMEM, "upload verdict allocation failed");
+        }
+        CK(c, cudaSetDevice(c->dev));
+        const int back = 1 - c->cur;
+        float *ph = (float *)c->phi[back], *ps = (float *)c->psi[back];
+        const size_t w = (size_t)c->grid.nx * sizeof(float), pb = (size_t)c->pitch * sizeof(float);
+        const size_t fb = (size_t)c->plane * sizeof(float);
+        CK(c, cudaMemcpy2DAsync(ph, pb, phi, w, w, c->grid.ny, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemcpy2DAsync(ps, pb, psi, w, w, c->grid.ny, cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaMemsetAsync(c->word, 0xFF, sizeof *c->word, c->stream));
+        check_state_kernel<<<grid_for(N), 256, 0, c->stream>>>(c->grid.nx, c->grid.ny, c->pitch,
+                                                               ph, ps, p.B0, p.B1, c->word);
+        CK(c, cudaGetLastError());
+        unsigned long long first = 0;
+        CK(c, cudaMemcpyAsync(&first, c->word, sizeof first, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (first != ~0ull) {
+            const size_t site = (size_t)(first >> 2);
+            if ((first & 3ull) == 1ull)
+                return fail(c, LBD_ENONFINITE, "non-finite initial value at site %zu", site);
+            return fail(c, LBD_EUNSTABLE, "psi <= 0 or B(psi) <= 0 at site %zu", site);
+        }
+        CK(c, cudaMemcpyAsync(c->phi[c->cur], ph, fb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemcpyAsync(c->psi[c->cur], ps, fb, cudaMemcpyDeviceToDevice, c->stream));
+        CK(c, cudaMemsetAsync(c->g[c->cur], 0, 9 * fb, c->stream));
+        return reset_checks(c);
+    }
     int rc = ensure_staging(c);
     if (rc != LBD_OK) return rc;
-    constexpr bool F32 = std::is_same<In, float>::value;
     if (F32) {
         rc = ensure_staging32(c);
         if (rc != LBD_OK) return rc;
@@ -1456,6 +1541,46 @@ int lbd_get_fields(lbd_ctx *c, double *rho, double *ux, double *uy, double *phi,
 int lbd_get_fields_f32(lbd_ctx *c, float *rho, float *ux, float *uy, float *phi, float *psi) {
     if (!c) return LBD_EINVAL;
     if (c->sticky) return c->sticky;
+    if (c->params.precision == LBD_FP32) {
+        // phi and psi are the state itself: read back on the side stream while
+        // rho and u are evaluated and read back on the context's stream
+        int rc = ensure_side(c);
+        if (rc != LBD_OK) return rc;
+        CK(c, cudaSetDevice(c->dev));
+        const size_t w = (size_t)c->grid.nx * sizeof(float), pb = (size_t)c->pitch * sizeof(float);
+        const bool side = phi || psi;
+        if (side) {
+            CK(c, cudaEventRecord(c->ev_main, c->stream));
+            CK(c, cudaStreamWaitEvent(c->side, c->ev_main, 0));
+            if (phi)
+                CK(c, cudaMemcpy2DAsync(phi, w, c->phi[c->cur], pb, w, c->grid.ny,
+                                        cudaMemcpyDeviceToHost, c->side));
+            if (psi)
+                CK(c, cudaMemcpy2DAsync(psi, w, c->psi[c->cur], pb, w, c->grid.ny,
+                                        cudaMemcpyDeviceToHost, c->side));
+        }
+        if (rho || ux || uy) {
+            rc = eval_fields(c);
+            if (rc == LBD_OK) rc = ensure_staging32(c);
+            const size_t N = c->N;
+            float *outs[3] = {rho, ux, uy};
+            for (int k = 0; k < 3 && rc == LBD_OK; ++k)
+                if (outs[k]) {
+                    to_float_kernel<<<grid_for(N), 256, 0, c->stream>>>(
+                        (long long)N, c->staging + k * N, c->staging32 + k * N);
+                    if (cudaGetLastError() != cudaSuccess ||
+                        cudaMemcpyAsync(outs[k], c->staging32 + k * N, N * sizeof(float),
+                                        cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+                        rc = fail(c, LBD_ECUDA, "field read-back failed");
+                }
+        }
+        // the caller's arrays are complete when this returns, on success or not
+        if (side && cudaStreamSynchronize(c->side) != cudaSuccess && rc == LBD_OK)
+            rc = fail(c, LBD_ECUDA, "field read-back failed");
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess && rc == LBD_OK)
+            rc = fail(c, LBD_ECUDA, "field read-back failed");
+        return rc;
+    }
     int rc = eval_fields(c);
     if (rc == LBD_OK) rc = ensure_staging32(c);
     if (rc != LBD_OK) return rc;

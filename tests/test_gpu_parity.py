@@ -371,3 +371,32 @@ def test_float_io_rejects_bad_input():
     assert e.value.code == lbd.LBD_EINVAL
     r = sim.fields_f32()
     assert np.array_equal(r[3], before[3].astype(np.float32))
+
+
+def test_float_io_fast_paths_fp32():
+    """FP32 context: a float rest-state upload lands in the state only when every
+    site is valid (psi <= 0 -> LBD_EUNSTABLE, state unchanged); the float
+    read-back fills exactly the arrays asked for (NULL skips a field)."""
+    import ctypes
+    nx, ny = 52, 36
+    d, phi, psi = droplet(nx, ny, seed=3)
+    sim = lbd.Sim(nx, ny, precision=lbd.LBD_FP32, **dict(ACTIVE, t_on=0))
+    sim.set_fields_f32(phi, psi)
+    sim.step(7)
+    before, pops = sim.fields(), sim.populations()
+    bad = np.asarray(psi, dtype=np.float32).copy()
+    bad[ny - 1, nx - 1] = -0.5
+    with pytest.raises(lbd.LbdError) as e:
+        sim.set_fields_f32(phi, bad)
+    assert e.value.code == lbd.LBD_EUNSTABLE
+    for a, b in zip(sim.fields(), before):
+        assert np.array_equal(a, b)
+    assert np.array_equal(sim.populations(), pops)
+    fp = ctypes.POINTER(ctypes.c_float)
+    full = sim.fields_f32()
+    outs = [np.full((ny, nx), 7.0, dtype=np.float32) for _ in range(5)]
+    ask = [False, True, False, False, True]
+    ptrs = [o.ctypes.data_as(fp) if a else None for o, a in zip(outs, ask)]
+    assert lbd.load().lbd_get_fields_f32(sim._h, *ptrs) == 0
+    for o, f, a in zip(outs, full, ask):
+        assert np.array_equal(o, f) if a else np.all(o == 7.0)
