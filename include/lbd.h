@@ -134,10 +134,13 @@ int lbd_set_fields(lbd_ctx *ctx, const double *rho, const double *ux, const doub
                    const double *phi, const double *psi);
 
 /* lbd_set_fields with host arrays of nx*ny floats: the values are widened to
- * double on the device (exactly), then everything is as for lbd_set_fields.
- * Half the host-to-device bytes; meant for FP32 contexts, whose state holds no
- * more than float precision anyway.  Allocates a float staging area of 5*nx*ny
- * floats on first use (LBD_ENOMEM if that fails).  Synchronises. */
+ * double on the device (exactly), then everything is as for lbd_set_fields
+ * (same state, same verdicts, state unchanged on a rejected upload).  Half the
+ * host-to-device bytes; meant for FP32 contexts, whose state holds no more than
+ * float precision anyway.  For an FP32 context without rho and u the values go
+ * straight into the context's second buffer set and are checked there (no
+ * staging); otherwise a float staging area of 5*nx*ny floats is allocated on
+ * first use.  LBD_ENOMEM if an allocation fails.  Synchronises. */
 int lbd_set_fields_f32(lbd_ctx *ctx, const float *rho, const float *ux, const float *uy,
                        const float *phi, const float *psi);
 
@@ -166,8 +169,11 @@ int lbd_get_fields(lbd_ctx *ctx, double *rho, double *ux, double *uy, double *ph
 /* lbd_get_fields into host arrays of nx*ny floats (the values of lbd_get_fields
  * rounded to float; for an FP32 context rho and u are computed in float and phi,
  * psi are stored in float, so nothing is lost).  Half the device-to-host bytes.
- * Allocates the float staging area of lbd_set_fields_f32 on first use.  NULL
- * skips a field.  Synchronises. */
+ * For an FP32 context phi and psi are copied from the state on a second stream
+ * that the context creates on first use, while rho and u are evaluated; the
+ * float staging area of lbd_set_fields_f32 is allocated on first use for rho
+ * and u.  NULL skips a field.  All arrays are complete when the call returns.
+ * Synchronises. */
 int lbd_get_fields_f32(lbd_ctx *ctx, float *rho, float *ux, float *uy, float *phi, float *psi);
 
 /* One droplet of a seeded initial state (lbd_init_droplets). */
