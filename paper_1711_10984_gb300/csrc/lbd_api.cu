@@ -1033,21 +1033,45 @@ int batch_build(lbd_batch *b) {
     // kernel's 118-column stripes.
     const int seg = b->tile.by;
     const int w_plain = b->tile.bx, w_walls = b->tile.bx == 116 ? 118 : b->tile.bx;
-    std::vector<lbd::BatchItem> items;
+    std::vector<lbd::BatchItem> plain, walled;
     for (int k = 0; k < b->n; ++k) {
         const int nx = b->ctx[k]->grid.nx, ny = b->ctx[k]->grid.ny;
-        const int bxo = (b->ctx[k]->params.flags & LBD_WALLS) ? w_walls : w_plain;
+        const bool walls = (b->ctx[k]->params.flags & LBD_WALLS) != 0;
+        const int bxo = walls ? w_walls : w_plain;
         for (int y0 = 0; y0 < ny; y0 += seg)
             for (int x0 = 0; x0 < nx; x0 += bxo)
-                items.push_back(lbd::BatchItem{k, x0, y0, seg});
+                (walls ? walled : plain).push_back(lbd::BatchItem{k, x0, y0, std::min(seg, ny - y0)});
     }
-    // periodic instances first (the plates take a launch of their own); within
-    // each, largest lattices first, so that the tail of the persistent walk is short
-    auto walls = [&](const lbd::BatchItem &u) { return (b->ctx[u.k]->params.flags & LBD_WALLS) != 0; };
-    std::stable_sort(items.begin(), items.end(), [&](const lbd::BatchItem &u, const lbd::BatchItem &v) {
-        if (walls(u) != walls(v)) return !walls(u);
-        return b->ctx[u.k]->N > b->ctx[v.k]->N;
-    });
+    int sms = 0;
+    BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
+    const int per_sm_plain = w_plain == 116 ? lbd::vstripe_batch_ctas_per_sm()
+                                            : lbd::stripe_batch_ctas_per_sm<T>(w_plain + 10);
+    const int per_sm_walls = lbd::stripe_batch_ctas_per_sm<T>(w_walls + 10);
+    b->ctas = std::min((int)plain.size(), sms * per_sm_plain);
+    b->ctas_walls = std::min((int)walled.size(), sms * per_sm_walls);
+    // CTA j of a persistent launch takes items j, j + P, j + 2P, ... (P CTAs).
+    // An item costs about its rows plus the pipeline fill, so the items are
+    // sorted by rows, largest first, and dealt in boustrophedon order: CTA j
+    // gets the j-th item of even rounds and the j-th from the end of odd ones,
+    // which evens the CTAs' totals out (greedy longest-first in effect).
+    auto deal = [](std::vector<lbd::BatchItem> &v, int P) {
+        std::stable_sort(v.begin(), v.end(), [](const lbd::BatchItem &u, const lbd::BatchItem &w) {
+            return u.rows > w.rows;
+        });
+        if (P < 1) return;
+        std::vector<lbd::BatchItem> out(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const size_t r = i / (size_t)P, k = i % (size_t)P;
+            const size_t cnt = std::min((size_t)P, v.size() - r * (size_t)P);
+            out[i] = v[r * (size_t)P + ((r & 1) ? cnt - 1 - k : k)];
+        }
+        v.swap(out);
+    };
+    deal(plain, b->ctas);
+    deal(walled, b->ctas_walls);
+    // periodic instances first: the plates take a launch of their own
+    std::vector<lbd::BatchItem> items(plain);
+    items.insert(items.end(), walled.begin(), walled.end());
     if (b->items_dev) cudaFree(b->items_dev);
     b->items_dev = nullptr;
     BCK(b, lbd::dev_malloc((void **)&b->items_dev, sizeof(lbd::BatchItem) * items.size()));
@@ -1055,14 +1079,7 @@ int batch_build(lbd_batch *b) {
                            cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     b->n_items = (int)items.size();
-    b->n_plain = (int)std::count_if(items.begin(), items.end(), [&](const lbd::BatchItem &u) { return !walls(u); });
-    int sms = 0;
-    BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
-    const int per_sm_plain = w_plain == 116 ? lbd::vstripe_batch_ctas_per_sm()
-                                            : lbd::stripe_batch_ctas_per_sm<T>(w_plain + 10);
-    const int per_sm_walls = lbd::stripe_batch_ctas_per_sm<T>(w_walls + 10);
-    b->ctas = std::min(b->n_plain, sms * per_sm_plain);
-    b->ctas_walls = std::min(b->n_items - b->n_plain, sms * per_sm_walls);
+    b->n_plain = (int)plain.size();
     batch_drop_graphs(b);
     return LBD_OK;
 }
@@ -2071,8 +2088,8 @@ int lbd_batch_set_tile(lbd_batch *b, int32_t bx, int32_t by) {
 int lbd_batch_autotune(lbd_batch *b, int32_t reps, int32_t *bx, int32_t *by) {
     if (!b || reps < 1) return LBD_EINVAL;
     if (b->sticky) return b->sticky;
-    const Tile cand[] = {{118, 32}, {118, 64}, {118, 128}, {246, 32},
-                         {246, 64}, {116, 32}, {116, 64}, {116, 128}};
+    const Tile cand[] = {{118, 32}, {118, 64}, {118, 128}, {246, 32}, {246, 64},
+                         {116, 32}, {116, 64}, {116, 96},  {116, 128}};
     cudaEvent_t e0, e1;
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
