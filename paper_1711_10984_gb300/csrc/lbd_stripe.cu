@@ -514,9 +514,11 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     };
     const std::integral_constant<bool, true> guarded;
     const std::integral_constant<bool, false> steady;
+    // steady iterations, i in [15, nrows + 9): every stage active (E writes
+    // owned rows from i = 15) and every written row owned (B's last at nrows + 8)
     const int s1 = (yend - y0) + 9;
     int i = 0;
-    for (; i < 16 && i < iters; ++i) body(guarded, i);
+    for (; i < 15 && i < iters; ++i) body(guarded, i);
 #pragma unroll 2
     for (; i < s1; ++i) body(steady, i);
     for (; i < iters; ++i) body(guarded, i);

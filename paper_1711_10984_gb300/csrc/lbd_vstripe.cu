@@ -408,10 +408,12 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
     const Ph<0> ph0;
     const Ph<1> ph1;
     const Ph<2> ph2;
-    // steady iterations: every stage active and every written row owned
+    // steady iterations, i in [15, nrows + 9): every stage active (E from
+    // i = 13, writing owned rows from i = 15) and every written row owned (B's
+    // last row at i = nrows + 8); 15 is a multiple of 3, as the unrolled loop needs
     const int s1 = (yend - y0) + 9;
     int i = 0;
-    for (; i < 18 && i < iters; ++i) body(guarded, i, i % 3);
+    for (; i < 15 && i < iters; ++i) body(guarded, i, i % 3);
 #pragma unroll 1
     for (; i + 3 <= s1; i += 3) {
         body(steady, i, ph0);
