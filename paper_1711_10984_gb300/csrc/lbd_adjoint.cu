@@ -506,13 +506,29 @@ int adjoint_run(const AdjointJob<T> &job) {
         allocs.push_back(ptr);
         return ptr;
     };
-    cudaGraphExec_t graphs[2] = {nullptr, nullptr};  // reverse sweep of a segment, per parity
+    // reverse sweep of a segment, per segment buffer set and adjoint buffer parity
+    cudaGraphExec_t graphs[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    // The recompute of segment s - 1 runs on a second stream while segment s is
+    // reversed: the two use the two segment buffer sets in turn, ordered by events.
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fwd = nullptr, rec_done[2] = {nullptr, nullptr}, rev_done[2] = {nullptr, nullptr};
     auto release = [&]() {
-        for (auto &g : graphs)
-            if (g) {
-                cudaGraphExecDestroy(g);
-                g = nullptr;
+        if (st2) {
+            cudaStreamSynchronize(st2);
+            cudaStreamDestroy(st2);
+            st2 = nullptr;
+        }
+        for (cudaEvent_t *e : {&ev_fwd, &rec_done[0], &rec_done[1], &rev_done[0], &rev_done[1]})
+            if (*e) {
+                cudaEventDestroy(*e);
+                *e = nullptr;
             }
+        for (auto &gp : graphs)
+            for (auto &g : gp)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
         for (void *ptr : allocs) cudaFree(ptr);
         allocs.clear();
         if (own) {
@@ -522,7 +538,8 @@ int adjoint_run(const AdjointJob<T> &job) {
         }
     };
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
-    T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1));
+    T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1) * 2);
+    T *const segs[2] = {seg, seg ? seg + state_elems * (size_t)(K + 1) : nullptr};
     const int n_dense = 49;  // dense arrays of the step's precision carved out below,
                              // after the per-site dL/dB1 accumulator in double
     void *dense_raw = dalloc(sizeof(double) * (size_t)N + sizeof(T) * (size_t)N * n_dense);
@@ -531,6 +548,16 @@ int adjoint_run(const AdjointJob<T> &job) {
     if (!ckpt || !seg || !dense_raw || !part || !gam) {
         release();
         return LBD_ENOMEM;
+    }
+    if (cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_fwd, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&rec_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&rec_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&rev_done[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&rev_done[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        release();
+        return LBD_ECUDA;
     }
     Work<T> w;
     {
@@ -561,15 +588,16 @@ int adjoint_run(const AdjointJob<T> &job) {
         }                                             \
     } while (0)
     auto slot = [&](T *base, int64_t k) { return base + (size_t)k * state_elems; };
-    auto copy_state = [&](T *dst, const T *g, const T *phi, const T *psi) -> cudaError_t {
-        cudaError_t e = cudaMemcpyAsync(dst, g, sizeof(T) * 9 * plane, cudaMemcpyDeviceToDevice, st);
+    auto copy_state = [&](T *dst, const T *g, const T *phi, const T *psi,
+                          cudaStream_t s) -> cudaError_t {
+        cudaError_t e = cudaMemcpyAsync(dst, g, sizeof(T) * 9 * plane, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dst + 9 * plane, phi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st);
+            e = cudaMemcpyAsync(dst + 9 * plane, phi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(dst + 10 * plane, psi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, st);
+            e = cudaMemcpyAsync(dst + 10 * plane, psi, sizeof(T) * plane, cudaMemcpyDeviceToDevice, s);
         return e;
     };
-    auto step_between = [&](const T *in, T *out, int64_t t) -> cudaError_t {
+    auto step_between = [&](const T *in, T *out, int64_t t, cudaStream_t s) -> cudaError_t {
         StepArgs<T> a = job.args;
         a.g_in = in; a.phi_in = in + 9 * plane; a.psi_in = in + 10 * plane;
         a.g_out = out; a.phi_out = out + 9 * plane; a.psi_out = out + 10 * plane;
@@ -577,7 +605,7 @@ int adjoint_run(const AdjointJob<T> &job) {
         activity_at(*job.params, t, &A, &gm);
         a.A = (T)A;
         a.gamma = (T)gm;
-        return launch_step<T>(a, MODE_STEP, job.tile, st);
+        return launch_step<T>(a, MODE_STEP, job.tile, s);
     };
     auto centroid = [&](const T *phi, double *X, double *W) -> cudaError_t {
         centroid_partial<T><<<RB, 256, 0, st>>>(nx, ny, pitch, phi, job.refx, part);
@@ -594,19 +622,25 @@ int adjoint_run(const AdjointJob<T> &job) {
     };
 
     // ---- forward with checkpoints ----
-    ACK(copy_state(slot(ckpt, 0), job.g0, job.phi0, job.psi0));
+    ACK(copy_state(slot(ckpt, 0), job.g0, job.phi0, job.psi0, st));
     double X0, W0;
     ACK(centroid(job.phi0, &X0, &W0));
     for (int64_t sgi = 0; sgi < nseg; ++sgi) {
         const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
-        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
-                       slot(ckpt, sgi) + 10 * plane));
+        // the last segment keeps all its states (buffer set (nseg - 1) & 1): the
+        // reverse sweep starts on them without a recompute; the others alternate
+        // between two slots
+        const bool keep = sgi == nseg - 1;
+        T *const sb = keep ? segs[sgi & 1] : seg;
+        auto at = [&](int64_t j) { return slot(sb, keep ? j : j % 2); };
+        ACK(copy_state(at(0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
+                       slot(ckpt, sgi) + 10 * plane, st));
         for (int64_t k = k0; k < k1; ++k) {
             const int64_t j = k - k0;
-            ACK(step_between(slot(seg, j % 2), slot(seg, (j + 1) % 2), job.t0 + k));
+            ACK(step_between(at(j), at(j + 1), job.t0 + k, st));
         }
-        const T *endp = slot(seg, (k1 - k0) % 2);
-        ACK(copy_state(slot(ckpt, sgi + 1), endp, endp + 9 * plane, endp + 10 * plane));
+        const T *endp = at(k1 - k0);
+        ACK(copy_state(slot(ckpt, sgi + 1), endp, endp + 9 * plane, endp + 10 * plane, st));
     }
     const T *fin = slot(ckpt, nseg);
     double XT, WT;
@@ -642,9 +676,9 @@ int adjoint_run(const AdjointJob<T> &job) {
         activity_at(*job.params, job.t0 + k, &A, &gm);
         gam_h[(size_t)k] = (T)gm;
     }
-    auto reverse_steps = [&](int64_t k0, int64_t k1) -> cudaError_t {
+    auto reverse_steps = [&](const T *sb, int64_t k0, int64_t k1) -> cudaError_t {
         for (int64_t k = k1 - 1; k >= k0; --k) {
-            const T *in = slot(seg, k - k0);
+            const T *in = sb + (size_t)(k - k0) * state_elems;
             fwd123<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, in, w);
             fwd45<T><<<g2, b2, 0, st>>>(ap, w);
             adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
@@ -660,25 +694,46 @@ int adjoint_run(const AdjointJob<T> &job) {
         }
         return cudaSuccess;
     };
+    // the states of segment sgi, recomputed from its checkpoint into buffer set
+    // sgi & 1 on the second stream
+    auto recompute = [&](int64_t sgi) -> cudaError_t {
+        T *const sb = segs[sgi & 1];
+        const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
+        cudaError_t e = copy_state(slot(sb, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
+                                   slot(ckpt, sgi) + 10 * plane, st2);
+        for (int64_t k = k0; k < k1 - 1 && e == cudaSuccess; ++k)
+            e = step_between(slot(sb, k - k0), slot(sb, k - k0 + 1), job.t0 + k, st2);
+        if (e == cudaSuccess) e = cudaEventRecord(rec_done[sgi & 1], st2);
+        return e;
+    };
+    // every recompute follows the forward pass, which used buffer set 0 and left
+    // the last segment's states in its set
+    ACK(cudaEventRecord(ev_fwd, st));
+    ACK(cudaStreamWaitEvent(st2, ev_fwd, 0));
+    ACK(cudaEventRecord(rec_done[(nseg - 1) & 1], st));
     int parity = 0;  // adjoint buffer alternation at the current segment start
     for (int64_t sgi = nseg - 1; sgi >= 0; --sgi) {
         const int64_t k0 = sgi * K, k1 = k0 + K < nsteps ? k0 + K : nsteps;
-        ACK(copy_state(slot(seg, 0), slot(ckpt, sgi), slot(ckpt, sgi) + 9 * plane,
-                       slot(ckpt, sgi) + 10 * plane));
-        for (int64_t k = k0; k < k1 - 1; ++k)
-            ACK(step_between(slot(seg, k - k0), slot(seg, k - k0 + 1), job.t0 + k));
+        const int set = (int)(sgi & 1);
+        // the next segment's recompute overlaps this segment's reverse sweep; its
+        // buffer set was last read by the reverse sweep of segment sgi + 1
+        if (sgi >= 1) {
+            if (sgi + 1 <= nseg - 1) ACK(cudaStreamWaitEvent(st2, rev_done[(sgi + 1) & 1], 0));
+            ACK(recompute(sgi - 1));
+        }
+        ACK(cudaStreamWaitEvent(st, rec_done[set], 0));
         // stream-ordered after the previous segment's reads of gam
         ACK(cudaMemcpyAsync(gam, gam_h.data() + k0, sizeof(T) * (size_t)(k1 - k0),
                             cudaMemcpyHostToDevice, st));
         if (k1 - k0 == K && K > 1) {
-            cudaGraphExec_t &ge = graphs[parity];
+            cudaGraphExec_t &ge = graphs[set][parity];
             if (!ge) {
                 cudaGraph_t g = nullptr;
                 if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
                     release();
                     return LBD_ECUDA;
                 }
-                const cudaError_t e1 = reverse_steps(k0, k1);
+                const cudaError_t e1 = reverse_steps(segs[set], k0, k1);
                 const cudaError_t e2 = cudaStreamEndCapture(st, &g);
                 cudaError_t e3 = cudaErrorUnknown;
                 if (e1 == cudaSuccess && e2 == cudaSuccess)
@@ -705,12 +760,13 @@ int adjoint_run(const AdjointJob<T> &job) {
                 return LBD_ECUDA;
             }
         } else {
-            const cudaError_t e = reverse_steps(k0, k1);
+            const cudaError_t e = reverse_steps(segs[set], k0, k1);
             if (e != cudaSuccess) {
                 release();
                 return LBD_ECUDA;
             }
         }
+        ACK(cudaEventRecord(rev_done[set], st));
         parity ^= (int)((k1 - k0) & 1);
     }
     // dL/dpsi(t0) = lambda psi; dL/dB1 = sum of the per-site accumulator
