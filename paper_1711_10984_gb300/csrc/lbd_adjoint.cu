@@ -512,13 +512,25 @@ int adjoint_run(const AdjointJob<T> &job) {
     // reversed: the two use the two segment buffer sets in turn, ordered by events.
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_fwd = nullptr, rec_done[2] = {nullptr, nullptr}, rev_done[2] = {nullptr, nullptr};
+    // Within a reverse sweep the forward intermediates of step k (fwd123, fwd45)
+    // need only state k, so they run on a third stream, into the set of the
+    // step's parity, while the adjoint kernels of step k + 1 run.
+    cudaStream_t sf = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_f[2] = {nullptr, nullptr},
+                ev_a[2] = {nullptr, nullptr};
     auto release = [&]() {
         if (st2) {
             cudaStreamSynchronize(st2);
             cudaStreamDestroy(st2);
             st2 = nullptr;
         }
-        for (cudaEvent_t *e : {&ev_fwd, &rec_done[0], &rec_done[1], &rev_done[0], &rev_done[1]})
+        if (sf) {
+            cudaStreamSynchronize(sf);
+            cudaStreamDestroy(sf);
+            sf = nullptr;
+        }
+        for (cudaEvent_t *e : {&ev_fwd, &rec_done[0], &rec_done[1], &rev_done[0], &rev_done[1],
+                               &ev_fork, &ev_join, &ev_f[0], &ev_f[1], &ev_a[0], &ev_a[1]})
             if (*e) {
                 cudaEventDestroy(*e);
                 *e = nullptr;
@@ -540,8 +552,9 @@ int adjoint_run(const AdjointJob<T> &job) {
     T *ckpt = (T *)dalloc(sizeof(T) * state_elems * (size_t)(nseg + 1));
     T *seg = (T *)dalloc(sizeof(T) * state_elems * (size_t)(K + 1) * 2);
     T *const segs[2] = {seg, seg ? seg + state_elems * (size_t)(K + 1) : nullptr};
-    const int n_dense = 49;  // dense arrays of the step's precision carved out below,
-                             // after the per-site dL/dB1 accumulator in double
+    const int n_dense = 72;  // dense arrays of the step's precision carved out below,
+                             // after the per-site dL/dB1 accumulator in double: 49, and a
+                             // second set of the 23 forward intermediates
     void *dense_raw = dalloc(sizeof(double) * (size_t)N + sizeof(T) * (size_t)N * n_dense);
     double *part = (double *)dalloc(sizeof(double) * 2 * RB);
     T *gam = (T *)dalloc(sizeof(T) * (size_t)K);  // sink rate of each step of a segment
@@ -554,12 +567,19 @@ int adjoint_run(const AdjointJob<T> &job) {
         cudaEventCreateWithFlags(&rec_done[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&rec_done[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&rev_done[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&rev_done[1], cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&rev_done[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sf, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_f[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_f[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_a[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev_a[1], cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
         release();
         return LBD_ECUDA;
     }
-    Work<T> w;
+    Work<T> w, wf;  // wf: the second set of forward intermediates (the rest unused)
     {
         w.dB1 = reinterpret_cast<double *>(dense_raw);
         T *const dense = reinterpret_cast<T *>(w.dB1 + N);
@@ -574,6 +594,13 @@ int adjoint_run(const AdjointJob<T> &job) {
         w.Lphi = take(1); w.Lpsi = take(1); w.Lbuf = take(9);
         w.Lphi0 = take(1); w.Lpsi0 = take(1); w.Lbuf0 = take(9);
         w.LPHS = take(1); w.LPSS = take(1); w.LFX = take(1); w.LFY = take(1);
+        wf = w;
+        wf.PH = take(1); wf.PS = take(1); wf.GPx = take(1); wf.GPy = take(1); wf.LP = take(1);
+        wf.GSx = take(1); wf.GSy = take(1);
+        wf.GMx = take(1); wf.GMy = take(1); wf.GNx = take(1); wf.GNy = take(1);
+        wf.Fx = take(1); wf.Fy = take(1); wf.RHO = take(1); wf.UX = take(1);
+        wf.UY = take(1); wf.PSS = take(1); wf.GQx = take(1); wf.GQy = take(1);
+        wf.LQ = take(1); wf.GRx = take(1); wf.GRy = take(1); wf.MS = take(1);
         if (d - dense != (ptrdiff_t)n_dense * N) {  // carve-out must match the allocation
             release();
             return LBD_EINVAL;
@@ -676,23 +703,48 @@ int adjoint_run(const AdjointJob<T> &job) {
         activity_at(*job.params, job.t0 + k, &A, &gm);
         gam_h[(size_t)k] = (T)gm;
     }
+    // Step j = k - k0 of a sweep uses forward set j & 1.  fwd(k) on sf waits
+    // for the adjoint kernels of step k + 2 (the last readers of its set); the
+    // adjoint kernels of step k on st wait for fwd(k).  Both orders are events,
+    // so that a captured sweep keeps them as graph edges.
     auto reverse_steps = [&](const T *sb, int64_t k0, int64_t k1) -> cudaError_t {
-        for (int64_t k = k1 - 1; k >= k0; --k) {
+        cudaError_t e = cudaEventRecord(ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(sf, ev_fork, 0);
+        for (int64_t k = k1 - 1; k >= k0 && e == cudaSuccess; --k) {
             const T *in = sb + (size_t)(k - k0) * state_elems;
-            fwd123<T><<<g2, b2, 0, st>>>(ap, in + 9 * plane, in + 10 * plane, in, w);
-            fwd45<T><<<g2, b2, 0, st>>>(ap, w);
-            adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), w);
-            adj_cb<T><<<g2, b2, 0, st>>>(ap, w);
-            adj_a<T><<<g2, b2, 0, st>>>(ap, w);
-            const cudaError_t e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
+            const int q = (int)((k - k0) & 1);
+            Work<T> wk = w;
+            if (q) {
+                wk.PH = wf.PH; wk.PS = wf.PS; wk.GPx = wf.GPx; wk.GPy = wf.GPy; wk.LP = wf.LP;
+                wk.GSx = wf.GSx; wk.GSy = wf.GSy; wk.GMx = wf.GMx; wk.GMy = wf.GMy;
+                wk.GNx = wf.GNx; wk.GNy = wf.GNy; wk.Fx = wf.Fx; wk.Fy = wf.Fy; wk.RHO = wf.RHO;
+                wk.UX = wf.UX; wk.UY = wf.UY; wk.PSS = wf.PSS; wk.GQx = wf.GQx; wk.GQy = wf.GQy;
+                wk.LQ = wf.LQ; wk.GRx = wf.GRx; wk.GRy = wf.GRy; wk.MS = wf.MS;
+            }
+            if (k + 2 < k1) e = cudaStreamWaitEvent(sf, ev_a[q], 0);
+            if (e != cudaSuccess) break;
+            fwd123<T><<<g2, b2, 0, sf>>>(ap, in + 9 * plane, in + 10 * plane, in, wk);
+            fwd45<T><<<g2, b2, 0, sf>>>(ap, wk);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ev_f[q], sf);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_f[q], 0);
+            if (e != cudaSuccess) break;
+            adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), wk);
+            adj_cb<T><<<g2, b2, 0, st>>>(ap, wk);
+            adj_a<T><<<g2, b2, 0, st>>>(ap, wk);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaEventRecord(ev_a[q], st);
+            if (e != cudaSuccess) break;
             // the input adjoints become the output adjoints of the previous step
             T *tp;
             tp = w.Lphi; w.Lphi = w.Lphi0; w.Lphi0 = tp;
             tp = w.Lpsi; w.Lpsi = w.Lpsi0; w.Lpsi0 = tp;
             tp = w.Lbuf; w.Lbuf = w.Lbuf0; w.Lbuf0 = tp;
         }
-        return cudaSuccess;
+        // join: the sweep ends when both streams have
+        if (e == cudaSuccess) e = cudaEventRecord(ev_join, sf);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_join, 0);
+        return e;
     };
     // the states of segment sgi, recomputed from its checkpoint into buffer set
     // sgi & 1 on the second stream
