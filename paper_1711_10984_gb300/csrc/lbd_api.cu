@@ -1038,9 +1038,14 @@ int batch_build(lbd_batch *b) {
         const int nx = b->ctx[k]->grid.nx, ny = b->ctx[k]->grid.ny;
         const bool walls = (b->ctx[k]->params.flags & LBD_WALLS) != 0;
         const int bxo = walls ? w_walls : w_plain;
-        for (int y0 = 0; y0 < ny; y0 += seg)
+        // ceil(ny / seg) row segments of equal height (within one row), so that
+        // no instance leaves a short tail segment that costs a full pipeline fill
+        const int nseg = (ny + seg - 1) / seg;
+        for (int j = 0; j < nseg; ++j) {
+            const int y0 = (int)((long long)ny * j / nseg), y1 = (int)((long long)ny * (j + 1) / nseg);
             for (int x0 = 0; x0 < nx; x0 += bxo)
-                (walls ? walled : plain).push_back(lbd::BatchItem{k, x0, y0, std::min(seg, ny - y0)});
+                (walls ? walled : plain).push_back(lbd::BatchItem{k, x0, y0, y1 - y0});
+        }
     }
     int sms = 0;
     BCK(b, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->ctx[0]->dev));
