@@ -297,9 +297,12 @@ __global__ void adj_ed(AdjPar<R> p, const R *gam, int jstep, Work<R> w) {
 
 // ---- reverse of the donor-cell advection (Eqs. 16-17), then of the collision
 // (Eqs. 10-13), moments (Eq. 11) and streaming at the same site ------------------
+// lambda F of site (x, y) (dense index s) into lFx, lFy; with own, the site's
+// other results too: lambda phi^n, psi^n (added to, set) and the streamed
+// lambda of the populations.
 template <typename R>
-__global__ void adj_cb(AdjPar<R> p, Work<R> w) {
-    LBD_SITE(p)
+__device__ __forceinline__ void adj_cb_site(const AdjPar<R> &p, const Work<R> &w, int x, int y,
+                                            long long s, bool own, R &lFx, R &lFy) {
     const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
     const R *UX = w.UX, *UY = w.UY, *P = w.PH, *C = w.PS;
     const R *LP = w.LPHS, *LC = w.LPSS;
@@ -316,8 +319,10 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
     if (!(uw > 0)) { lphi += lpw * uw; lpsi += lcw * uw; }
     if (un > 0) { lphi += lpn * un; lpsi += lcn * un; }
     if (!(us > 0)) { lphi += lps * us; lpsi += lcs * us; }
-    w.Lphi0[s] += lphi;
-    w.Lpsi0[s] = lpsi;
+    if (own) {
+        w.Lphi0[s] += lphi;
+        w.Lpsi0[s] = lpsi;
+    }
     R lux = R(0.5) * (lpe * up(ue, P[s], P[q.e]) + lce * up(ue, C[s], C[q.e]) +
                       lpw * up(uw, P[q.w], P[s]) + lcw * up(uw, C[q.w], C[s]));
     R luy = R(0.5) * (lpn * up(un, P[s], P[q.n]) + lcn * up(un, C[s], C[q.n]) +
@@ -325,7 +330,9 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
     // collision, moments and streaming
     const R n = w.RHO[s], ux = UX[s], uy = UY[s], Fx = w.Fx[s], Fy = w.Fy[s];
     const R om = p.omega, gk = p.guo, usq = ux * ux + uy * uy;
-    R ln = 0, lFx = 0, lFy = 0;
+    R ln = 0;
+    lFx = 0;
+    lFy = 0;
     R lpost[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -347,8 +354,7 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
     lFx += R(0.5) * lux / n;
     lFy += R(0.5) * luy / n;
     ln += -(lux * ux + luy * uy) / n;
-    w.LFX[s] = lFx;
-    w.LFY[s] = lFy;
+    if (!own) return;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const R lf = (R(1.0) - om) * lpost[i] + ln + ljx * EX(i) + ljy * EY(i);
@@ -358,6 +364,15 @@ __global__ void adj_cb(AdjPar<R> p, Work<R> w) {
         ys = ys < 0 ? ys + p.ny : (ys >= p.ny ? ys - p.ny : ys);
         w.Lbuf0[i * p.N + (long long)ys * p.nx + xs] = lf;
     }
+}
+
+template <typename R>
+__global__ void adj_cb(AdjPar<R> p, Work<R> w) {
+    LBD_SITE(p)
+    R lFx, lFy;
+    adj_cb_site(p, w, x, y, s, true, lFx, lFy);
+    w.LFX[s] = lFx;
+    w.LFY[s] = lFy;
 }
 
 // ---- reverse of the force (Eq. 14) on the tile and its halo: lambda mu =
@@ -396,6 +411,78 @@ __global__ void adj_a(AdjPar<R> p, Work<R> w) {
     const R lfx = LFX[s], lfy = LFY[s];
     const R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
     const R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) + Div(at(LFX, q), at(LFY, q));
+    const R lmu = sMU[t.c], lm = sM[t.c];
+    const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
+    const R ph = PH[s];
+    w.dB1[s] += (double)(lmu * (-PS[s] * w.LP[s] - (px * cx + py * cy)) +
+                         lm * R(0.5) * (px * px + py * py));
+    w.Lphi0[s] = (lphi + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
+                 (-Lap(T(0)) + B1 * Div(T(1), T(2)) - B1 * Div(T(5), T(6)));
+    w.Lpsi0[s] = (lpsi + -B1 * w.LP[s] * lmu) + B1 * Div(T(3), T(4));
+}
+
+// ---- adj_cb and adj_a in one kernel: lambda F (adj_cb) on the tile and a
+// two-site halo into shared memory, the tile's own sites also writing adj_cb's
+// other results; then adj_a's two stages reading lambda F from shared memory.
+// The arithmetic per site is that of the two kernels, so the results are the
+// same; one launch and one global round trip of lambda F fewer per step.
+constexpr int T2X = TBX + 4, T2N = T2X * (TBY + 4);
+template <typename R>
+__global__ void adj_cba(AdjPar<R> p, Work<R> w) {
+    __shared__ R sFX[T2N], sFY[T2N];  // lambda F on the tile and a two-site halo
+    __shared__ R sMU[THN], sM[THN];   // lambda mu, lambda m on the tile and a one-site halo
+    __shared__ R sT[7][THN];          // products at each halo-tile site
+    const int bx0 = blockIdx.x * TBX, by0 = blockIdx.y * TBY;
+    for (int e = threadIdx.y * TBX + threadIdx.x; e < T2N; e += TBX * TBY) {
+        const int ex = e % T2X, ey = e / T2X;
+        int x = (bx0 - 2 + ex) % p.nx, y = (by0 - 2 + ey) % p.ny;
+        x += x < 0 ? p.nx : 0;
+        y += y < 0 ? p.ny : 0;
+        // the tile's own sites, as adj_cb's threads would have them
+        const bool own = ex >= 2 && ex < 2 + TBX && ey >= 2 && ey < 2 + TBY &&
+                         bx0 + ex - 2 < p.nx && by0 + ey - 2 < p.ny;
+        R lFx, lFy;
+        adj_cb_site(p, w, x, y, (long long)y * p.nx + x, own, lFx, lFy);
+        sFX[e] = lFx;
+        sFY[e] = lFy;
+    }
+    __syncthreads();
+    // neighbourhood of the two-site-halo index c
+    auto nb2 = [](int c) {
+        return Nbr{c, c + 1, c - 1, c + T2X, c - T2X, c + T2X + 1, c + T2X - 1, c - T2X + 1,
+                   c - T2X - 1};
+    };
+    const R *PH = w.PH, *PS = w.PS;
+    const R B0 = p.B0, B1 = p.B1;
+    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
+        const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
+        const Nbr u = nb2((e / THX + 1) * T2X + e % THX + 1);
+        auto T1 = [&](int k) { return PH[q[k]] * sFX[u[k]]; };  // -> lambda mu
+        auto T2 = [&](int k) { return PH[q[k]] * sFY[u[k]]; };
+        auto T3 = [&](int k) { return PS[q[k]] * sFX[u[k]]; };  // -> lambda m
+        auto T4 = [&](int k) { return PS[q[k]] * sFY[u[k]]; };
+        const R lmu = Div(T1, T2), lm = Div(T3, T4);
+        sMU[e] = lmu;
+        sM[e] = lm;
+        const long long s = q.c;
+        const R gpx = w.GPx[s], gpy = w.GPy[s];
+        sT[0][e] = (B0 + B1 * PS[s]) * lmu;
+        sT[1][e] = lmu * w.GSx[s];
+        sT[2][e] = lmu * w.GSy[s];
+        sT[3][e] = lmu * gpx;
+        sT[4][e] = lmu * gpy;
+        sT[5][e] = lm * gpx;
+        sT[6][e] = lm * gpy;
+    });
+    __syncthreads();
+    LBD_SITE(p)
+    const Nbr t = tile_nbr();
+    const Nbr u = nb2((threadIdx.y + 2) * T2X + threadIdx.x + 2);
+    auto T = [&](int i) { return At<R>{sT[i], t}; };
+    const R lfx = sFX[u.c], lfy = sFY[u.c];
+    const R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
+    const R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) +
+                   Div(At<R>{sFX, u}, At<R>{sFY, u});
     const R lmu = sMU[t.c], lm = sM[t.c];
     const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
     const R ph = PH[s];
@@ -730,8 +817,7 @@ int adjoint_run(const AdjointJob<T> &job) {
             if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_f[q], 0);
             if (e != cudaSuccess) break;
             adj_ed<T><<<g2, b2, 0, st>>>(ap, gam, (int)(k - k0), wk);
-            adj_cb<T><<<g2, b2, 0, st>>>(ap, wk);
-            adj_a<T><<<g2, b2, 0, st>>>(ap, wk);
+            adj_cba<T><<<g2, b2, 0, st>>>(ap, wk);
             e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaEventRecord(ev_a[q], st);
             if (e != cudaSuccess) break;
