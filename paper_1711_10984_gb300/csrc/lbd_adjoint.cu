@@ -366,66 +366,16 @@ __device__ __forceinline__ void adj_cb_site(const AdjPar<R> &p, const Work<R> &w
     }
 }
 
-template <typename R>
-__global__ void adj_cb(AdjPar<R> p, Work<R> w) {
-    LBD_SITE(p)
-    R lFx, lFy;
-    adj_cb_site(p, w, x, y, s, true, lFx, lFy);
-    w.LFX[s] = lFx;
-    w.LFY[s] = lFy;
-}
-
-// ---- reverse of the force (Eq. 14) on the tile and its halo: lambda mu =
-// div(phi lambda F), lambda m = div(psi lambda F), and there the products that
-// the transposed stencils of mu, m need; then the force's local terms and grad
-// psi term, and the reverse of mu, m (Eqs. 3, 5) on the tile -------------------
-template <typename R>
-__global__ void adj_a(AdjPar<R> p, Work<R> w) {
-    __shared__ R sMU[THN], sM[THN];  // lambda mu, lambda m
-    __shared__ R sT[7][THN];         // products at each halo-tile site
-    const R *LFX = w.LFX, *LFY = w.LFY, *PH = w.PH, *PS = w.PS;
-    const R B0 = p.B0, B1 = p.B1;
-    over_halo_tile(p.nx, p.ny, [&](int e, int x, int y) {
-        const Nbr q = nbr(x, y, p.nx, p.ny, p.nx);
-        auto T1 = [&](int k) { return PH[q[k]] * LFX[q[k]]; };  // -> lambda mu
-        auto T2 = [&](int k) { return PH[q[k]] * LFY[q[k]]; };
-        auto T3 = [&](int k) { return PS[q[k]] * LFX[q[k]]; };  // -> lambda m
-        auto T4 = [&](int k) { return PS[q[k]] * LFY[q[k]]; };
-        const R lmu = Div(T1, T2), lm = Div(T3, T4);
-        sMU[e] = lmu;
-        sM[e] = lm;
-        const long long s = q.c;
-        const R gpx = w.GPx[s], gpy = w.GPy[s];
-        sT[0][e] = (B0 + B1 * PS[s]) * lmu;
-        sT[1][e] = lmu * w.GSx[s];
-        sT[2][e] = lmu * w.GSy[s];
-        sT[3][e] = lmu * gpx;
-        sT[4][e] = lmu * gpy;
-        sT[5][e] = lm * gpx;
-        sT[6][e] = lm * gpy;
-    });
-    __syncthreads();
-    LBD_SITE(p)
-    const Nbr q = nbr(x, y, p.nx, p.ny, p.nx), t = tile_nbr();
-    auto T = [&](int i) { return At<R>{sT[i], t}; };
-    const R lfx = LFX[s], lfy = LFY[s];
-    const R lphi = w.Lphi0[s] + -(lfx * w.GMx[s] + lfy * w.GMy[s]);
-    const R lpsi = (w.Lpsi0[s] + -(lfx * w.GNx[s] + lfy * w.GNy[s])) + Div(at(LFX, q), at(LFY, q));
-    const R lmu = sMU[t.c], lm = sM[t.c];
-    const R px = w.GPx[s], py = w.GPy[s], cx = w.GSx[s], cy = w.GSy[s];
-    const R ph = PH[s];
-    w.dB1[s] += (double)(lmu * (-PS[s] * w.LP[s] - (px * cx + py * cy)) +
-                         lm * R(0.5) * (px * px + py * py));
-    w.Lphi0[s] = (lphi + (p.a + R(3.0) * p.b * ph * ph) * lmu) +
-                 (-Lap(T(0)) + B1 * Div(T(1), T(2)) - B1 * Div(T(5), T(6)));
-    w.Lpsi0[s] = (lpsi + -B1 * w.LP[s] * lmu) + B1 * Div(T(3), T(4));
-}
-
-// ---- adj_cb and adj_a in one kernel: lambda F (adj_cb) on the tile and a
-// two-site halo into shared memory, the tile's own sites also writing adj_cb's
-// other results; then adj_a's two stages reading lambda F from shared memory.
-// The arithmetic per site is that of the two kernels, so the results are the
-// same; one launch and one global round trip of lambda F fewer per step.
+// ---- reverse of the advection, collision and streaming, then of the force
+// (Eq. 14) and of mu, m (Eqs. 3, 5).  Three stages, two barriers:
+//  1. lambda F (adj_cb_site) on the tile and a two-site halo into shared
+//     memory; the tile's own sites also write lambda phi^n, psi^n and the
+//     streamed lambda of the populations;
+//  2. on the tile and a one-site halo: lambda mu = div(phi lambda F), lambda m =
+//     div(psi lambda F), and there the products that the transposed stencils of
+//     mu, m need;
+//  3. on the tile: the force's local terms and grad psi term, and the reverse of
+//     mu, m.
 constexpr int T2X = TBX + 4, T2N = T2X * (TBY + 4);
 template <typename R>
 __global__ void adj_cba(AdjPar<R> p, Work<R> w) {
@@ -438,7 +388,7 @@ __global__ void adj_cba(AdjPar<R> p, Work<R> w) {
         int x = (bx0 - 2 + ex) % p.nx, y = (by0 - 2 + ey) % p.ny;
         x += x < 0 ? p.nx : 0;
         y += y < 0 ? p.ny : 0;
-        // the tile's own sites, as adj_cb's threads would have them
+        // the tile's own sites (one writer per lattice site)
         const bool own = ex >= 2 && ex < 2 + TBX && ey >= 2 && ey < 2 + TBY &&
                          bx0 + ex - 2 < p.nx && by0 + ey - 2 < p.ny;
         R lFx, lFy;
