@@ -144,8 +144,13 @@ def test_adjoint_matches_central_differences():
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():
+    """Every checkpoint interval gives the same gradient bit for bit: one segment
+    (90, 1000), even and odd intervals (2, 45, 13; the recompute of a segment runs
+    on its own stream into one of two buffer sets, and the reverse sweeps of full
+    segments replay graphs per set and adjoint-buffer parity), a partial last
+    segment (13), one step per segment (1)."""
     n, steps = 48, 90
-    outs = [gpu_grad(n, steps, K) for K in (1, 13, 90, 1000)]
+    outs = [gpu_grad(n, steps, K) for K in (1, 2, 13, 45, 90, 1000)]
     for L, dpsi, dB1 in outs[1:]:
         assert L == outs[0][0] and dB1 == outs[0][2]
         assert np.array_equal(dpsi, outs[0][1])
