@@ -463,17 +463,17 @@ RefImage ref_image(int nx, int ny, double refx, double refy) {
 // The FP32 form of the diagnostics reduction, with the results of the FP64
 // form up to rounding, in one launch of RED32_BLOCKS (<= RED_BLOCKS) blocks:
 //  * each thread walks 4-site row chunks (16-byte loads where rows and planes
-//    are 16-byte aligned) and accumulates the six sums in FP32 with Neumaier
-//    compensation; the warps merge the (sum, compensation) pairs by TwoSum
-//    over shuffles; each warp's totals are combined in FP64 per block in a
-//    fixed order, into partial[k * gridDim.x + block];
+//    are 16-byte aligned), sums each chunk's four sites in FP32 and adds the
+//    chunk sums to six Neumaier-compensated FP32 sums; the warps merge the
+//    (sum, compensation) pairs by TwoSum over shuffles, and so do the blocks
+//    (into partial, one float2 slot per value and block) and the last block;
+//    only the final totals are formed in FP64;
 //  * min and max psi stay in FP32: min B = B0 + B1 psi is monotone in psi, so
 //    it is evaluated once, at the extreme psi (max for B1 < 0);
-//  * the minimum-image displacements are integers (RefImage); slots 3-4 are
-//    shifted by the fraction of ref times the phi >= 0 mass in FP64;
-//  * a site whose eleven values do not add up to a finite number is
-//    re-examined value by value, so the count is that of sites holding a
-//    non-finite value;
+//  * the minimum-image displacements are integers (RefImage); slots 3-4 of the
+//    totals are shifted by the fraction of ref times the phi >= 0 mass in FP64;
+//  * a chunk whose values do not add up to a finite number is re-examined
+//    value by value, so the count is that of sites holding a non-finite value;
 //  * the block that finishes last (a counter at partial[NRED * RED_BLOCKS],
 //    zero between calls) combines the block partials in a fixed order and
 //    writes the NRED results to out, so the results do not depend on which
@@ -482,8 +482,9 @@ __global__ void __launch_bounds__(RED_THREADS, 3) reduce_f32(
     int nx, int ny, long long pitch, long long plane, const float *g, const float *phi,
     const float *psi, double B0, double B1, RefImage ri, int vec, double *partial, double *out) {
     constexpr int NW = RED_THREADS / 32;
-    __shared__ double wsum[6][NW];
-    __shared__ float wext[3][NW];  // min psi, max psi, bad count
+    __shared__ float2 wsum[6][NW];  // (sum, compensation) of each warp
+    __shared__ float wext[3][NW];   // min psi, max psi, bad count
+    __shared__ float2 bres[NRED];   // the block's results
     __shared__ bool last;
     float s[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, cmp[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     auto add = [&](int k, float x) {
@@ -519,28 +520,39 @@ __global__ void __launch_bounds__(RED_THREADS, 3) reduce_f32(
                 cv[k] = psi[o + k];
             }
         }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (k >= cnt) break;
-            const float ph = pv[k], c = cv[k];
-            if (!isfinite(gv[k] + ph + c)) {
-                bool nf = !isfinite(ph) || !isfinite(c);
+        // the chunk's sites are summed first, in a fixed order, then each sum
+        // takes one compensated add per chunk
+        const float g4 = (gv[0] + gv[1]) + (gv[2] + gv[3]);
+        const float p4 = (pv[0] + pv[1]) + (pv[2] + pv[3]);
+        const float c4 = (cv[0] + cv[1]) + (cv[2] + cv[3]);
+        if (!isfinite(g4 + p4 + c4)) {
+            for (int k = 0; k < cnt; ++k) {
+                bool nf = !isfinite(pv[k]) || !isfinite(cv[k]);
                 for (int i = 0; i < 9; ++i) nf |= !isfinite(g[i * plane + o + k]);
                 bad += nf ? 1.f : 0.f;
             }
-            add(0, gv[k]);
-            add(1, ph);
-            add(2, c);
-            if (ph >= 0.f) {
-                int kx = x0 + k - ri.ix;
-                if (kx >= ri.hix) kx -= nx; else if (kx < ri.lox) kx += nx;
-                add(3, ph * (float)kx);
-                add(4, ph * (float)ky);
-                add(5, ph);
-            }
-            pmin = fminf(pmin, c);
-            pmax = fmaxf(pmax, c);
         }
+        float cx = 0.f, cw = 0.f;  // phi >= 0: sum of phi x, sum of phi (the row's y is common)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (k < cnt) {
+                const float ph = pv[k], c = cv[k];
+                if (ph >= 0.f) {
+                    int kx = x0 + k - ri.ix;
+                    if (kx >= ri.hix) kx -= nx; else if (kx < ri.lox) kx += nx;
+                    cx = fmaf(ph, (float)kx, cx);
+                    cw += ph;
+                }
+                pmin = fminf(pmin, c);
+                pmax = fmaxf(pmax, c);
+            }
+        }
+        add(0, g4);
+        add(1, p4);
+        add(2, c4);
+        add(3, cx);
+        add(4, cw * (float)ky);
+        add(5, cw);
     }
     // warp: merge the compensated pairs (TwoSum of the sums, compensations added)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -560,64 +572,97 @@ __global__ void __launch_bounds__(RED_THREADS, 3) reduce_f32(
         bad += __shfl_down_sync(0xffffffffu, bad, o);
     }
     if (lane == 0) {
-        for (int k = 0; k < 6; ++k) wsum[k][warp] = (double)s[k] + (double)cmp[k];
+        for (int k = 0; k < 6; ++k) wsum[k][warp] = make_float2(s[k], cmp[k]);
         wext[0][warp] = pmin;
         wext[1][warp] = pmax;
         wext[2][warp] = bad;
     }
     __syncthreads();
+    // The block's totals, then the grid's, stay (sum, compensation) pairs of
+    // floats merged by TwoSum in a fixed order: the FP64 pipe is a small
+    // fraction of the FP32 one, and a few thousand dependent double operations in
+    // one block used to be the kernel's tail.  Each value takes one float2 slot
+    // of the partial array (extremes and the count in .x).
     const int nb = gridDim.x;
+    float2 *const pp = reinterpret_cast<float2 *>(partial);
     // the completion counter sits after the RED_BLOCKS partials of either form
     unsigned long long *counter =
         reinterpret_cast<unsigned long long *>(partial + NRED * RED_BLOCKS);
-    if (threadIdx.x == 0) {
-        double v[6] = {0, 0, 0, 0, 0, 0};
-        float mn = INFINITY, mx = -INFINITY, bd = 0.f;
-        for (int w = 0; w < NW; ++w) {
-            for (int k = 0; k < 6; ++k) v[k] += wsum[k][w];
-            mn = fminf(mn, wext[0][w]);
-            mx = fmaxf(mx, wext[1][w]);
-            bd += wext[2][w];
+    if (threadIdx.x < NRED) {
+        const int k = threadIdx.x;
+        float hi, lo = 0.f;
+        if (k < 6) {
+            hi = wsum[k][0].x;
+            lo = wsum[k][0].y;
+            for (int w = 1; w < NW; ++w) {
+                float t, e;
+                two_sum(hi, wsum[k][w].x, t, e);
+                hi = t;
+                lo = (lo + wsum[k][w].y) + e;
+            }
+        } else {
+            hi = wext[k - 6][0];
+            for (int w = 1; w < NW; ++w)
+                hi = k == 6 ? fminf(hi, wext[0][w]) : (k == 7 ? fmaxf(hi, wext[1][w]) : hi + wext[2][w]);
         }
-        v[3] -= ri.frx * v[5];
-        v[4] -= ri.fry * v[5];
-        for (int k = 0; k < 6; ++k) partial[k * nb + blockIdx.x] = v[k];
-        partial[6 * nb + blockIdx.x] = mn;
-        partial[7 * nb + blockIdx.x] = mx;
-        partial[8 * nb + blockIdx.x] = bd;
-        __threadfence();
+        bres[k] = make_float2(hi, lo);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < NRED; ++k) pp[k * nb + blockIdx.x] = bres[k];
+        asm volatile("fence.acq_rel.gpu;\n" ::: "memory");  // release the block's partials
         last = atomicAdd(counter, 1ull) == (unsigned long long)(nb - 1);
     }
     __syncthreads();
     if (!last) return;
-    // the last block: thread t combines the partials of blocks t, t + 256, ...
-    // (sums in double, extremes), then a fixed tree over the threads; the
-    // order does not depend on which block finished last
-    __threadfence();
-    double v[NRED];
-    for (int k = 0; k < NRED; ++k) v[k] = k == 6 ? INFINITY : (k == 7 ? -INFINITY : 0.0);
-    for (int b = threadIdx.x; b < nb; b += blockDim.x)
-        for (int k = 0; k < NRED; ++k) {
-            const double x = __ldcg(partial + k * nb + b);
-            v[k] = k == 6 ? fmin(v[k], x) : (k == 7 ? fmax(v[k], x) : v[k] + x);
-        }
-    __shared__ double tree[NRED][NW];
+    // the last block: thread t merges the partials of blocks t, t + 256, ...,
+    // then the warps by shuffles and the warp totals in warp order; the order
+    // does not depend on which block finished last
+    asm volatile("fence.acq_rel.gpu;\n" ::: "memory");  // acquire every block's partials
+    float hi[NRED], lo[NRED];
     for (int k = 0; k < NRED; ++k) {
-        double x = v[k];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double y = __shfl_down_sync(0xffffffffu, x, o);
-            x = k == 6 ? fmin(x, y) : (k == 7 ? fmax(x, y) : x + y);
+        hi[k] = k == 6 ? INFINITY : (k == 7 ? -INFINITY : 0.f);
+        lo[k] = 0.f;
+    }
+    auto merge = [](int k, float &h, float &l, float xh, float xl) {
+        if (k == 6) {
+            h = fminf(h, xh);
+        } else if (k == 7) {
+            h = fmaxf(h, xh);
+        } else {
+            float t, e;
+            two_sum(h, xh, t, e);
+            h = t;
+            l = (l + xl) + e;
         }
-        if (lane == 0) tree[k][warp] = x;
+    };
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NRED; ++k) {
+            const float2 x = __ldcg(pp + k * nb + b);
+            merge(k, hi[k], lo[k], x.x, x.y);
+        }
+    __shared__ float2 tree[NRED][NW];
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            const float yh = __shfl_down_sync(0xffffffffu, hi[k], o);
+            const float yl = __shfl_down_sync(0xffffffffu, lo[k], o);
+            merge(k, hi[k], lo[k], yh, yl);
+        }
+        if (lane == 0) tree[k][warp] = make_float2(hi[k], lo[k]);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double r[NRED];
         for (int k = 0; k < NRED; ++k) {
-            r[k] = tree[k][0];
-            for (int w = 1; w < NW; ++w)
-                r[k] = k == 6 ? fmin(r[k], tree[k][w]) : (k == 7 ? fmax(r[k], tree[k][w]) : r[k] + tree[k][w]);
+            float h = tree[k][0].x, l = tree[k][0].y;
+            for (int w = 1; w < NW; ++w) merge(k, h, l, tree[k][w].x, tree[k][w].y);
+            r[k] = (double)h + (double)l;
         }
+        // the minimum-image shift by the fraction of ref, on the totals
+        r[3] -= ri.frx * r[5];
+        r[4] -= ri.fry * r[5];
         for (int k = 0; k < 6; ++k) out[k] = r[k];
         // min B = B0 + B1 psi at the extreme psi; +inf without any site
         const double ext = B1 < 0.0 ? r[7] : r[6];
