@@ -392,51 +392,53 @@ __device__ __forceinline__ void march_zw(const Arg3<T> &p, const T *const (&src)
 template <typename V, bool GRAD, bool LAP>
 struct ZWin {
     using S = typename Lane<V>::type;
-    V cm, tm, dxm, dym;                // plane z - 1
-    V c0, t0, dx0, dy0, e0, ex0, ey0;  // plane z
+    // Kept as partial sums of the outputs at plane z (the last plane before the
+    // arriving one), so that each arrival recomputes every kept value instead of
+    // shifting a window (no register moves in the plane loop).  With D = C - C_prev:
+    //   ax = DX_z / 6 + EX_z / 12 + DX_{z-1} / 12     (d/dx at z = ax + DX_{z+1} / 12)
+    //   ay likewise                                    (d/dy)
+    //   az = D_z / 2 - T_{z-1} / 12                    (d/dz = az + D_{z+1} / 2 + T_{z+1} / 12)
+    //   al = T_z / 3 + E_z / 6 + T_{z-1} / 6 - D_z     (lap = al + T_{z+1} / 6 + D_{z+1})
+    // and bx = DX_z / 12, by = DY_z / 12, tp = T_z, cp = C_z.
+    V ax, ay, az, al, bx, by, tp, cp;
     __device__ __forceinline__ void reset() {
-        cm = tm = dxm = dym = c0 = t0 = dx0 = dy0 = e0 = ex0 = ey0 = Lane<V>::splat(S(0));
+        ax = ay = az = al = bx = by = tp = cp = Lane<V>::splat(S(0));
     }
     // the arriving plane z + 1 (values from get(ex, ey)); with out, the
     // gradient and Laplacian at plane z and its centre value
     template <class Get>
     __device__ __forceinline__ void arrive(Get get, bool out, V &gx, V &gy, V &gz, V &lap,
                                            V &mid) {
+        const V k6 = Lane<V>::splat(S(1) / S(6)), k12 = Lane<V>::splat(S(1) / S(12));
         const V c = get(0, 0);
         const V xp = get(1, 0), xm = get(-1, 0), yp = get(0, 1), ym = get(0, -1);
         const V pp = get(1, 1), pm = get(1, -1), mp = get(-1, 1), mn = get(-1, -1);
         const V t = vfma(c, Lane<V>::splat(S(-4)), (xp + xm) + (yp + ym));
         const V a = pp + pm, b = mp + mn;
-        V e = e0, dx = dx0, dy = dy0, ex = ex0, ey = ey0;
-        if (LAP) e = vfma(c, Lane<V>::splat(S(-4)), a + b);
-        if (GRAD) {
-            dx = xp - xm;
-            dy = yp - ym;
-            ex = a - b;
-            ey = (pp + mp) - (pm + mn);
-        }
+        const V d = c - cp;
         if (out) {
             if (GRAD) {
-                gx = vfma(dx0, Lane<V>::splat(S(1) / S(6)), (ex0 + (dxm + dx)) * Lane<V>::splat(S(1) / S(12)));
-                gy = vfma(dy0, Lane<V>::splat(S(1) / S(6)), (ey0 + (dym + dy)) * Lane<V>::splat(S(1) / S(12)));
-                gz = vfma(c - cm, Lane<V>::splat(S(0.5)), (t - tm) * Lane<V>::splat(S(1) / S(12)));
+                gx = vfma(xp - xm, k12, ax);
+                gy = vfma(yp - ym, k12, ay);
+                gz = az + vfma(d, Lane<V>::splat(S(0.5)), t * k12);
             }
-            if (LAP)
-                lap = vfma(t0, Lane<V>::splat(S(1) / S(3)),
-                           vfma((e0 + tm) + t, Lane<V>::splat(S(1) / S(6)), (c - c0) - (c0 - cm)));
-            mid = c0;
+            if (LAP) lap = al + vfma(t, k6, d);
+            mid = cp;
         }
-        cm = c0;
-        tm = t0;
-        dxm = dx0;
-        dym = dy0;
-        c0 = c;
-        t0 = t;
-        dx0 = dx;
-        dy0 = dy;
-        e0 = e;
-        ex0 = ex;
-        ey0 = ey;
+        if (GRAD) {
+            const V dx = xp - xm, dy = yp - ym;
+            ax = vfma(dx, k6, vfma(a - b, k12, bx));
+            ay = vfma(dy, k6, vfma((pp + mp) - (pm + mn), k12, by));
+            az = vfma(d, Lane<V>::splat(S(0.5)), tp * Lane<V>::splat(S(-1) / S(12)));
+            bx = dx * k12;
+            by = dy * k12;
+        }
+        if (LAP) {
+            const V e = vfma(c, Lane<V>::splat(S(-4)), a + b);
+            al = vfma(t, Lane<V>::splat(S(1) / S(3)), vfma(e + tp, k6, Lane<V>::splat(S(0)) - d));
+        }
+        tp = t;
+        cp = c;
     }
 };
 
