@@ -46,11 +46,13 @@ BYTES_PER_SITE = {1: 22 * 4, 0: 22 * 8}
 # Floating-point operations per site-step of the scheme, counted from the per-site
 # arithmetic of each stage done once (no halo recomputation; an FMA counts 2):
 # mu_phi and m 61, force 10 + moments 26 + gradient window 26 + BGK/Guo
-# collision 92, advection 24, mu*, m* and p* 62, phi/psi updates 58.  Nsight
-# Compute's FP64 counters on the FP64 step (DADD + DMUL + 2 DFMA) give 412
-# executed flops per output site at 512^2 in the 118 x 128 shape, whose halo
-# recomputation adds 15-25 %, consistent with this count.
-FLOPS_PER_SITE = 359
+# collision 92, advection 24, mu*, m* and p* 62, phi/psi updates 58, i.e. 359
+# with every gradient scaled by its 1/12; the kernels return 12 grad and fold
+# the 1/12 into the constants that use it (12 multiplies fewer, the force's
+# body-force add becoming an FMA, m's 1/2 folded into B1): 347.  Nsight
+# Compute's FP64 counters on the FP64 step (DADD + DMUL + 2 DFMA) are in the
+# FP64 profile summary; the 118 x 128 shape's halo recomputation adds 7 %.
+FLOPS_PER_SITE = 347
 # FP64 rate of GB300: 1.25 TFLOP/s nominal at the 2070 MHz maximum SM clock,
 # scaled to the median SM clock sampled during the run.
 FP64_NOMINAL_TFLOPS = 1.25

@@ -102,11 +102,13 @@ __device__ __forceinline__ double2 vmake(double a, double b) { return make_doubl
 // Stencil history of one column for a pair of fields: rows r-1 and r are kept in
 // the well-conditioned form T = L + R - 2C, D = R - L and the centre C; push(r+1)
 // gives the derivatives at row r and advances:
-//   d/dx = (4 D_r + D_{r-1} + D_{r+1}) / 12
-//   d/dy = (C_{r+1} - C_{r-1}) / 2 + (T_{r+1} - T_{r-1}) / 12
-//   lap  = (2/3) T_r + (T_{r-1} + T_{r+1}) / 6 + (C_{r+1} - 2 C_r + C_{r-1})
+//   12 d/dx = 4 D_r + D_{r-1} + D_{r+1}
+//   12 d/dy = 6 (C_{r+1} - C_{r-1}) + T_{r+1} - T_{r-1}
+//   lap     = (2/3) T_r + (T_{r-1} + T_{r+1}) / 6 + (C_{r+1} - 2 C_r + C_{r-1})
 // i.e. the isotropic D2Q9 stencils (1/3, 1/12 gradient weights; 2/3, 1/6
-// Laplacian link weights).
+// Laplacian link weights).  The gradients come out 12 times too large: their
+// users fold the 1/12 into their own constants, which saves a multiply per
+// gradient component on the FP64 pipe.
 template <typename V>
 struct Win2 {
     V cm, c0, tm, t0, dm, d0;
@@ -115,8 +117,8 @@ struct Win2 {
         using S = decltype(cm.x);
         const V t = vfma(c, vsplat(S(-2)), l + r);
         const V d = r - l;
-        gx = vfma(d0, vsplat(S(4)), dm + d) * vsplat(S(1.0 / 12.0));
-        gy = vfma(c - cm, vsplat(S(0.5)), (t - tm) * vsplat(S(1.0 / 12.0)));
+        gx = vfma(d0, vsplat(S(4)), dm + d);
+        gy = vfma(c - cm, vsplat(S(6)), t - tm);
         lap = vfma(t0, vsplat(S(2.0 / 3.0)),
                    vfma(tm + t, vsplat(S(1.0 / 6.0)), (c - c0) - (c0 - cm)));
         mid = c0;
@@ -128,8 +130,8 @@ struct Win2 {
     // as pushing row r's data again, taken from the window instead of shared memory
     __device__ __forceinline__ void push_mirror(V &gx, V &gy, V &lap, V &mid) {
         using S = decltype(cm.x);
-        gx = vfma(d0, vsplat(S(4)), dm + d0) * vsplat(S(1.0 / 12.0));
-        gy = vfma(c0 - cm, vsplat(S(0.5)), (t0 - tm) * vsplat(S(1.0 / 12.0)));
+        gx = vfma(d0, vsplat(S(4)), dm + d0);
+        gy = vfma(c0 - cm, vsplat(S(6)), t0 - tm);
         lap = vfma(t0, vsplat(S(2.0 / 3.0)),
                    vfma(tm + t0, vsplat(S(1.0 / 6.0)), (c0 - c0) - (c0 - cm)));
         mid = c0;
@@ -139,8 +141,8 @@ struct Win2 {
         using S = decltype(cm.x);
         const V t = vfma(c, vsplat(S(-2)), l + r);
         const V d = r - l;
-        gx = vfma(d0, vsplat(S(4)), dm + d) * vsplat(S(1.0 / 12.0));
-        gy = vfma(c - cm, vsplat(S(0.5)), (t - tm) * vsplat(S(1.0 / 12.0)));
+        gx = vfma(d0, vsplat(S(4)), dm + d);
+        gy = vfma(c - cm, vsplat(S(6)), t - tm);
         mid = c0;
         cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
     }
@@ -315,6 +317,8 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     T ux1 = 0, ux2 = 0, uy1 = 0, uy2 = 0, uy3 = 0;  // own u from B, 1..3 iterations old
 
     const T a = p.a, b = p.b, B0 = p.B0, B1 = p.B1;
+    // B1 with the 1/12 of each of two gradient factors (the windows return 12 grad)
+    const T B1g = B1 * T(1.0 / 144.0), B1h = B1 * T(0.5 / 144.0);
     char *const g_out = reinterpret_cast<char *>(p.g_out);
     char *const phi_out = reinterpret_cast<char *>(p.phi_out);
     char *const psi_out = reinterpret_cast<char *>(p.psi_out);
@@ -385,8 +389,8 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 if (!GUARD || i >= 12) {
                     const T pn = r_ps[((r - y0) & (LD - 1)) * RS].x;  // phi^n for the cubic
                     const T mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
-                                  B1 * (gx.x * gx.y + gy.x * gy.y);
-                    const T ms = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
+                                  B1g * (gx.x * gx.y + gy.x * gy.y);
+                    const T ms = B1h * (gx.x * gx.x + gy.x * gy.x);
                     const int so = ((r - y0) & (RM - 1)) * RS;
                     r_ms[so] = vmake(mus, ms);
                     r_pp[so] = vmake(mid.y, mid.y * ms);
@@ -426,10 +430,11 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 wB.push_grad(M1[0], M1[-1], M1[1], gx, gy, mid);  // lanes: mu, m
                 if (!GUARD || i >= 6) {
                     const V pp = r_ps[((r - y0) & (LD - 1)) * RS];  // (phi, psi) at r
-                    // F = -phi grad mu - (grad psi + psi grad m); lanes x, y
+                    // F = -phi grad mu - (grad psi + psi grad m); lanes x, y (the
+                    // gradients 12 times too large, hence the 1/12)
                     V F = vmake(fma(-pp.x, gx.x, fma(-pp.y, gx.y, -gps2.x)),
                                 fma(-pp.x, gy.x, fma(-pp.y, gy.y, -gps2.y)));
-                    F = F + vmake(p.fx, p.fy);  // zero unless LBD_BODY_FORCE
+                    F = vfma(F, vsplat(T(1.0 / 12.0)), vmake(p.fx, p.fy));  // fx, fy: LBD_BODY_FORCE
                     const T *G = s_pop + ps * 9 * NT;
                     const T g0 = G[0];
                     const V g12 = vmake(G[NT], G[2 * NT]), g34 = vmake(G[3 * NT], G[4 * NT]);
@@ -503,8 +508,8 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                 if (!GUARD || i >= 3) {
                     const T ph = mid.x;
                     const T mu = a * ph + b * (ph * ph * ph) - (B0 + B1 * mid.y) * lap.x -
-                                 B1 * (gx.x * gx.y + gy.x * gy.y);
-                    const T m = T(0.5) * B1 * (gx.x * gx.x + gy.x * gy.x);
+                                 B1g * (gx.x * gx.y + gy.x * gy.y);
+                    const T m = B1h * (gx.x * gx.x + gy.x * gy.x);
                     r_mm[((r - y0) & (RM - 1)) * RS] = vmake(mu, m);
                 }
             }
