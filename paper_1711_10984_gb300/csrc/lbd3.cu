@@ -277,8 +277,8 @@ __device__ __forceinline__ void march(const Arg3<T> &p, const T *const (&src)[2 
 // Laplacian of ring fields (and nothing else of the neighbours).  The 19-point
 // stencil splits into per-plane sums over the in-plane 3 x 3 neighbourhood
 // (ZWin below), so each plane is read once, when it arrives, and a thread
-// keeps the sums of the two planes before it in registers: at the arrival of
-// plane k the output is plane k - 1.  The ring holds the arriving plane and
+// keeps in registers the partial sums of its outputs at the plane before it:
+// at the arrival of plane k the output is plane k - 1.  The ring holds the arriving plane and
 // AHEAD planes in flight.  arrive(nb, out, x, y, z, s) receives the arriving
 // plane's neighbourhood (nb.pair(f, ex, ey), nb.one(f, ex, ey)); out says
 // whether plane z = k - 1 (element offset s) is one of the CTA's planes;
