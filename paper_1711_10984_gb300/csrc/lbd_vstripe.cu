@@ -69,39 +69,59 @@ __device__ __forceinline__ float2 vmake(float a, float b) { return make_float2(a
 //   d/dy = (C_{r+1} - C_{r-1}) / 2 + (T_{r+1} - T_{r-1}) / 12
 //   lap  = (2/3) T_r + (T_{r-1} + T_{r+1}) / 6 + (C_{r+1} - 2 C_r + C_{r-1})
 struct Win {
-    float2 cm, c0, tm, t0, dm, d0;
+    // partial sums of the outputs at the last row n (kept values are all
+    // recomputed at each arrival, none is copied from another):
+    //   ax = (D_{n-1} + 4 D_n) / 12, bx = D_n / 12,
+    //   ay = (C_n - C_{n-1}) / 2 - T_{n-1} / 12,
+    //   al = (2/3) T_n + T_{n-1} / 6 - (C_n - C_{n-1}),
+    //   tp = T_n, cp = C_n
+    float2 ax, bx, ay, al, tp, cp;
     __device__ __forceinline__ void reset() {
-        cm = c0 = tm = t0 = dm = d0 = vsplat(0.f);
+        ax = bx = ay = al = tp = cp = vsplat(0.f);
     }
     __device__ __forceinline__ void push(float2 c, float2 l, float2 r, float2 &gx, float2 &gy,
                                          float2 &lap, float2 &mid) {
         const float2 t = vfma(c, vsplat(-2.f), l + r);
         const float2 d = r - l;
-        gx = vfma(d0, vsplat(4.f), dm + d) * vsplat(1.f / 12.f);
-        gy = vfma(c - cm, vsplat(0.5f), (t - tm) * vsplat(1.f / 12.f));
-        lap = vfma(t0, vsplat(2.f / 3.f), vfma(tm + t, vsplat(1.f / 6.f), (c - c0) - (c0 - cm)));
-        mid = c0;
-        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
+        const float2 e = c - cp;
+        const float2 q = tp * vsplat(1.f / 6.f);
+        gx = vfma(d, vsplat(1.f / 12.f), ax);
+        ax = vfma(d, vsplat(1.f / 3.f), bx);
+        bx = d * vsplat(1.f / 12.f);
+        gy = vfma(e, vsplat(0.5f), vfma(t, vsplat(1.f / 12.f), ay));
+        ay = vfma(q, vsplat(-0.5f), e * vsplat(0.5f));
+        lap = vfma(t, vsplat(1.f / 6.f), al + e);
+        al = vfma(t, vsplat(2.f / 3.f), q - e);
+        mid = cp;
+        tp = t;
+        cp = c;
     }
     __device__ __forceinline__ void push_grad(float2 c, float2 l, float2 r, float2 &gx, float2 &gy,
                                               float2 &mid) {
         const float2 t = vfma(c, vsplat(-2.f), l + r);
         const float2 d = r - l;
-        gx = vfma(d0, vsplat(4.f), dm + d) * vsplat(1.f / 12.f);
-        gy = vfma(c - cm, vsplat(0.5f), (t - tm) * vsplat(1.f / 12.f));
-        mid = c0;
-        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
+        const float2 e = c - cp;
+        gx = vfma(d, vsplat(1.f / 12.f), ax);
+        ax = vfma(d, vsplat(1.f / 3.f), bx);
+        bx = d * vsplat(1.f / 12.f);
+        gy = vfma(e, vsplat(0.5f), vfma(t, vsplat(1.f / 12.f), ay));
+        ay = vfma(tp, vsplat(-1.f / 12.f), e * vsplat(0.5f));
+        mid = cp;
+        tp = t;
+        cp = c;
     }
 };
 
 struct WinLap {
-    float2 cm, c0, tm, t0;
-    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = vsplat(0.f); }
+    float2 al, tp, cp;  // as in Win
+    __device__ __forceinline__ void reset() { al = tp = cp = vsplat(0.f); }
     __device__ __forceinline__ float2 push(float2 c, float2 l, float2 r) {
         const float2 t = vfma(c, vsplat(-2.f), l + r);
-        const float2 lap =
-            vfma(t0, vsplat(2.f / 3.f), vfma(tm + t, vsplat(1.f / 6.f), (c - c0) - (c0 - cm)));
-        cm = c0; c0 = c; tm = t0; t0 = t;
+        const float2 e = c - cp;
+        const float2 lap = vfma(t, vsplat(1.f / 6.f), al + e);
+        al = vfma(t, vsplat(2.f / 3.f), vfma(tp, vsplat(1.f / 6.f), vsplat(0.f) - e));
+        tp = t;
+        cp = c;
         return lap;
     }
 };
@@ -215,7 +235,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
     };
 
     uint32_t theta_w = 0;
-    float phs_e = 0.f;
+    float phs_e = 0.f, phs_n = 0.f;
     Win wA, wB, wD;
     WinLap wEm, wEp;
     wA.reset(); wB.reset(); wD.reset(); wEm.reset(); wEp.reset();
@@ -248,7 +268,7 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
             if (!GUARD || i >= 13) {
                 const float2 *M1 = r_ms + s3<-14>(ph) * RS;
                 const float2 *P1 = r_pp + s3<-14>(ph) * RS;
-                const float2 mc = wEm.c0, pc = wEp.c0;
+                const float2 mc = wEm.cp, pc = wEp.cp;
                 const float2 lm = wEm.push(M1[0], M1[-1], M1[1]);
                 const float2 lp = wEp.push(P1[0], P1[-1], P1[1]);
                 if ((!GUARD || r >= y0) && inE) {
@@ -273,8 +293,9 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
             if (!GUARD || (i >= 10 && r < yend + 1)) {
                 const float2 *S1 = r_st + s3<-12>(ph) * RS;
                 float2 gx, gy, lap, mid;
-                phs_e = wD.cm.x;
                 wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);
+                phs_e = phs_n;  // phi* of row y0 - 14 + i, for stage E next iteration
+                phs_n = mid.x;
                 if (!GUARD || i >= 12) {
                     const float pn = Bp[0].x;
                     const float mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
