@@ -99,44 +99,72 @@ __device__ __forceinline__ float rcp_rn(float x) { return __fdividef(1.f, x); }
 __device__ __forceinline__ double rcp_rn(double x) { return 1.0 / x; }
 __device__ __forceinline__ double2 vmake(double a, double b) { return make_double2(a, b); }
 
-// Stencil history of one column for a pair of fields: rows r-1 and r are kept in
-// the well-conditioned form T = L + R - 2C, D = R - L and the centre C; push(r+1)
-// gives the derivatives at row r and advances:
-//   12 d/dx = 4 D_r + D_{r-1} + D_{r+1}
-//   12 d/dy = 6 (C_{r+1} - C_{r-1}) + T_{r+1} - T_{r-1}
-//   lap     = (2/3) T_r + (T_{r-1} + T_{r+1}) / 6 + (C_{r+1} - 2 C_r + C_{r-1})
-// i.e. the isotropic D2Q9 stencils (1/3, 1/12 gradient weights; 2/3, 1/6
-// Laplacian link weights).  The gradients come out 12 times too large: their
-// users fold the 1/12 into their own constants, which saves a multiply per
-// gradient component on the FP64 pipe.
+__device__ __forceinline__ float2 vneg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ double2 vneg(double2 a) { return make_double2(-a.x, -a.y); }
+
+// Stencil history of one column for a pair of fields, for the isotropic D2Q9
+// stencils (1/3, 1/12 gradient weights; 2/3, 1/6 Laplacian link weights).  With
+// T = L + R - 2C, D = R - L and C the centre of row n, arriving row n + 1 gives
+// the derivatives at row n:
+//   12 d/dx = D_{n-1} + 4 D_n + D_{n+1}
+//   12 d/dy = 6 (C_{n+1} - C_{n-1}) + T_{n+1} - T_{n-1}
+//   lap     = (2/3) T_n + (T_{n-1} + T_{n+1}) / 6 + (C_{n+1} - 2 C_n + C_{n-1})
+// The gradients come out 12 times too large: their users fold the 1/12 into
+// their own constants, which saves a multiply per gradient component on the
+// FP64 pipe.  The window keeps partial sums of the outputs at row n, each
+// recomputed at every arrival (nothing is shifted from one kept value to
+// another), with e_n = C_n - C_{n-1}:
+//   ax = D_{n-1} + 4 D_n,   bx = D_n,   ay = 6 e_n - T_{n-1},
+//   al = (2/3) T_n + T_{n-1} / 6 - e_n,   tp = T_n,   cp = C_n,
+// so that 12 d/dx = ax + D_{n+1}, 12 d/dy = ay + T_{n+1} + 6 e_{n+1} and
+// lap = al + T_{n+1} / 6 + e_{n+1}: one FP64 operation per lane fewer than
+// differencing a window of raw rows.
 template <typename V>
 struct Win2 {
+    V ax, bx, ay, al, tp, cp;
+    __device__ __forceinline__ void reset() {
+        ax = bx = ay = al = tp = cp = vsplat(decltype(ax.x)(0));
+    }
+    // row n + 1 as (C, T, D)
+    __device__ __forceinline__ void arrive(V c, V t, V d, V &gx, V &gy, V &lap, V &mid) {
+        using S = decltype(ax.x);
+        const V e = c - cp;
+        gx = ax + d;
+        gy = vfma(e, vsplat(S(6)), ay + t);
+        lap = vfma(t, vsplat(S(1.0 / 6.0)), al + e);
+        mid = cp;
+        ax = vfma(d, vsplat(S(4)), bx);
+        bx = d;
+        ay = vfma(e, vsplat(S(6)), vneg(tp));
+        al = vfma(t, vsplat(S(2.0 / 3.0)), vfma(tp, vsplat(S(1.0 / 6.0)), vneg(e)));
+        tp = t;
+        cp = c;
+    }
+    __device__ __forceinline__ void push(V c, V l, V r, V &gx, V &gy, V &lap, V &mid) {
+        using S = decltype(ax.x);
+        arrive(c, vfma(c, vsplat(S(-2)), l + r), r - l, gx, gy, lap, mid);
+    }
+    // the row below the current one is the current row mirrored (a plate
+    // between): D_{n-1} = D_n, T_{n-1} = T_n, e_n = 0
+    __device__ __forceinline__ void mirror_below() {
+        using S = decltype(ax.x);
+        ax = bx * vsplat(S(5));
+        ay = vneg(tp);
+        al = tp * vsplat(S(5.0 / 6.0));
+    }
+    // push(n + 1) where row n + 1 is row n mirrored (a plate above)
+    __device__ __forceinline__ void push_mirror(V &gx, V &gy, V &lap, V &mid) {
+        arrive(cp, tp, bx, gx, gy, lap, mid);
+    }
+};
+
+// Gradients only, for (mu, m): a window of raw rows (rows n - 1 and n as C, T
+// and D), which costs one operation per lane fewer than partial sums when no
+// Laplacian is formed.
+template <typename V>
+struct WinG2 {
     V cm, c0, tm, t0, dm, d0;
     __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = dm = d0 = vsplat(decltype(cm.x)(0)); }
-    __device__ __forceinline__ void push(V c, V l, V r, V &gx, V &gy, V &lap, V &mid) {
-        using S = decltype(cm.x);
-        const V t = vfma(c, vsplat(S(-2)), l + r);
-        const V d = r - l;
-        gx = vfma(d0, vsplat(S(4)), dm + d);
-        gy = vfma(c - cm, vsplat(S(6)), t - tm);
-        lap = vfma(t0, vsplat(S(2.0 / 3.0)),
-                   vfma(tm + t, vsplat(S(1.0 / 6.0)), (c - c0) - (c0 - cm)));
-        mid = c0;
-        cm = c0; c0 = c; tm = t0; t0 = t; dm = d0; d0 = d;
-    }
-    // the row below the current one is the current row mirrored (a plate between)
-    __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; dm = d0; }
-    // push(r+1) where row r+1 is row r mirrored (a plate above): the same values
-    // as pushing row r's data again, taken from the window instead of shared memory
-    __device__ __forceinline__ void push_mirror(V &gx, V &gy, V &lap, V &mid) {
-        using S = decltype(cm.x);
-        gx = vfma(d0, vsplat(S(4)), dm + d0);
-        gy = vfma(c0 - cm, vsplat(S(6)), t0 - tm);
-        lap = vfma(t0, vsplat(S(2.0 / 3.0)),
-                   vfma(tm + t0, vsplat(S(1.0 / 6.0)), (c0 - c0) - (c0 - cm)));
-        mid = c0;
-        cm = c0; tm = t0; dm = d0;
-    }
     __device__ __forceinline__ void push_grad(V c, V l, V r, V &gx, V &gy, V &mid) {
         using S = decltype(cm.x);
         const V t = vfma(c, vsplat(S(-2)), l + r);
@@ -148,26 +176,29 @@ struct Win2 {
     }
 };
 
+// Laplacian only, in the partial-sum form of Win2: al, tp, cp.
 template <typename V>
 struct WinLap2 {
-    V cm, c0, tm, t0;
-    __device__ __forceinline__ void reset() { cm = c0 = tm = t0 = vsplat(decltype(cm.x)(0)); }
+    V al, tp, cp;
+    __device__ __forceinline__ void reset() { al = tp = cp = vsplat(decltype(al.x)(0)); }
+    __device__ __forceinline__ V arrive(V c, V t) {
+        using S = decltype(al.x);
+        const V e = c - cp;
+        const V lap = vfma(t, vsplat(S(1.0 / 6.0)), al + e);
+        al = vfma(t, vsplat(S(2.0 / 3.0)), vfma(tp, vsplat(S(1.0 / 6.0)), vneg(e)));
+        tp = t;
+        cp = c;
+        return lap;
+    }
     __device__ __forceinline__ V push(V c, V l, V r) {
-        using S = decltype(cm.x);
-        const V t = vfma(c, vsplat(S(-2)), l + r);
-        const V lap = vfma(t0, vsplat(S(2.0 / 3.0)),
-                           vfma(tm + t, vsplat(S(1.0 / 6.0)), (c - c0) - (c0 - cm)));
-        cm = c0; c0 = c; tm = t0; t0 = t;
-        return lap;
+        using S = decltype(al.x);
+        return arrive(c, vfma(c, vsplat(S(-2)), l + r));
     }
-    __device__ __forceinline__ void mirror_below() { cm = c0; tm = t0; }
-    __device__ __forceinline__ V push_mirror() {
-        using S = decltype(cm.x);
-        const V lap = vfma(t0, vsplat(S(2.0 / 3.0)),
-                           vfma(tm + t0, vsplat(S(1.0 / 6.0)), (c0 - c0) - (c0 - cm)));
-        cm = c0; tm = t0;
-        return lap;
+    __device__ __forceinline__ void mirror_below() {
+        using S = decltype(al.x);
+        al = tp * vsplat(S(5.0 / 6.0));
     }
+    __device__ __forceinline__ V push_mirror() { return arrive(cp, tp); }
 };
 
 template <typename T>
@@ -309,8 +340,9 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     };
 
     uint32_t theta_w = 0;         // source-mask word of stage E's current row
-    T phs_e = T(0);               // phi* of stage E's next row, from stage D's window
-    Win2<V> wA, wB, wD;           // (phi, psi), (mu, m), (phi*, psi*)
+    T phs_e = T(0), phs_n = T(0); // phi* of stage E's next row and the row after
+    Win2<V> wA, wD;               // (phi, psi), (phi*, psi*)
+    WinG2<V> wB;                  // (mu, m)
     WinLap2<V> wEm, wEp;          // (mu*, m*), (psi*, p*)
     wA.reset(); wB.reset(); wD.reset(); wEm.reset(); wEp.reset();
     V gps1 = vsplat(T(0)), gps2 = vsplat(T(0));  // grad psi (x, y) from A, 1 and 2 iterations old
@@ -345,7 +377,7 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
                     wEm.mirror_below();
                     wEp.mirror_below();
                 }
-                const V mc = wEm.c0, pc = wEp.c0;            // (mu*, m*), (psi*, p*) at r
+                const V mc = wEm.cp, pc = wEp.cp;            // (mu*, m*), (psi*, p*) at r
                 V lm, lp;                                     // (lap mu*, lap m*), (lap psi*, lap p*)
                 if (WALLS && r == ny - 1) {
                     lm = wEm.push_mirror();
@@ -380,12 +412,13 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
             if (!GUARD || (i >= 10 && r < yend + 1)) {
                 const V *S1 = r_st + ((r + 1 - y0) & (CD - 1)) * RS;
                 V gx, gy, lap, mid;
-                phs_e = wD.cm.x;  // phi* at row r - 1: stage E's row in the next iteration
                 if (WALLS && r == 0) wD.mirror_below();
                 if (WALLS && r == ny - 1)
                     wD.push_mirror(gx, gy, lap, mid);
                 else
                     wD.push(S1[0], S1[-1], S1[1], gx, gy, lap, mid);  // lanes: phi*, psi*
+                phs_e = phs_n;  // phi* at row r - 1: stage E's row in the next iteration
+                phs_n = mid.x;
                 if (!GUARD || i >= 12) {
                     const T pn = r_ps[((r - y0) & (LD - 1)) * RS].x;  // phi^n for the cubic
                     const T mus = a * mid.x + b * (pn * pn * pn) - (B0 + B1 * mid.y) * lap.x -
