@@ -165,7 +165,8 @@ KERNEL_SOURCES = {116: ("lbd_vstripe.cu", "lbd_internal.h"),
 def kernel_name(tile, prec):
     t = "float" if prec == 1 else "double"
     if tile[0] == 116:
-        return "vstripe_kernel (FP32, 116-column stripes, segments of %d rows)" % tile[1]
+        return ("vstripe_kernel (FP32, 116-column stripes, row segments of at most %d rows, "
+                "as many as fill the resident CTA slots evenly)" % tile[1])
     if tile[0] in (118, 246):
         return "stripe_kernel<%s,%d> (segments of %d rows)" % (t, tile[0] + 10, tile[1])
     return "step_kernel<%s,%d,%d>" % (t, tile[0], tile[1])

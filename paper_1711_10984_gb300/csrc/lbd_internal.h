@@ -65,8 +65,10 @@ enum { MODE_STEP = 0, MODE_FIELDS = 1 };
 //   bx in {118, 246}: stripe-marching kernel (lbd_stripe.cu), bx + 10 threads,
 //                     segments of by rows;
 //   bx == 116:        FP32 stripe kernel with 16-byte population staging
-//                     (lbd_vstripe.cu), 128 threads, segments of by rows
-//                     (periodic lattices with nx % 4 == 0 only).
+//                     (lbd_vstripe.cu), 128 threads, segments of at most by
+//                     rows, shorter (down to by / 2) where that fills the
+//                     resident CTA slots evenly (periodic lattices with
+//                     nx % 4 == 0 only).
 struct Tile {
     int bx, by;
 };

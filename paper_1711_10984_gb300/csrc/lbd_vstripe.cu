@@ -26,6 +26,11 @@
 //    s and s + 12: the eight rows an iteration reads (y0 - 13 + i ..
 //    y0 - 6 + i) then sit at fixed offsets from one base slot, which advances
 //    by one slot per iteration, with no wrap to compute per read.
+//  * Launch.  A 1-D grid of (stripe, row segment) CTAs.  Where ceil(ny / by)
+//    segments per stripe would leave resident CTA slots free (2048^2 at by = 64:
+//    576 CTAs for 608 slots, so that 32 SMs would run one CTA fewer than the
+//    rest while the others set the time), the stripes are cut into more,
+//    shorter segments (down to by / 2 rows) until the CTAs fill the slots.
 #include <cstdint>
 #include <type_traits>
 
@@ -445,10 +450,26 @@ __device__ __forceinline__ void vstripe_body(const StepArgs<float> &p, const int
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
-__global__ void __launch_bounds__(NT, 4) vstripe_kernel(const StepArgs<float> p, const int seg) {
+// One CTA per (stripe, row segment) on a 1-D grid, stripes fastest (as a 2-D
+// grid would run them): the first `rem` stripes are cut into base + 1 row
+// segments, the others into base, the heights of a stripe's segments differing
+// by at most one row.
+__global__ void __launch_bounds__(NT, 4) vstripe_kernel(const StepArgs<float> p, const int stripes,
+                                                        const int base, const int rem) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const int x0 = blockIdx.x * W, y0 = blockIdx.y * seg;
-    vstripe_body(p, x0, y0, seg, smem_raw);
+    const int b = blockIdx.x;
+    int s, j;
+    if (b < stripes * base) {
+        j = b / stripes;
+        s = b - j * stripes;
+    } else {
+        s = b - stripes * base;
+        j = base;
+    }
+    const int n = s < rem ? base + 1 : base;
+    // the first ny % n segments one row taller
+    const int q = p.ny / n, r = p.ny - q * n;
+    vstripe_body(p, s * W, j * q + min(j, r), q + (j < r ? 1 : 0), smem_raw);
 }
 
 // Batched step: a persistent grid walks the work items of periodic FP32
@@ -502,8 +523,25 @@ cudaError_t launch_vstripe(const StepArgs<float> &a, int seg, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    dim3 grid((a.nx + W - 1) / W, (a.ny + seg - 1) / seg);
-    vstripe_kernel<<<grid, NT, smem, s>>>(a, seg);
+    // ceil(ny / seg) segments per stripe; when that leaves resident CTA slots
+    // free, more segments (equal heights, at least half a segment each), so
+    // that every SM holds as many CTAs as the others
+    static int slots[64] = {0};
+    if (!slots[dev & 63]) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vstripe_kernel, NT, smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        slots[dev & 63] = per_sm * sms > 0 ? per_sm * sms : 1;
+    }
+    const int stripes = (a.nx + W - 1) / W;
+    const int per = (a.ny + seg - 1) / seg;
+    long long total = (long long)stripes * per;
+    const long long cap = (long long)stripes * (2 * a.ny / seg > per ? 2 * a.ny / seg : per);
+    if (total < slots[dev & 63]) total = slots[dev & 63] < cap ? slots[dev & 63] : cap;
+    const int base = (int)(total / stripes), rem = (int)(total % stripes);
+    vstripe_kernel<<<(unsigned)total, NT, smem, s>>>(a, stripes, base, rem);
     return cudaGetLastError();
 }
 
