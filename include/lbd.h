@@ -268,10 +268,11 @@ int lbd_squirmer(lbd_ctx *ctx, int32_t n, const lbd_droplet *drops, double *b1, 
 
 /* Select the launch shape of the step: bx output columns x by output rows per
  * CTA.  bx 32 or 64: tiled kernel; bx 118 or 246: stripe-marching kernel (one
- * column per thread, segments of by rows); bx 116: FP32 stripe-marching kernel
- * with 16-byte population staging (periodic lattices with nx % 4 == 0; not
- * valid with LBD_WALLS), segments of at most by rows, cut shorter (down to by / 2)
- * where that fills the GPU's resident CTA slots evenly.  Shapes not compiled in, or not valid for the
+ * column per thread); bx 116: FP32 stripe-marching kernel with 16-byte
+ * population staging (periodic lattices with nx % 4 == 0; not valid with
+ * LBD_WALLS).  The stripe kernels cut each stripe into row segments of at most
+ * by rows, shorter (down to by / 2) where that fills the GPU's resident CTA
+ * slots evenly.  Shapes not compiled in, or not valid for the
  * context's precision and lattice, return LBD_EINVAL.  All shapes of one kernel give bit-identical results; different
  * kernels agree to rounding. */
 int lbd_set_tile(lbd_ctx *ctx, int32_t bx, int32_t by);

@@ -563,11 +563,26 @@ __device__ __forceinline__ void stripe_body(const StepArgs<T> &p, const int x0, 
     asm volatile("cp.async.wait_all;\n" ::);
 }
 
+// One CTA per (stripe, row segment) on a 1-D grid, stripes fastest: the first
+// `rem` stripes are cut into base + 1 row segments, the others into base, the
+// heights of a stripe's segments differing by at most one row.
 template <typename T, int NT, bool WALLS>
 __global__ void __launch_bounds__(NT, StripeOcc<T, NT>::value)
-    stripe_kernel(const StepArgs<T> p, const int seg) {
+    stripe_kernel(const StepArgs<T> p, const int stripes, const int base, const int rem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    stripe_body<T, NT, WALLS>(p, blockIdx.x * (NT - 10), blockIdx.y * seg, seg, p.A, p.gamma, smem_raw);
+    const int b = blockIdx.x;
+    int s, j;
+    if (b < stripes * base) {
+        j = b / stripes;
+        s = b - j * stripes;
+    } else {
+        s = b - stripes * base;
+        j = base;
+    }
+    const int n = s < rem ? base + 1 : base;
+    const int q = p.ny / n, r = p.ny - q * n;  // the first ny % n segments one row taller
+    stripe_body<T, NT, WALLS>(p, s * (NT - 10), j * q + min(j, r), q + (j < r ? 1 : 0), p.A,
+                              p.gamma, smem_raw);
 }
 
 // Batched step: CTAs walk the work list; the arguments of the item's instance
@@ -624,8 +639,26 @@ cudaError_t launch_stripe_as(const StepArgs<T> &a, int seg, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         configured |= bit;
     }
-    dim3 grid((a.nx + (NT - 10) - 1) / (NT - 10), (a.ny + seg - 1) / seg);
-    stripe_kernel<T, NT, WALLS><<<grid, NT, smem, s>>>(a, seg);
+    // ceil(ny / seg) segments per stripe; when that leaves resident CTA slots
+    // free, more segments (at least half a segment high), so that every SM
+    // holds as many CTAs as the others
+    static int slots[64] = {0};
+    if (!slots[dev & 63]) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stripe_kernel<T, NT, WALLS>, NT,
+                                                          smem);
+        if (e != cudaSuccess) return e;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        slots[dev & 63] = per_sm * sms > 0 ? per_sm * sms : 1;
+    }
+    const int stripes = (a.nx + (NT - 10) - 1) / (NT - 10);
+    const int per = (a.ny + seg - 1) / seg;
+    long long total = (long long)stripes * per;
+    const long long cap = (long long)stripes * (2 * a.ny / seg > per ? 2 * a.ny / seg : per);
+    if (total < slots[dev & 63]) total = slots[dev & 63] < cap ? slots[dev & 63] : cap;
+    const int base = (int)(total / stripes), rem = (int)(total % stripes);
+    stripe_kernel<T, NT, WALLS><<<(unsigned)total, NT, smem, s>>>(a, stripes, base, rem);
     return cudaGetLastError();
 }
 
